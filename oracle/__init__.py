@@ -1,0 +1,304 @@
+"""CPU FP64 oracle of the short-range TreePM path -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
+``cpu_baseline`` / reference leg may import this package.  The product path
+(the CUDA library and its Python binding) never imports it and shares no code
+with it; the two meet only in the seeded input generators.
+
+The arithmetic lives in ``treepm_oracle.c`` (plain C, FP64, no FMA
+contraction); this module compiles it with gcc and exposes it through ctypes.
+Every function follows the paper (Ishiyama, Nitadori & Makino, SC12):
+Eq. 2 (pair sum), Eq. 3 (cutoff g_P3M), the tree algorithm of Sec. I and
+Barnes' grouped traversal of Sec. II; the readings where the paper is silent
+are listed at the top of the C file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "treepm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_D = C.POINTER(C.c_double)
+_I64 = C.POINTER(C.c_int64)
+_U64 = C.POINTER(C.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2 -ffp-contract=off -fopenmp)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = C.CDLL(build())
+    lib.or_g.restype = C.c_double
+    lib.or_g.argtypes = [C.c_double]
+    lib.or_gpx.restype = C.c_double
+    lib.or_gpx.argtypes = [C.c_double]
+    lib.or_pair.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
+    lib.or_pair_jw.argtypes = [_D, C.c_double, _D, C.c_double, C.c_double, C.c_double, _D]
+    lib.or_brute_force.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D]
+    lib.or_brute_force_sample.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double,
+                                          C.c_int64, _I64, _D]
+    lib.or_brute_vjp.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, _D]
+    lib.or_morton.restype = C.c_uint64
+    lib.or_morton.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
+    lib.or_key_of.restype = C.c_uint64
+    lib.or_key_of.argtypes = [C.c_double, C.c_double, C.c_double]
+    lib.or_build.restype = C.c_void_p
+    lib.or_build.argtypes = [C.c_int64, _D, _D, C.c_int32, C.c_int32]
+    lib.or_lists.restype = C.c_int64
+    lib.or_lists.argtypes = [C.c_void_p, C.c_double, C.c_double]
+    lib.or_list_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
+    lib.or_list_vjp.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, _D]
+    lib.or_refresh_moments.argtypes = [C.c_void_p, _D]
+    lib.or_sizes.argtypes = [C.c_void_p, _I64]
+    lib.or_export_keys.argtypes = [C.c_void_p, _U64, _I64]
+    lib.or_export_nodes.argtypes = [C.c_void_p, _I64, _D]
+    lib.or_export_groups.argtypes = [C.c_void_p, _I64, _D]
+    lib.or_export_lists.argtypes = [C.c_void_p, _I64, _I64]
+    lib.or_free.argtypes = [C.c_void_p]
+    lib.or_num_threads.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def g(xi) -> np.ndarray | float:
+    """Cutoff function g_P3M of Eq. 3."""
+    lib = _load()
+    if np.isscalar(xi):
+        return lib.or_g(float(xi))
+    return np.array([lib.or_g(float(v)) for v in np.ravel(xi)]).reshape(np.shape(xi))
+
+
+def gpx(xi) -> np.ndarray | float:
+    """g'(xi)/xi, Eq. 3 differentiated."""
+    lib = _load()
+    if np.isscalar(xi):
+        return lib.or_gpx(float(xi))
+    return np.array([lib.or_gpx(float(v)) for v in np.ravel(xi)]).reshape(np.shape(xi))
+
+
+def pair(d, mj, G, eps, rcut) -> np.ndarray:
+    """One term of Eq. 2: acceleration from mass mj at offset d = x_j - x_i."""
+    d = _f64(d)
+    out = np.zeros(3)
+    _load().or_pair(_dp(d), float(mj), float(G), float(eps), float(rcut), _dp(out))
+    return out
+
+
+def pair_jw(d, mj, w, G, eps, rcut) -> np.ndarray:
+    """G mj J(d) w for the Jacobian J of one Eq. 2 term."""
+    d, w = _f64(d), _f64(w)
+    out = np.zeros(3)
+    _load().or_pair_jw(_dp(d), float(mj), _dp(w), float(G), float(eps), float(rcut), _dp(out))
+    return out
+
+
+def brute_force(pos, mass, G, eps, rcut) -> np.ndarray:
+    """Eq. 2 summed over all pairs (O(N^2), periodic minimum image)."""
+    pos, mass = _f64(pos), _f64(mass)
+    n = pos.shape[0]
+    acc = np.zeros((n, 3))
+    _load().or_brute_force(n, _dp(pos), _dp(mass), G, eps, rcut, _dp(acc))
+    return acc
+
+
+def brute_force_sample(pos, mass, G, eps, rcut, idx) -> np.ndarray:
+    pos, mass = _f64(pos), _f64(mass)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    acc = np.zeros((idx.size, 3))
+    _load().or_brute_force_sample(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, idx.size,
+                                  idx.ctypes.data_as(_I64), _dp(acc))
+    return acc
+
+
+def brute_vjp(pos, mass, G, eps, rcut, w) -> np.ndarray:
+    """dL/dx of L = sum_i w_i . a_i for the direct sum."""
+    pos, mass, w = _f64(pos), _f64(mass), _f64(w)
+    grad = np.zeros_like(pos)
+    _load().or_brute_vjp(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), _dp(grad))
+    return grad
+
+
+def morton(qx: int, qy: int, qz: int) -> int:
+    return int(_load().or_morton(qx, qy, qz))
+
+
+def key_of(x: float, y: float, z: float) -> int:
+    return int(_load().or_key_of(x, y, z))
+
+
+@dataclass
+class Tree:
+    """Snapshot of an oracle tree (all arrays in key order unless noted)."""
+    n: int
+    keys: np.ndarray           # uint64 [n]
+    perm: np.ndarray           # int64  [n]  sorted -> input index
+    level: np.ndarray          # per node
+    first: np.ndarray
+    count: np.ndarray
+    child: np.ndarray
+    nchild: np.ndarray
+    parent: np.ndarray
+    M: np.ndarray
+    com: np.ndarray            # [nodes,3]
+    lo: np.ndarray
+    hi: np.ndarray
+    cen: np.ndarray
+    half: np.ndarray
+    gfirst: np.ndarray
+    gcount: np.ndarray
+    gcen: np.ndarray
+    ghalf: np.ndarray
+    loff: np.ndarray | None = None
+    ent: np.ndarray | None = None
+
+
+class OracleTree:
+    """Owns one oracle tree built from (pos, mass)."""
+
+    def __init__(self, pos, mass=None, n_leaf: int = 8, n_crit: int = 64):
+        lib = _load()
+        self.pos = _f64(pos)
+        self.mass = None if mass is None else _f64(mass)
+        self.n = self.pos.shape[0]
+        h = lib.or_build(self.n, _dp(self.pos), _dp(self.mass) if self.mass is not None else None,
+                         n_leaf, n_crit)
+        if not h:
+            raise ValueError("oracle rejected the tree parameters")
+        self._h = h
+        self.has_lists = False
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().or_free(h)
+            self._h = None
+
+    def sizes(self):
+        s = np.zeros(4, dtype=np.int64)
+        _load().or_sizes(self._h, s.ctypes.data_as(_I64))
+        return [int(v) for v in s]
+
+    def lists(self, rcut: float, theta: float) -> int:
+        n_ent = int(_load().or_lists(self._h, rcut, theta))
+        self.has_lists = True
+        return n_ent
+
+    def list_forces(self, G, eps, rcut) -> np.ndarray:
+        assert self.has_lists
+        acc = np.zeros((self.n, 3))
+        _load().or_list_forces(self._h, G, eps, rcut, _dp(acc))
+        return acc
+
+    def list_vjp(self, G, eps, rcut, w) -> np.ndarray:
+        assert self.has_lists
+        w = _f64(w)
+        grad = np.zeros((self.n, 3))
+        _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad))
+        return grad
+
+    def refresh(self, pos) -> None:
+        """Re-take monopoles from new positions with the structure frozen."""
+        pos = _f64(pos)
+        _load().or_refresh_moments(self._h, _dp(pos))
+
+    def export(self) -> Tree:
+        lib = _load()
+        n, nn, ng, ne = self.sizes()
+        keys = np.zeros(n, dtype=np.uint64)
+        perm = np.zeros(n, dtype=np.int64)
+        lib.or_export_keys(self._h, keys.ctypes.data_as(_U64), perm.ctypes.data_as(_I64))
+        ints = np.zeros((nn, 6), dtype=np.int64)
+        dbl = np.zeros((nn, 16))
+        lib.or_export_nodes(self._h, ints.ctypes.data_as(_I64), _dp(dbl))
+        gi = np.zeros((ng, 2), dtype=np.int64)
+        gd = np.zeros((ng, 6))
+        lib.or_export_groups(self._h, gi.ctypes.data_as(_I64), _dp(gd))
+        loff = ent = None
+        if self.has_lists:
+            loff = np.zeros(ng + 1, dtype=np.int64)
+            ent = np.zeros(max(ne, 1), dtype=np.int64)
+            lib.or_export_lists(self._h, loff.ctypes.data_as(_I64), ent.ctypes.data_as(_I64))
+            ent = ent[:ne]
+        return Tree(n=n, keys=keys, perm=perm, level=ints[:, 0], first=ints[:, 1],
+                    count=ints[:, 2], child=ints[:, 3], nchild=ints[:, 4], parent=ints[:, 5],
+                    M=dbl[:, 0], com=dbl[:, 1:4], lo=dbl[:, 4:7], hi=dbl[:, 7:10],
+                    cen=dbl[:, 10:13], half=dbl[:, 13:16], gfirst=gi[:, 0], gcount=gi[:, 1],
+                    gcen=gd[:, 0:3], ghalf=gd[:, 3:6], loff=loff, ent=ent)
+
+
+def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64):
+    """Build, list and sum: the oracle's whole short-range force path."""
+    t = OracleTree(pos, mass, n_leaf, n_crit)
+    t.lists(rcut, theta)
+    return t.list_forces(G, eps, rcut), t
+
+
+def leapfrog(pos0, vel0, mass, G, eps, rcut, theta, dt, steps, n_leaf=8, n_crit=64,
+             keep_trees=False):
+    """Kick-drift-kick leapfrog with the short-range force only, rebuilding the
+    tree every force evaluation.  Returns (x_T, v_T, trees) where `trees` holds
+    the oracle tree of each evaluation when keep_trees is set (for frozen-
+    structure finite differences)."""
+    x = _f64(pos0).copy()
+    v = _f64(vel0).copy()
+    trees = []
+    a, t = tree_forces(x, mass, G, eps, rcut, theta, n_leaf, n_crit)
+    if keep_trees:
+        trees.append(t)
+    for _ in range(steps):
+        v = v + a * (0.5 * dt)
+        x = x + v * dt
+        a, t = tree_forces(x, mass, G, eps, rcut, theta, n_leaf, n_crit)
+        if keep_trees:
+            trees.append(t)
+        v = v + a * (0.5 * dt)
+    return x, v, trees
+
+
+def leapfrog_frozen(pos0, vel0, trees, G, eps, rcut, dt, steps):
+    """The same integration with every force evaluation's structure frozen to
+    the given trees (monopoles re-taken from the current positions)."""
+    x = _f64(pos0).copy()
+    v = _f64(vel0).copy()
+
+    def force(t):
+        t.refresh(x)
+        return t.list_forces(G, eps, rcut)
+
+    a = force(trees[0])
+    for s in range(steps):
+        v = v + a * (0.5 * dt)
+        x = x + v * dt
+        a = force(trees[s + 1])
+        v = v + a * (0.5 * dt)
+    return x, v
