@@ -1,0 +1,378 @@
+"""Benchmark of the short-range TreePM path on GB300.
+
+One step = the whole hot path on one synthetic box: tree build (keys, sort,
+octree, monopoles, groups, interaction lists), the FP32 force (Eq. 2 on the
+lists) and its adjoint (VJP with a fixed cotangent).  The workload is the
+FP32-precision clustered box: N = 128^3 = 2,097,152 particles, 70 % in 2000
+NFW halos, r_cut = 3/128, eps = 1/6400, theta = 0.5, n_crit = 64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = short-range interactions per second, counting
+each (i, list entry) pair of the forward pass and of the adjoint pass once
+(interactions = sum over groups of n_i * n_j, the paper's count).  With N > 1
+every rank runs an independent replica (the path does not shard one box), so
+scaling is weak and value sums the ranks' interactions over the slowest rank's
+time.  --impl reference times the CPU FP64 oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "short-range interactions/s (FP32 forward + adjoint, clustered 2M box)"
+UNIT = "interactions/s"
+FLOPS_PER_INTERACTION = 43       # counted FP32 mix of the forward pair term (FMA = 2)
+PAPER_FLOPS_PER_INTERACTION = 51 # the paper's convention (Sec. II-A)
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+CONFIG_K = 2
+
+
+def workload_config():
+    return {"workload": "clustered-2M", "n": 128 ** 3, "halos": 2000, "r_cut": "3/128",
+            "eps": "1/6400", "theta": 0.5, "n_crit": 64, "n_leaf": 8, "seed": 14408,
+            "l2": "flushed (256 MiB write) before every timed step"}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None):
+    """Time the oracle: build + lists once, then `steps` samples of forward +
+    adjoint over a contiguous range of groups holding ~target_fraction of the
+    interactions.  Each step is charged its share of the build + lists time."""
+    import oracle
+    t0 = time.perf_counter()
+    ot = oracle.OracleTree(box.pos, box.mass, box.n_leaf, box.n_crit)
+    ot.lists(box.r_cut, box.theta)
+    t_build = time.perf_counter() - t0
+    ex = ot.export()
+    inter = ex.gcount * np.diff(ex.loff)
+    total = int(inter.sum())
+    cum = np.cumsum(inter)
+    g1 = int(np.searchsorted(cum, target_fraction * total)) + 1
+    sample = int(cum[g1 - 1])
+    frac = sample / total
+    w64 = w.astype(np.float64)
+    times = []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        ot.list_forces_range(0, g1, box.G, box.eps, box.r_cut)
+        ot.list_vjp_range(0, g1, box.G, box.eps, box.r_cut, w64)
+        dt = time.perf_counter() - t0 + frac * t_build
+        if s >= warmup:
+            times.append(dt)
+    cores = oracle.num_threads()
+    per_step = 2 * sample
+    return {"per_step_interactions": per_step, "times": times, "cores": cores,
+            "sample": f"groups [0,{g1}) of {ex.gfirst.size}: {sample} of {total} pair "
+                      f"interactions (x2 forward+adjoint); build+lists {t_build:.2f}s charged "
+                      f"pro rata ({frac:.3f})", "frac": frac, "t_build": t_build}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1211_4406_gb300 import inputs
+    box = inputs.config_box(CONFIG_K)
+    w = inputs.cotangent(box.n, box.seed + 7)
+    r = oracle_sample_rate(box, w, steps=args.steps, warmup=args.warmup)
+    total_t = sum(r["times"])
+    value = r["per_step_interactions"] * len(r["times"]) / total_t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(r["times"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count, measure_peak
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    box = inputs.config_box(CONFIG_K)
+    w = inputs.cotangent(box.n, box.seed + 7)
+    pos_h = torch.tensor(box.pos).pin_memory()
+    mass_h = torch.tensor(box.mass).pin_memory()
+    cot_h = torch.tensor(w).pin_memory()
+    pos = pos_h.to(dev)
+    mass = mass_h.to(dev)
+    cot = cot_h.to(dev)
+    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
+    tree = ShortRangeTree(pos, mass, prm)                   # allocating build (setup)
+    st = tree.stats()
+    acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(p, m, c, evs=None):
+        if evs:
+            evs[0].record(stream)
+        tree.rebuild(p, m)
+        if evs:
+            evs[1].record(stream)
+        tree.force(acc)
+        if evs:
+            evs[2].record(stream)
+        tree.vjp(c, grad)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(pos, mass, cot)
+    torch.cuda.synchronize()
+    status = tree.status()
+    if status != 0:
+        raise RuntimeError(f"tree status {status} after warm-up")
+
+    # ---- device-resident timed region -------------------------------------
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = launch_count()
+    per = []
+    for _ in range(args.steps):
+        flush.zero_()
+        evs = [ev() for _ in range(4)]
+        step(pos, mass, cot, evs)
+        per.append(evs)
+    torch.cuda.synchronize()
+    launches = launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_build = [e[0].elapsed_time(e[1]) for e in per]
+    t_force = [e[1].elapsed_time(e[2]) for e in per]
+    t_vjp = [e[2].elapsed_time(e[3]) for e in per]
+    t_step = [e[0].elapsed_time(e[3]) for e in per]
+    ms_step = sum(t_step) / len(t_step)
+    if tree.status() != 0:
+        raise RuntimeError("tree status after the timed region")
+
+    # ---- end to end from host buffers ---------------------------------------
+    acc_h = torch.empty((box.n, 3), dtype=torch.float32).pin_memory()
+    grad_h = torch.empty((box.n, 3), dtype=torch.float64).pin_memory()
+    pos_d = torch.empty_like(pos)
+    mass_d = torch.empty_like(mass)
+    cot_d = torch.empty_like(cot)
+
+    def e2e_step():
+        pos_d.copy_(pos_h, non_blocking=True)
+        mass_d.copy_(mass_h, non_blocking=True)
+        cot_d.copy_(cot_h, non_blocking=True)
+        step(pos_d, mass_d, cot_d)
+        acc_h.copy_(acc, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    h2d = pos_h.numel() * 8 + mass_h.numel() * 8 + cot_h.numel() * 4
+    d2h = acc_h.numel() * 4 + grad_h.numel() * 8
+
+    # ---- plain FP64 GPU path (same lists), for the speedup --------------------
+    tree64 = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit,
+                                              box.n_leaf, "fp64"))
+    acc64 = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
+    tree64.force(acc64)
+    torch.cuda.synchronize()
+    f64_ms = []
+    for _ in range(2):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        tree64.force(acc64)
+        b.record(stream)
+        b.synchronize()
+        f64_ms.append(a.elapsed_time(b))
+    tree64.close()
+
+    # ---- max over ranks --------------------------------------------------------
+    inter = int(st["n_interactions"])
+    per_step_inter = 2 * inter
+    tot_ms = sum(t_step)
+    tot_e2e = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms, tot_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, tot_e2e = float(t[0]), float(t[1])
+    value = world * per_step_inter * args.steps / (tot_ms * 1e-3)
+    e2e_value = world * per_step_inter * args.steps / (tot_e2e * 1e-3)
+
+    if rank != 0:
+        tree.close()
+        return
+    force_ms = sum(t_force) / len(t_force)
+    vjp_ms = sum(t_vjp) / len(t_vjp)
+    build_ms = sum(t_build) / len(t_build)
+    fp32_peak_nominal = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    achieved = FLOPS_PER_INTERACTION * inter / (force_ms * 1e-3)
+    meas_ffma = measure_peak("fp32")
+    meas_ffma2 = measure_peak("fp32x2")
+    meas_dfma = measure_peak("fp64")
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "pair_fp32_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak_nominal / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak_nominal, "traffic": traffic,
+                     "kernel": "k_pair<float> (FP32 forward pair kernel)",
+                     "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": tot_e2e / args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "phases_ms": {"build": build_ms, "force_fp32": force_ms, "vjp_fp32": vjp_ms,
+                      "force_fp64": sum(f64_ms) / len(f64_ms)},
+        "forward_interactions_per_s": inter / (force_ms * 1e-3),
+        "adjoint_interactions_per_s": inter / (vjp_ms * 1e-3),
+        "fp64_forward_interactions_per_s": inter / (sum(f64_ms) / len(f64_ms) * 1e-3),
+        "fp32_over_fp64_forward_speedup": (sum(f64_ms) / len(f64_ms)) / force_ms,
+        "paper_convention_frac": PAPER_FLOPS_PER_INTERACTION * inter / (force_ms * 1e-3) / fp32_peak_nominal,
+        "measured_peaks_tflops": {"ffma": meas_ffma / 1e12, "ffma2": meas_ffma2 / 1e12,
+                                  "dfma": meas_dfma / 1e12},
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions",
+                                    "n_ambiguous", "mean_ni", "mean_nj", "max_nj")},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample_rate(box, w, steps=1)
+        line["cpu_baseline"] = {"value": r["per_step_interactions"] / r["times"][0], "unit": UNIT,
+                                "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+    tree.close()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

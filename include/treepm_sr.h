@@ -1,0 +1,170 @@
+/*
+ * treepm_sr.h -- C-ABI of libtreepm_sr.so, the GB300 (sm_103a) short-range
+ * TreePM gravity path of Ishiyama, Nitadori & Makino (SC12).
+ *
+ * Problem statement (Sec. II, Eq. 2): given periodic positions r_i in the unit
+ * box, masses m_i and the gravitational constant G, return for every particle
+ * the short-range acceleration
+ *
+ *     f_i = sum_{j != i} G m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ *                        * g_P3M(2 |r_j - r_i| / r_cut)                 (Eq. 2)
+ *
+ * with the cutoff shape g_P3M of Eq. 3 (zero for |r_j - r_i| >= r_cut), the
+ * minimum-image convention of the periodic box (Sec. I), and the sum evaluated
+ * with Barnes' grouped tree traversal (Sec. II): each group of nearby particles
+ * shares one interaction list of particles and monopole tree nodes, built by a
+ * cutoff-pruned walk with opening angle theta (Sec. I).  Eq. 2 carries no m_i:
+ * the result is an acceleration.
+ *
+ * Conventions common to every call
+ *   - Pointers marked "device" must be CUDA device (or managed) memory of the
+ *     current device; pointers marked "host" are ordinary host memory.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; calls return without waiting unless
+ *     stated otherwise.
+ *   - Positions are FP64 [n][3] row-major (x,y,z per particle), any finite
+ *     value (they are wrapped into [0,1)).  Masses are FP64 [n] >= 0, or NULL
+ *     for equal masses 1/n.
+ *   - The caller owns every buffer it passes; they must stay valid until the
+ *     enqueued work has completed.  The library owns tp_tree and everything it
+ *     allocates, released only by tp_tree_free.
+ *   - Errors are returned, never raised: no call aborts, exits or throws.
+ *     Argument errors return synchronously.  Errors detected on the device
+ *     (list overflow, non-finite positions, a bounded wait that expired) are
+ *     latched in the tree and returned by tp_tree_status and by the next call
+ *     on that tree that synchronises.
+ */
+#ifndef TREEPM_SR_H
+#define TREEPM_SR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TP_OK = 0,
+    TP_ERR_INVALID_ARG = -1,   /* a bad pointer, size or parameter           */
+    TP_ERR_CUDA = -2,          /* a CUDA runtime call failed                 */
+    TP_ERR_OOM = -3,           /* device allocation failed                   */
+    TP_ERR_LIST_OVERFLOW = -4, /* a preallocated capacity was too small      */
+    TP_ERR_TIMEOUT = -5,       /* a bounded device-side wait expired         */
+    TP_ERR_NONFINITE = -6,     /* a position was NaN or infinite             */
+    TP_ERR_NO_DEVICE = -7      /* no usable CUDA device                      */
+} tp_status;
+
+typedef enum { TP_FP64 = 0, TP_FP32 = 1 } tp_precision;
+
+/* Per-box parameters (Sec. II and III-A).
+ *   G       gravitational constant
+ *   eps     Plummer softening length, 0 <= eps (Sec. II: eps << r_cut)
+ *   r_cut   cutoff radius, 0 < r_cut < 0.5 of the unit box (Sec. III-A uses
+ *           r_cut = 3 / N_PM^{1/3})
+ *   theta   opening angle, >= 0; 0 gives the exact cutoff sum
+ *   n_crit  largest group size (Barnes' modified algorithm, Sec. II), 1..4096
+ *   n_leaf  a tree node holding more than n_leaf particles is split, 1..64
+ *   precision  TP_FP32 (pair arithmetic in FP32 on group-relative
+ *           coordinates) or TP_FP64 (plain FP64 reference path)
+ *   flags   reserved, must be 0                                              */
+typedef struct {
+    double G, eps, r_cut, theta;
+    int32_t n_crit, n_leaf, precision, flags;
+} tp_params;
+
+typedef struct tp_tree tp_tree; /* opaque, library-owned */
+
+/* Statistics of a built tree (Table I reports the same quantities).
+ * n_interactions = sum over groups of n_i * n_j, the paper's count.        */
+typedef struct {
+    int64_t n, n_nodes, n_groups, n_entries, n_interactions;
+    int64_t n_ambiguous;   /* walk decisions settled by the exact FP64 test  */
+    double mean_ni, mean_nj;
+    int32_t max_nj, nbox;
+} tp_stats;
+
+/* Build the tree of one box: Morton keys, sort, octree, monopoles, groups
+ * and interaction lists (Sec. I and II).  pos: device [n][3]; mass: device
+ * [n] or NULL; p: host.  Synchronises `stream` once (sizes are read back) and
+ * returns the first error seen, including device-detected ones.  On success
+ * *out receives a new tree (free it with tp_tree_free).  n = 0 is valid.     */
+tp_status tp_build_tree(const double *pos, const double *mass, int64_t n,
+                        const tp_params *p, void *stream, tp_tree **out);
+
+/* The same for nbox independent periodic unit boxes stored back to back:
+ * box b holds particles [box_offsets[b], box_offsets[b+1]) of pos/mass.
+ * box_offsets: host [nbox+1], non-decreasing, box_offsets[0] = 0.
+ * per_box: host [nbox], one parameter set per box (precision must agree).
+ * Forces and gradients of a batched tree are written for all boxes at once,
+ * in the input order of pos.                                                */
+tp_status tp_build_tree_batched(const double *pos, const double *mass,
+                                const int64_t *box_offsets, int32_t nbox,
+                                const tp_params *per_box, void *stream, tp_tree **out);
+
+/* Rebuild an existing tree in place from new positions (same n, boxes and
+ * parameters) without allocating and without synchronising: every size is
+ * kept on the device, so the call can be captured in a CUDA graph.  If a
+ * capacity taken from the previous build is exceeded, TP_ERR_LIST_OVERFLOW is
+ * latched (check tp_tree_status after the work completes) and the following
+ * force/vjp calls write zeros; rebuild outside the graph with tp_build_tree. */
+tp_status tp_rebuild_tree(tp_tree *t, const double *pos, const double *mass, void *stream);
+
+/* Short-range accelerations, Eq. 2, for the lists of t.  acc: device [n][3]
+ * in input order; float when the tree's precision is TP_FP32, double when it
+ * is TP_FP64.  Overwritten.  Asynchronous.                                  */
+tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream);
+
+/* Vector-Jacobian product of tp_short_range_force for the fixed tree and
+ * lists of t: given cot = dL/da (device [n][3], same type as acc), writes
+ * grad = dL/dx (device [n][3] double, input order, overwritten).  Per pair
+ * the 3x3 tidal tensor J = phi I + (phi'/r) d d^T of Eq. 2's term acts on the
+ * cotangent; monopole entries pass their share to member particles through
+ * the centre of mass.  Walk decisions are piecewise constant and are not
+ * differentiated.  Asynchronous.                                            */
+tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *stream);
+
+/* Synchronise the tree's last stream and return its first latched error.   */
+tp_status tp_tree_status(tp_tree *t);
+
+/* Host copy of the tree statistics (synchronises).                          */
+tp_status tp_tree_stats(tp_tree *t, tp_stats *out);
+
+/* Parity exports (synchronise; host buffers sized from tp_tree_stats).
+ * keys: [n] Morton keys in key order; perm: [n] input index of each sorted
+ * particle.                                                                 */
+tp_status tp_export_keys(tp_tree *t, uint64_t *keys, int64_t *perm);
+/* ints: [n_nodes][7] = level, first, count, first_child (-1 leaf), n_children,
+ * parent (-1 root), box; dbl: [n_nodes][16] = M, com xyz, lo xyz, hi xyz,
+ * centre xyz, half-width xyz.  Nodes are numbered breadth first.            */
+tp_status tp_export_nodes(tp_tree *t, int64_t *ints, double *dbl);
+/* ints: [n_groups][3] = first, count, box; dbl: [n_groups][6] = centre xyz,
+ * half-width xyz.                                                           */
+tp_status tp_export_groups(tp_tree *t, int64_t *ints, double *dbl);
+/* offsets: [n_groups+1]; entries: [n_entries], >= 0 a particle (key-order
+ * index), < 0 a node -(id+1); each group's list in depth-first order.       */
+tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
+
+tp_status tp_tree_free(tp_tree *t);
+
+/* Leapfrog helpers for the kick-drift-kick integrator (y += a * x):
+ * y: device double [n]; x: device [n], float when x_is_f32 else double.     */
+tp_status tp_axpy(double *y, const void *x, int32_t x_is_f32, double a, int64_t n,
+                  void *stream);
+/* out = a * x with out float when out_is_f32 else double; x: device double. */
+tp_status tp_scale(void *out, int32_t out_is_f32, const double *x, double a, int64_t n,
+                   void *stream);
+
+/* Arithmetic peak of this GPU measured by a dependency-free FMA loop:
+ * kind 0 = FP32 FFMA, 1 = FP32 packed f32x2 FMA, 2 = FP64 DFMA.  Writes flops
+ * per second (an FMA counts 2) to *flops.  Synchronises.                    */
+tp_status tp_measure_peak(int32_t kind, double *flops, void *stream);
+
+/* Number of kernels this library launched since it was loaded.             */
+int64_t tp_launch_count(void);
+
+const char *tp_status_string(tp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREEPM_SR_H */

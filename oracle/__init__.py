@@ -66,6 +66,10 @@ def _load():
     lib.or_lists.argtypes = [C.c_void_p, C.c_double, C.c_double]
     lib.or_list_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
     lib.or_list_vjp.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, _D]
+    lib.or_list_forces_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                         C.c_double, _D]
+    lib.or_list_vjp_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                      C.c_double, _D, _D]
     lib.or_refresh_moments.argtypes = [C.c_void_p, _D]
     lib.or_sizes.argtypes = [C.c_void_p, _I64]
     lib.or_export_keys.argtypes = [C.c_void_p, _U64, _I64]
@@ -224,6 +228,21 @@ class OracleTree:
         w = _f64(w)
         grad = np.zeros((self.n, 3))
         _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad))
+        return grad
+
+    def list_forces_range(self, g0, g1, G, eps, rcut) -> np.ndarray:
+        """Forces of groups [g0, g1) only (other rows stay zero)."""
+        assert self.has_lists
+        acc = np.zeros((self.n, 3))
+        _load().or_list_forces_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(acc))
+        return acc
+
+    def list_vjp_range(self, g0, g1, G, eps, rcut, w) -> np.ndarray:
+        """Gradient of sum over groups [g0, g1) of w_i . a_i."""
+        assert self.has_lists
+        w = _f64(w)
+        grad = np.zeros((self.n, 3))
+        _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad))
         return grad
 
     def refresh(self, pos) -> None:

@@ -605,13 +605,14 @@ static inline void entry_src(const or_tree *t, int64_t e, double *xj, double *mj
     }
 }
 
-/* Eq. 2 over each group's list (nodes enter as monopoles, the self entry is
- * skipped); acc is written in input order. */
-void or_list_forces(const or_tree *t, double G, double eps, double rcut, double *acc)
+/* Eq. 2 over the lists of groups [g0, g1) (nodes enter as monopoles, the self
+ * entry is skipped); acc is written in input order for those groups' particles. */
+void or_list_forces_range(const or_tree *t, int64_t g0, int64_t g1, double G, double eps,
+                          double rcut, double *acc)
 {
     or_prm P = make_prm(G, eps, rcut, 0.0);
 #pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t g = 0; g < t->n_groups; g++) {
+    for (int64_t g = g0; g < g1; g++) {
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
             double ax = 0, ay = 0, az = 0;
             for (int64_t q = t->loff[g]; q < t->loff[g + 1]; q++) {
@@ -628,20 +629,25 @@ void or_list_forces(const or_tree *t, double G, double eps, double rcut, double 
     }
 }
 
+void or_list_forces(const or_tree *t, double G, double eps, double rcut, double *acc)
+{
+    or_list_forces_range(t, 0, t->n_groups, G, eps, rcut, acc);
+}
+
 /* Vector-Jacobian product of or_list_forces for fixed lists: w = dL/da (input
  * order) -> dL/dx (input order).  Per pair v = G m_j J(d) w_i goes to -i and +j;
  * for a node entry it goes to the node's cotangent c_n, which reaches each
  * member p as m_p * sum over the ancestors a of p of c_a / M_a (the derivative
  * of the centre of mass). */
-void or_list_vjp(const or_tree *t, double G, double eps, double rcut, const double *wv,
-                 double *grad)
+void or_list_vjp_range(const or_tree *t, int64_t g0, int64_t g1, double G, double eps,
+                       double rcut, const double *wv, double *grad)
 {
     or_prm P = make_prm(G, eps, rcut, 0.0);
     int64_t n = t->n, nn = t->n_nodes;
     double *gs = (double *)calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
     double *cot = (double *)calloc((size_t)(3 * (nn > 0 ? nn : 1)), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t g = 0; g < t->n_groups; g++) {
+    for (int64_t g = g0; g < g1; g++) {
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
             const double *wi = wv + 3 * t->perm[i];
             double gi[3] = {0, 0, 0};
@@ -683,6 +689,13 @@ void or_list_vjp(const or_tree *t, double G, double eps, double rcut, const doub
     free(pre);
     free(cot);
     free(gs);
+}
+
+/* The gradient of sum_i w_i . a_i for all groups' lists. */
+void or_list_vjp(const or_tree *t, double G, double eps, double rcut, const double *wv,
+                 double *grad)
+{
+    or_list_vjp_range(t, 0, t->n_groups, G, eps, rcut, wv, grad);
 }
 
 /* Re-take the monopoles from new positions (input order) with the tree, the

@@ -1,0 +1,211 @@
+"""Python front end of the short-range TreePM library.
+
+Thin marshalling over the C-ABI: torch tensors on the GPU supply device
+pointers, torch's current stream supplies the CUDA stream, and every step of
+the path runs in libtreepm_sr.so.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(x: torch.Tensor, shape_last=None) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if x.dtype != torch.float64:
+        raise TypeError("positions and masses must be float64")
+    x = x.contiguous()
+    if shape_last is not None and (x.dim() != 2 or x.shape[1] != shape_last):
+        raise ValueError(f"expected shape [n, {shape_last}]")
+    return x
+
+
+@dataclass
+class Params:
+    """Short-range parameters of one periodic unit box (Sec. II, III-A)."""
+    G: float = 1.0
+    eps: float = 0.0
+    r_cut: float = 0.1
+    theta: float = 0.5
+    n_crit: int = 64
+    n_leaf: int = 8
+    precision: str = "fp32"
+
+    def c(self) -> _lib.TPParams:
+        return _lib.params(self.G, self.eps, self.r_cut, self.theta, self.n_crit, self.n_leaf,
+                           self.precision)
+
+
+class ShortRangeTree:
+    """A built tree (keys, octree, monopoles, groups, interaction lists) over
+    one box or a batch of independent boxes, owned by the library."""
+
+    def __init__(self, pos: torch.Tensor, mass: torch.Tensor | None, params,
+                 box_offsets=None, stream=None):
+        lib = _lib.load()
+        pos = _dev_f64(pos, 3)
+        if mass is not None:
+            mass = _dev_f64(mass)
+        self.n = int(pos.shape[0])
+        if isinstance(params, Params):
+            params = [params]
+        params = list(params)
+        if box_offsets is None:
+            box_offsets = [0, self.n]
+        box_offsets = [int(v) for v in box_offsets]
+        if len(box_offsets) != len(params) + 1 or box_offsets[-1] != self.n:
+            raise ValueError("box_offsets must have len(params)+1 entries ending at n")
+        self.params = params
+        self.box_offsets = box_offsets
+        self.precision = params[0].precision
+        self.acc_dtype = torch.float32 if self.precision == "fp32" else torch.float64
+        self._pos, self._mass = pos, mass          # keep alive until the build completes
+        arr = (C.c_int64 * len(box_offsets))(*box_offsets)
+        prm = (_lib.TPParams * len(params))(*[p.c() for p in params])
+        h = C.c_void_p()
+        code = lib.tp_build_tree_batched(C.c_void_p(pos.data_ptr()),
+                                         C.c_void_p(mass.data_ptr()) if mass is not None else None,
+                                         arr, len(params), prm, _stream(stream), C.byref(h))
+        _lib.check(code, "tp_build_tree_batched")
+        self._h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.load().tp_tree_free(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise RuntimeError("tree has been freed")
+        return self._h
+
+    # -- path ---------------------------------------------------------------
+    def rebuild(self, pos: torch.Tensor, mass: torch.Tensor | None = None, stream=None) -> None:
+        pos = _dev_f64(pos, 3)
+        if pos.shape[0] != self.n:
+            raise ValueError("rebuild needs the same particle count")
+        self._pos, self._mass = pos, mass
+        code = _lib.load().tp_rebuild_tree(self.handle, C.c_void_p(pos.data_ptr()),
+                                           C.c_void_p(mass.data_ptr()) if mass is not None else None,
+                                           _stream(stream))
+        _lib.check(code, "tp_rebuild_tree")
+
+    def force(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Short-range accelerations (Eq. 2), [n, 3] in input order."""
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=self.acc_dtype, device=self._pos.device)
+        if out.dtype != self.acc_dtype or not out.is_contiguous() or tuple(out.shape) != (self.n, 3):
+            raise ValueError("out must be a contiguous [n,3] tensor of the tree's precision")
+        code = _lib.load().tp_short_range_force(self.handle, C.c_void_p(out.data_ptr()), _stream(stream))
+        _lib.check(code, "tp_short_range_force")
+        return out
+
+    def vjp(self, cot: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """dL/dx (float64 [n,3]) for the cotangent dL/da of the force."""
+        cot = cot.to(self.acc_dtype).contiguous()
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=torch.float64, device=self._pos.device)
+        code = _lib.load().tp_short_range_vjp(self.handle, C.c_void_p(cot.data_ptr()),
+                                              C.c_void_p(out.data_ptr()), _stream(stream))
+        _lib.check(code, "tp_short_range_vjp")
+        return out
+
+    def status(self) -> int:
+        return int(_lib.load().tp_tree_status(self.handle))
+
+    # -- statistics and parity exports ----------------------------------------
+    def stats(self) -> dict:
+        st = _lib.TPStats()
+        _lib.check(_lib.load().tp_tree_stats(self.handle, C.byref(st)), "tp_tree_stats")
+        return {f: getattr(st, f) for f, _ in _lib.TPStats._fields_}
+
+    def export_keys(self):
+        n = self.n
+        keys = np.zeros(n, dtype=np.uint64)
+        perm = np.zeros(n, dtype=np.int64)
+        _lib.check(_lib.load().tp_export_keys(self.handle, keys.ctypes.data_as(C.c_void_p),
+                                              perm.ctypes.data_as(C.c_void_p)), "tp_export_keys")
+        return keys, perm
+
+    def export_nodes(self):
+        nn = self.stats()["n_nodes"]
+        ints = np.zeros((max(nn, 1), 7), dtype=np.int64)
+        dbl = np.zeros((max(nn, 1), 16))
+        _lib.check(_lib.load().tp_export_nodes(self.handle, ints.ctypes.data_as(C.c_void_p),
+                                               dbl.ctypes.data_as(C.c_void_p)), "tp_export_nodes")
+        return ints[:nn], dbl[:nn]
+
+    def export_groups(self):
+        ng = self.stats()["n_groups"]
+        ints = np.zeros((max(ng, 1), 3), dtype=np.int64)
+        dbl = np.zeros((max(ng, 1), 6))
+        _lib.check(_lib.load().tp_export_groups(self.handle, ints.ctypes.data_as(C.c_void_p),
+                                                dbl.ctypes.data_as(C.c_void_p)), "tp_export_groups")
+        return ints[:ng], dbl[:ng]
+
+    def export_lists(self):
+        st = self.stats()
+        off = np.zeros(st["n_groups"] + 1, dtype=np.int64)
+        ent = np.zeros(max(st["n_entries"], 1), dtype=np.int32)
+        _lib.check(_lib.load().tp_export_lists(self.handle, off.ctypes.data_as(C.c_void_p),
+                                               ent.ctypes.data_as(C.c_void_p)), "tp_export_lists")
+        return off, ent[:st["n_entries"]]
+
+
+def short_range_force(pos: torch.Tensor, mass: torch.Tensor | None, params: Params,
+                      stream=None) -> torch.Tensor:
+    """Build and evaluate in one call (the tree is freed afterwards)."""
+    t = ShortRangeTree(pos, mass, params, stream=stream)
+    try:
+        return t.force(stream=stream)
+    finally:
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        t.close()
+
+
+def axpy(y: torch.Tensor, x: torch.Tensor, a: float, stream=None) -> None:
+    """y += a * x in the library (y float64; x float32 or float64)."""
+    if y.dtype != torch.float64 or not y.is_contiguous() or not x.is_contiguous():
+        raise TypeError("y must be contiguous float64, x contiguous")
+    code = _lib.load().tp_axpy(C.c_void_p(y.data_ptr()), C.c_void_p(x.data_ptr()),
+                               1 if x.dtype == torch.float32 else 0, float(a), y.numel(), _stream(stream))
+    _lib.check(code, "tp_axpy")
+
+
+def scale(out: torch.Tensor, x: torch.Tensor, a: float, stream=None) -> None:
+    """out = a * x in the library (x float64; out float32 or float64)."""
+    code = _lib.load().tp_scale(C.c_void_p(out.data_ptr()), 1 if out.dtype == torch.float32 else 0,
+                                C.c_void_p(x.data_ptr()), float(a), x.numel(), _stream(stream))
+    _lib.check(code, "tp_scale")
+
+
+def measure_peak(kind: str, stream=None) -> float:
+    """FLOP/s of a dependency-free FMA loop: 'fp32', 'fp32x2' or 'fp64'."""
+    k = {"fp32": 0, "fp32x2": 1, "fp64": 2}[kind]
+    v = C.c_double()
+    _lib.check(_lib.load().tp_measure_peak(k, C.byref(v), _stream(stream)), "tp_measure_peak")
+    return v.value
+
+
+def launch_count() -> int:
+    return int(_lib.load().tp_launch_count())

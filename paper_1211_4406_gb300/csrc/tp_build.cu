@@ -1,0 +1,391 @@
+// tp_build.cu -- tree construction on the GPU: Morton keys of the wrapped
+// positions, key-order gather, breadth-first octree topology, node monopoles
+// and particle groups (the "tree construction" phase of Table I; the tree
+// algorithm of Sec. I and Barnes' grouping of Sec. II).
+//
+// Every FP64 operation that decides a result the CPU oracle must reproduce bit
+// for bit is written with explicit round-to-nearest intrinsics, so that no
+// multiply-add is contracted into an FMA.
+#include "tp_common.cuh"
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kLevelGrid = 152 * 4;   // fixed grid: node counts live on the device
+
+__device__ __forceinline__ double wrap01(double x)
+{
+    double w = __dsub_rn(x, floor(x));
+    return w >= 1.0 ? 0.0 : w;
+}
+
+// 21 bits -> every third bit of 63 (bit b lands on 3b).
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t quantise(double w)
+{
+    double q = floor(w * 2097152.0);
+    if (q > 2097151.0) q = 2097151.0;
+    if (q < 0.0) q = 0.0;
+    return (uint32_t)q;
+}
+
+// a1: wrap, quantise to 21 bits per axis, interleave (x bit highest).
+__global__ void k_keys(const double *pos, int64_t n, uint64_t *key, uint32_t *perm, int32_t *status)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+            tp_latch(status, TP_ERR_NONFINITE);
+            key[i] = 0;
+        } else {
+            key[i] = (spread3(quantise(wrap01(x))) << 2) | (spread3(quantise(wrap01(y))) << 1) |
+                     spread3(quantise(wrap01(z)));
+        }
+        perm[i] = (uint32_t)i;
+    }
+}
+
+// a3: sorted FP64 SoA (wrapped), masses, 64-bit fixed-point images.
+__global__ void k_gather(const double *pos, const double *mass, TreeDev T)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < T.n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = T.perm[s];
+        const double x = wrap01(pos[3 * i]), y = wrap01(pos[3 * i + 1]), z = wrap01(pos[3 * i + 2]);
+        T.x[s] = x; T.y[s] = y; T.z[s] = z;
+        T.X[s] = tp_fixed64(x); T.Y[s] = tp_fixed64(y); T.Z[s] = tp_fixed64(z);
+        T.m[s] = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
+    }
+}
+
+__global__ void k_init_roots(TreeDev T)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) {
+        T.lstart[0] = 0;
+        T.lcount[0] = T.nbox;
+        for (int L = 1; L <= TP_NLEVELS; L++) { T.lstart[L] = T.nbox; T.lcount[L] = 0; }
+        *T.n_nodes = T.nbox;
+    }
+    if (b < T.nbox) {
+        T.first[b] = (int32_t)T.box_off[b];
+        T.count[b] = (int32_t)(T.box_off[b + 1] - T.box_off[b]);
+        T.level[b] = 0;
+        T.parent[b] = -1;
+        T.skip[b] = -1;
+        T.child[b] = -1;
+        T.nchild[b] = 0;
+        T.nbx[b] = b;
+    }
+}
+
+// First index in [lo, hi) whose octant digit (at `shift`) is >= o.
+__device__ __forceinline__ int32_t octant_lower(const uint64_t *key, int32_t lo, int32_t hi, int shift,
+                                                uint32_t o)
+{
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (((uint32_t)(key[mid] >> shift) & 7u) < o) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int child_bounds(const TreeDev &T, int32_t i, int L, int32_t *b)
+{
+    const int32_t f = T.first[i], c = T.count[i];
+    if (L >= TP_MAX_LEVEL || c <= T.box[T.nbx[i]].n_leaf) return 0;
+    const int shift = 3 * (TP_MAX_LEVEL - 1 - L);
+    b[0] = f;
+    b[8] = f + c;
+    int k = 0;
+    for (uint32_t o = 1; o < 8; o++) b[o] = octant_lower(T.key, b[o - 1], f + c, shift, o);
+    for (int o = 0; o < 8; o++) k += b[o + 1] > b[o];
+    return k;
+}
+
+// a4 (count): number of non-empty children of every node of level L.
+__global__ void k_split_count(TreeDev T, int L, uint32_t *nch)
+{
+    const int64_t nl = T.lcount[L], s0 = T.lstart[L];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b[9];
+        nch[t] = (uint32_t)child_bounds(T, (int32_t)(s0 + t), L, b);
+    }
+}
+
+__global__ void k_level_finish(TreeDev T, int L)
+{
+    if (blockIdx.x || threadIdx.x) return;
+    const int64_t next = T.lstart[L] + T.lcount[L];
+    T.lstart[L + 1] = next;
+    if (next + T.lcount[L + 1] > T.cap_nodes) {
+        tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+        T.lcount[L + 1] = 0;
+    }
+    *T.n_nodes = T.lstart[L + 1] + T.lcount[L + 1];
+}
+
+// a4 (write): children of level-L nodes at lstart[L+1] + scan offset, in
+// octant order; skip pointers make the breadth-first array walkable depth
+// first without a stack (next sibling, else the parent's skip).
+__global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint32_t *ofs)
+{
+    const int64_t nl = T.lcount[L], s0 = T.lstart[L];
+    const int64_t nnext = T.lcount[L + 1], base0 = T.lstart[L + 1];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(s0 + t);
+        if (nch[t] == 0 || nnext == 0) {
+            T.child[i] = -1;
+            T.nchild[i] = 0;
+            continue;
+        }
+        int32_t b[9];
+        const int k = child_bounds(T, i, L, b);
+        const int64_t base = base0 + ofs[t];
+        if (base + k > base0 + nnext) {   // truncated by an overflow
+            T.child[i] = -1;
+            T.nchild[i] = 0;
+            continue;
+        }
+        int j = 0;
+        for (int o = 0; o < 8; o++) {
+            if (b[o + 1] <= b[o]) continue;
+            const int32_t c = (int32_t)(base + j);
+            T.first[c] = b[o];
+            T.count[c] = b[o + 1] - b[o];
+            T.level[c] = (uint8_t)(L + 1);
+            T.parent[c] = i;
+            T.nbx[c] = T.nbx[i];
+            T.child[c] = -1;
+            T.nchild[c] = 0;
+            T.skip[c] = (j == k - 1) ? T.skip[i] : c + 1;
+            j++;
+        }
+        T.child[i] = (int32_t)base;
+        T.nchild[i] = k;
+    }
+}
+
+// a5: monopoles bottom-up in canonical order (leaf: particles in key order;
+// internal: children in octant order), tight boxes, fixed-point images and
+// the walk record.
+__global__ void k_moments(TreeDev T, int L)
+{
+    const int64_t nl = T.lcount[L], s0 = T.lstart[L];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(s0 + t);
+        double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
+        double lx = INFINITY, ly = INFINITY, lz = INFINITY;
+        double hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        const int32_t nc = T.nchild[i];
+        if (nc == 0) {
+            const int32_t f = T.first[i], e = f + T.count[i];
+            for (int32_t p = f; p < e; p++) {
+                const double mp = T.m[p], xp = T.x[p], yp = T.y[p], zp = T.z[p];
+                M = __dadd_rn(M, mp);
+                Sx = __dadd_rn(Sx, __dmul_rn(mp, xp));
+                Sy = __dadd_rn(Sy, __dmul_rn(mp, yp));
+                Sz = __dadd_rn(Sz, __dmul_rn(mp, zp));
+                lx = fmin(lx, xp); ly = fmin(ly, yp); lz = fmin(lz, zp);
+                hx = fmax(hx, xp); hy = fmax(hy, yp); hz = fmax(hz, zp);
+            }
+        } else {
+            const int32_t c0 = T.child[i];
+            for (int32_t c = c0; c < c0 + nc; c++) {
+                M = __dadd_rn(M, T.M[c]);
+                Sx = __dadd_rn(Sx, T.Sx[c]);
+                Sy = __dadd_rn(Sy, T.Sy[c]);
+                Sz = __dadd_rn(Sz, T.Sz[c]);
+                lx = fmin(lx, T.lox[c]); ly = fmin(ly, T.loy[c]); lz = fmin(lz, T.loz[c]);
+                hx = fmax(hx, T.hix[c]); hy = fmax(hy, T.hiy[c]); hz = fmax(hz, T.hiz[c]);
+            }
+        }
+        if (T.count[i] == 0) { lx = ly = lz = hx = hy = hz = 0.0; }
+        T.M[i] = M; T.Sx[i] = Sx; T.Sy[i] = Sy; T.Sz[i] = Sz;
+        T.lox[i] = lx; T.loy[i] = ly; T.loz[i] = lz;
+        T.hix[i] = hx; T.hiy[i] = hy; T.hiz[i] = hz;
+        const double cx = __dmul_rn(__dadd_rn(lx, hx), 0.5), cy = __dmul_rn(__dadd_rn(ly, hy), 0.5),
+                     cz = __dmul_rn(__dadd_rn(lz, hz), 0.5);
+        const double fx = __dmul_rn(__dsub_rn(hx, lx), 0.5), fy = __dmul_rn(__dsub_rn(hy, ly), 0.5),
+                     fz = __dmul_rn(__dsub_rn(hz, lz), 0.5);
+        T.cenx[i] = cx; T.ceny[i] = cy; T.cenz[i] = cz;
+        T.hfx[i] = fx; T.hfy[i] = fy; T.hfz[i] = fz;
+        const double mx = M > 0.0 ? __ddiv_rn(Sx, M) : cx;
+        const double my = M > 0.0 ? __ddiv_rn(Sy, M) : cy;
+        const double mz = M > 0.0 ? __ddiv_rn(Sz, M) : cz;
+        T.comx[i] = mx; T.comy[i] = my; T.comz[i] = mz;
+        T.cX[i] = tp_fixed64(mx); T.cY[i] = tp_fixed64(my); T.cZ[i] = tp_fixed64(mz);
+        WNode w;
+        w.cx = (uint32_t)(tp_fixed64(cx) >> 32);
+        w.cy = (uint32_t)(tp_fixed64(cy) >> 32);
+        w.cz = (uint32_t)(tp_fixed64(cz) >> 32);
+        w.hx = (uint32_t)(tp_fixed64(fx) >> 32);
+        w.hy = (uint32_t)(tp_fixed64(fy) >> 32);
+        w.hz = (uint32_t)(tp_fixed64(fz) >> 32);
+        w.child = nc ? T.child[i] : -1;
+        w.skip = T.skip[i];
+        w.first = T.first[i];
+        w.count = T.count[i];
+        w.level = L;
+        w.pad = 0;
+        T.wn[i] = w;
+    }
+}
+
+// a6: group starts.  Under every node holding more than n_crit particles each
+// maximal run of consecutive small children is cut into k = ceil(S/n_crit)
+// balanced groups; a big leaf is a group by itself; a small root is one group.
+__global__ void k_group_flags(TreeDev T, uint32_t *flag)
+{
+    const int64_t nn = *T.n_nodes;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)t;
+        const int32_t c = T.count[i];
+        const int32_t nc = T.box[T.nbx[i]].n_crit;
+        const bool leaf = T.nchild[i] == 0;
+        if (T.level[i] == 0 && c > 0 && (c <= nc || leaf)) flag[T.first[i]] = 1u;
+        if (c <= nc || leaf) continue;
+        const int32_t c0 = T.child[i], c1 = c0 + T.nchild[i];
+        int32_t run0 = c0;          // first child of the current run
+        for (int32_t k = c0; k <= c1; k++) {
+            const bool big = k < c1 && T.count[k] > nc;
+            if (k == c1 || big) {
+                // flush the run [run0, k)
+                int64_t S = 0;
+                for (int32_t r = run0; r < k; r++) S += T.count[r];
+                if (S > 0) {
+                    const int64_t kg = (S + nc - 1) / nc;
+                    const int64_t target = (S + kg - 1) / kg;
+                    int64_t cur = 0;
+                    for (int32_t r = run0; r < k; r++) {
+                        const int64_t cr = T.count[r];
+                        if (cur > 0 && (cur + cr > nc || cur >= target)) cur = 0;
+                        if (cur == 0) flag[T.first[r]] = 1u;
+                        cur += cr;
+                    }
+                }
+                if (big && T.nchild[k] == 0) flag[T.first[k]] = 1u;
+                run0 = k + 1;
+            }
+        }
+    }
+}
+
+__global__ void k_group_fill(TreeDev T, const uint32_t *flag, const uint32_t *gofs)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T.n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[p]) continue;
+        const uint32_t g = gofs[p];
+        if ((int64_t)g >= T.cap_groups) { tp_latch(T.status, TP_ERR_LIST_OVERFLOW); continue; }
+        T.gfirst[g] = (int32_t)p;
+        T.gbox[g] = tp_box_of(T.box_off, T.nbox, p);
+    }
+}
+
+// Group counts and tight boxes: one warp per group; min/max on the IEEE bit
+// patterns (positions are >= +0, where the bit order is the numeric order).
+__global__ void k_group_bbox(TreeDev T)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = w0; g < G; g += nw) {
+        const int32_t f = T.gfirst[g];
+        const int32_t e = (g + 1 < G) ? T.gfirst[g + 1] : (int32_t)T.n;
+        unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+        for (int32_t p = f + lane; p < e; p += 32) {
+            const unsigned long long a = __double_as_longlong(T.x[p]), b = __double_as_longlong(T.y[p]),
+                                     c = __double_as_longlong(T.z[p]);
+            lo[0] = min(lo[0], a); lo[1] = min(lo[1], b); lo[2] = min(lo[2], c);
+            hi[0] = max(hi[0], a); hi[1] = max(hi[1], b); hi[2] = max(hi[2], c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane == 0) {
+            T.gcount[g] = e - f;
+            double c[3], h[3];
+            for (int k = 0; k < 3; k++) {
+                const double l = __longlong_as_double(lo[k]), u = __longlong_as_double(hi[k]);
+                c[k] = __dmul_rn(__dadd_rn(l, u), 0.5);
+                h[k] = __dmul_rn(__dsub_rn(u, l), 0.5);
+            }
+            T.gcx[g] = c[0]; T.gcy[g] = c[1]; T.gcz[g] = c[2];
+            T.ghx[g] = h[0]; T.ghy[g] = h[1]; T.ghz[g] = h[2];
+            const uint64_t X = tp_fixed64(c[0]), Y = tp_fixed64(c[1]), Z = tp_fixed64(c[2]);
+            T.gX[g] = X; T.gY[g] = Y; T.gZ[g] = Z;
+            T.gux[g] = (uint32_t)(X >> 32); T.guy[g] = (uint32_t)(Y >> 32); T.guz[g] = (uint32_t)(Z >> 32);
+            T.ghux[g] = (uint32_t)(tp_fixed64(h[0]) >> 32);
+            T.ghuy[g] = (uint32_t)(tp_fixed64(h[1]) >> 32);
+            T.ghuz[g] = (uint32_t)(tp_fixed64(h[2]) >> 32);
+        }
+    }
+}
+
+}  // namespace
+
+namespace tp {
+
+void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, uint64_t *key2,
+                            uint32_t *perm2, void *radix_tmp, cudaStream_t s)
+{
+    if (T.n == 0) return;
+    TP_LAUNCH(k_keys, grid_for(T.n, kBlock), kBlock, 0, s, pos, T.n, T.key, T.perm, T.status);
+    radix_sort(T.key, T.perm, key2, perm2, T.n, 63, T.box_off, T.nbox, radix_tmp, s);
+    TP_LAUNCH(k_gather, grid_for(T.n, kBlock), kBlock, 0, s, pos, mass, T);
+}
+
+// Topology and monopoles.  nch/ofs: scratch of cap_nodes u32 each.
+void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, void *scan_tmp, cudaStream_t s)
+{
+    TP_LAUNCH(k_init_roots, (T.nbox + 127) / 128, 128, 0, s, T);
+    for (int L = 0; L < TP_MAX_LEVEL; L++) {
+        TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch);
+        scan_u32(nch, ofs, 0, T.lcount + L, T.lcount + L + 1, scan_tmp, s);
+        TP_LAUNCH(k_level_finish, 1, 32, 0, s, T, L);
+        TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs);
+    }
+    for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_moments, kLevelGrid, kBlock, 0, s, T, L);
+}
+
+// Group starts and their count (into *T.n_groups).  flag/gofs: [n] u32.
+void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_tmp, cudaStream_t s)
+{
+    if (T.n == 0) {
+        cudaMemsetAsync(T.n_groups, 0, sizeof(int64_t), s);
+        return;
+    }
+    cudaMemsetAsync(flag, 0, sizeof(uint32_t) * (size_t)T.n, s);
+    TP_LAUNCH(k_group_flags, kLevelGrid, kBlock, 0, s, T, flag);
+    scan_u32(flag, gofs, T.n, nullptr, T.n_groups, scan_tmp, s);
+}
+
+void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s)
+{
+    if (T.n == 0) return;
+    TP_LAUNCH(k_group_fill, grid_for(T.n, kBlock), kBlock, 0, s, T, flag, gofs);
+    TP_LAUNCH(k_group_bbox, kLevelGrid, kBlock, 0, s, T);
+}
+
+}  // namespace tp

@@ -1,0 +1,441 @@
+// tp_pair.cu -- the particle-particle force loop (Sec. II-A; "force
+// calculation" in Table I) and its adjoint.
+//
+// Work unit: one group and its interaction list.  A CTA stages list entries as
+// group-relative offsets in shared memory (tiles of kTile) and each thread
+// keeps one i-particle in registers; when the group is smaller than the CTA,
+// several threads hold the same i and split the list between them ("streams"),
+// and their partial sums are reduced at the end in a fixed order.
+//
+// Group-relative offsets come from the 64-bit fixed-point images: the
+// wrap-around integer difference of two images is the exact periodic minimum
+// image offset, so the only rounding is the final conversion to the working
+// precision.  Offsets are scaled by k = 2/r_cut, so the cutoff argument of
+// Eq. 3 is xi = |d'| and the cutoff test is |d'|^2 < 4; the sum is multiplied
+// by G k^2 once per particle.
+#include "tp_common.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTile = 256;
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <class R> struct Arith;
+
+template <> struct Arith<float> {
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrt_approx(x); }
+    static __device__ __forceinline__ float from_fixed(uint64_t a, uint64_t b, float sc)
+    {
+        return __ll2float_rn((long long)(a - b)) * sc;
+    }
+};
+
+template <> struct Arith<double> {
+    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double from_fixed(uint64_t a, uint64_t b, double sc)
+    {
+        return __ll2double_rn((long long)(a - b)) * sc;
+    }
+};
+
+// Eq. 3 in the nested form with the zeta branch folded in: xi = |d'|,
+// r2 = xi^2.  g = 1 + xi^3 (-8/5 + xi^2 (8/5 + xi (-1/2 + xi (-12/35 +
+// xi 3/20)))) - zeta^6 (3/35 + xi (18/35 + xi/5)), zeta = max(0, xi - 1).
+template <class R>
+__device__ __forceinline__ R g_p3m(R xi, R r2, R &z2)
+{
+    R p = R(3.0 / 20.0) * xi + R(-12.0 / 35.0);
+    p = p * xi + R(-0.5);
+    p = p * xi + R(8.0 / 5.0);
+    p = p * r2 + R(-8.0 / 5.0);
+    R g = p * (r2 * xi) + R(1.0);
+    R zeta = xi - R(1.0);
+    zeta = zeta > R(0) ? zeta : R(0);
+    z2 = zeta * zeta;
+    R q = R(1.0 / 5.0) * xi + R(18.0 / 35.0);
+    q = q * xi + R(3.0 / 35.0);
+    return g - (z2 * z2 * z2) * q;
+}
+
+// g'(xi)/xi from Eq. 3: -24/5 xi + 8 xi^3 - 3 xi^4 - 12/5 xi^5 + 6/5 xi^6
+// minus zeta^5 (8/5)(xi + 2) above xi = 1.
+template <class R>
+__device__ __forceinline__ R gpx_p3m(R xi, R r2, R z2)
+{
+    R p = R(6.0 / 5.0) * xi + R(-12.0 / 5.0);
+    p = p * xi + R(-3.0);
+    p = p * xi + R(8.0);
+    p = p * r2 + R(-24.0 / 5.0);
+    const R lo = p * xi;
+    const R zeta = xi - R(1.0) > R(0) ? xi - R(1.0) : R(0);
+    const R z5 = z2 * z2 * zeta;
+    return lo - z5 * (R(8.0 / 5.0) * xi + R(16.0 / 5.0));
+}
+
+struct Group {
+    int32_t first, ni;
+    int64_t e0;
+    int32_t ne;
+    uint64_t X, Y, Z;
+    const BoxPrm *P;
+};
+
+__device__ __forceinline__ Group load_group(const TreeDev &T, int64_t g)
+{
+    Group G;
+    G.first = T.gfirst[g];
+    G.ni = T.gcount[g];
+    G.e0 = T.loff[g];
+    G.ne = T.lcnt[g];
+    G.X = T.gX[g]; G.Y = T.gY[g]; G.Z = T.gZ[g];
+    G.P = &T.box[T.gbox[g]];
+    return G;
+}
+
+template <class R>
+__device__ __forceinline__ void stage_entry(const TreeDev &T, const Group &G, int32_t e, R sc, R *sx,
+                                            R *sy, R *sz, R *sm, int q)
+{
+    uint64_t ex, ey, ez;
+    double mj;
+    if (e >= 0) {
+        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = T.m[e];
+    } else {
+        const int32_t nd = -e - 1;
+        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = T.M[nd];
+    }
+    sx[q] = Arith<R>::from_fixed(ex, G.X, sc);
+    sy[q] = Arith<R>::from_fixed(ey, G.Y, sc);
+    sz[q] = Arith<R>::from_fixed(ez, G.Z, sc);
+    sm[q] = (R)mj;
+}
+
+template <class R>
+__device__ __forceinline__ R scale_of(const BoxPrm &P);
+template <> __device__ __forceinline__ float scale_of<float>(const BoxPrm &P) { return P.scale; }
+template <> __device__ __forceinline__ double scale_of<double>(const BoxPrm &P)
+{
+    return P.scale_d * (2.0 / P.rcut);
+}
+template <class R>
+__device__ __forceinline__ R eps2_of(const BoxPrm &P);
+template <> __device__ __forceinline__ float eps2_of<float>(const BoxPrm &P) { return P.eps2s; }
+template <> __device__ __forceinline__ double eps2_of<double>(const BoxPrm &P)
+{
+    const double k = 2.0 / P.rcut;
+    return (k * P.eps) * (k * P.eps);
+}
+
+// Next work item: a persistent queue (atomic counter over an LPT order) or a
+// plain grid-stride over groups.
+template <bool QUEUE>
+__device__ __forceinline__ int64_t next_item(int32_t *queue, int64_t cur, int *s_item)
+{
+    if (!QUEUE) return cur < 0 ? (int64_t)blockIdx.x : cur + gridDim.x;
+    if (threadIdx.x == 0) *s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int64_t it = *s_item;
+    __syncthreads();
+    return it;
+}
+
+// ---------------------------------------------------------------------------
+// Forward: a_i = G k^2 sum_j m_j d' g(|d'|) / (|d'|^2 + (k eps)^2)^{3/2}.
+// ---------------------------------------------------------------------------
+template <class R, bool QUEUE>
+__global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *queue,
+                                                   const int32_t *order)
+{
+    __shared__ R sx[kTile], sy[kTile], sz[kTile], sm[kTile];
+    __shared__ R red[3][kThreads];
+    __shared__ int s_item;
+    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
+    for (int64_t item = next_item<QUEUE>(queue, -1, &s_item); item < G_n;
+         item = next_item<QUEUE>(queue, item, &s_item)) {
+        const int64_t g = order ? order[item] : item;
+        const Group G = load_group(T, g);
+        const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
+        const R gk2 = (R)G.P->gk2;
+        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
+            const int nic = min(kThreads, G.ni - i0);
+            const int ns = kThreads / nic;
+            const int slot = threadIdx.x;
+            const bool active = slot < nic * ns;
+            const int il = active ? slot % nic : 0, st = active ? slot / nic : 0;
+            const int32_t p = G.first + i0 + il;
+            const R xi = Arith<R>::from_fixed(T.X[p], G.X, sc);
+            const R yi = Arith<R>::from_fixed(T.Y[p], G.Y, sc);
+            const R zi = Arith<R>::from_fixed(T.Z[p], G.Z, sc);
+            R ax = 0, ay = 0, az = 0;
+            const int ne = bad ? 0 : G.ne;
+            for (int t0 = 0; t0 < ne; t0 += kTile) {
+                const int nt = min(kTile, ne - t0);
+                __syncthreads();
+                for (int q = threadIdx.x; q < nt; q += kThreads)
+                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, sx, sy, sz, sm, q);
+                __syncthreads();
+                if (active) {
+                    for (int j = st; j < nt; j += ns) {
+                        const R dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
+                        const R r2 = dx * dx + dy * dy + dz * dz;
+                        const R ri = Arith<R>::rsqrt(r2 + eps2);
+                        const R x = Arith<R>::sqrt(r2);
+                        R z2;
+                        const R g = g_p3m<R>(x, r2, z2);
+                        R f = sm[j] * g * (ri * ri * ri);
+                        f = (r2 < R(4) && r2 > R(0)) ? f : R(0);
+                        ax += f * dx;
+                        ay += f * dy;
+                        az += f * dz;
+                    }
+                }
+            }
+            red[0][slot] = ax; red[1][slot] = ay; red[2][slot] = az;
+            __syncthreads();
+            if (slot < nic) {
+                R sxx = 0, syy = 0, szz = 0;
+                for (int s = 0; s < ns; s++) {
+                    sxx += red[0][s * nic + slot];
+                    syy += red[1][s * nic + slot];
+                    szz += red[2][s * nic + slot];
+                }
+                const int64_t o = T.perm[G.first + i0 + slot];
+                acc[3 * o] = sxx * gk2;
+                acc[3 * o + 1] = syy * gk2;
+                acc[3 * o + 2] = szz * gk2;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint.  With f(d') = d' phi, phi = g(xi)/s'^3, s'^2 = xi^2 + (k eps)^2:
+//   J' = phi I + psi d' d'^T,  psi = (g'/xi)/s'^3 - 3 g/s'^5,
+//   v  = m_j J' w_i = alpha w_i + beta d',  alpha = m_j phi, beta = m_j psi (d'.w_i)
+// and dL/dx_i -= G k^3 v, dL/dx_j += G k^3 v (a node passes its share to its
+// centre-of-mass cotangent).  The i side accumulates A = sum alpha and
+// B = sum beta d' in registers; the j side needs the sum over the group's i for
+// each entry, so every warp holds one stream (32 distinct i) and reduces with
+// shuffles before one shared-memory add per warp and entry.
+// ---------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, double *gs, double *ncot,
+                                                  int32_t *queue, const int32_t *order)
+{
+    __shared__ R sx[kTile], sy[kTile], sz[kTile], sm[kTile];
+    __shared__ R jx[kTile], jy[kTile], jz[kTile];
+    __shared__ int s_item;
+    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
+         item = next_item<true>(queue, item, &s_item)) {
+        const int64_t g = order ? order[item] : item;
+        const Group G = load_group(T, g);
+        const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
+        const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
+        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
+            const int nic = min(kThreads, G.ni - i0);
+            const int nwi = (nic + 31) >> 5;                 // warps per stream
+            const int ns = (kThreads >> 5) / nwi;            // streams
+            const bool wactive = warp < nwi * ns;
+            const int st = wactive ? warp / nwi : 0;
+            const int il = (warp % nwi) * 32 + lane;
+            const bool active = wactive && il < nic;
+            const int32_t p = G.first + i0 + (active ? il : 0);
+            const R xi = Arith<R>::from_fixed(T.X[p], G.X, sc);
+            const R yi = Arith<R>::from_fixed(T.Y[p], G.Y, sc);
+            const R zi = Arith<R>::from_fixed(T.Z[p], G.Z, sc);
+            const int64_t o = T.perm[p];
+            const R wx = active ? cot[3 * o] : R(0), wy = active ? cot[3 * o + 1] : R(0),
+                    wz = active ? cot[3 * o + 2] : R(0);
+            R A = 0, Bx = 0, By = 0, Bz = 0;
+            const int ne = bad ? 0 : G.ne;
+            for (int t0 = 0; t0 < ne; t0 += kTile) {
+                const int nt = min(kTile, ne - t0);
+                __syncthreads();
+                for (int q = threadIdx.x; q < nt; q += kThreads) {
+                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, sx, sy, sz, sm, q);
+                    jx[q] = 0; jy[q] = 0; jz[q] = 0;
+                }
+                __syncthreads();
+                if (wactive) {
+                    for (int j = st; j < nt; j += ns) {
+                        const R dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
+                        const R r2 = dx * dx + dy * dy + dz * dz;
+                        const R ri = Arith<R>::rsqrt(r2 + eps2);
+                        const R x = Arith<R>::sqrt(r2);
+                        R z2;
+                        const R gv = g_p3m<R>(x, r2, z2);
+                        const R gp = gpx_p3m<R>(x, r2, z2);
+                        const R ri2 = ri * ri, ri3 = ri2 * ri;
+                        const R phi = gv * ri3;
+                        const R psi = gp * ri3 - R(3) * phi * ri2;
+                        const bool in = active && r2 < R(4) && r2 > R(0);
+                        const R alpha = in ? sm[j] * phi : R(0);
+                        const R beta = in ? sm[j] * psi * (dx * wx + dy * wy + dz * wz) : R(0);
+                        A += alpha;
+                        Bx += beta * dx; By += beta * dy; Bz += beta * dz;
+                        R vx = alpha * wx + beta * dx, vy = alpha * wy + beta * dy, vz = alpha * wz + beta * dz;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            vx += __shfl_xor_sync(0xffffffffu, vx, off);
+                            vy += __shfl_xor_sync(0xffffffffu, vy, off);
+                            vz += __shfl_xor_sync(0xffffffffu, vz, off);
+                        }
+                        if (lane == 0) {
+                            if (nwi == 1) { jx[j] = vx; jy[j] = vy; jz[j] = vz; }
+                            else { atomicAdd(&jx[j], vx); atomicAdd(&jy[j], vy); atomicAdd(&jz[j], vz); }
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int q = threadIdx.x; q < nt; q += kThreads) {
+                    const int32_t e = T.ent[G.e0 + t0 + q];
+                    double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
+                    atomicAdd(dst, gk3 * (double)jx[q]);
+                    atomicAdd(dst + 1, gk3 * (double)jy[q]);
+                    atomicAdd(dst + 2, gk3 * (double)jz[q]);
+                }
+            }
+            if (active) {
+                // i side: dL/dx_i -= G k^3 (A w_i + B); streams meet in global atomics
+                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (double)(A * wx + Bx));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (double)(A * wy + By));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (double)(A * wz + Bz));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Node cotangents reach member particles through the centre of mass: for each
+// leaf, P = sum over the path root..leaf of c_a / M_a (summed from the root
+// down); grad_p += m_p P.  Then key order -> input order.
+__global__ void k_pushdown(TreeDev T, double *gs, const double *ncot)
+{
+    const int64_t nn = *T.n_nodes;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)t;
+        if (T.nchild[i] != 0 || T.count[i] == 0) continue;
+        int32_t path[TP_NLEVELS + 1];
+        int d = 0;
+        for (int32_t a = i; a >= 0 && d <= TP_NLEVELS; a = T.parent[a]) path[d++] = a;
+        double Px = 0.0, Py = 0.0, Pz = 0.0;
+        for (int k = d - 1; k >= 0; k--) {
+            const int32_t a = path[k];
+            const double M = T.M[a];
+            if (M > 0.0) {
+                Px += ncot[3 * (int64_t)a] / M;
+                Py += ncot[3 * (int64_t)a + 1] / M;
+                Pz += ncot[3 * (int64_t)a + 2] / M;
+            }
+        }
+        for (int32_t p = T.first[i]; p < T.first[i] + T.count[i]; p++) {
+            const double mp = T.m[p];
+            gs[3 * (int64_t)p] += mp * Px;
+            gs[3 * (int64_t)p + 1] += mp * Py;
+            gs[3 * (int64_t)p + 2] += mp * Pz;
+        }
+    }
+}
+
+__global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < T.n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = T.perm[s];
+        grad[3 * o] = gs[3 * s];
+        grad[3 * o + 1] = gs[3 * s + 1];
+        grad[3 * o + 2] = gs[3 * s + 2];
+    }
+}
+
+template <class R>
+int pair_blocks_per_sm()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<R, true>, kThreads, 0);
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace
+
+namespace tp {
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
+                      cudaStream_t s)
+{
+    if (G <= 0) return;
+    cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    static int bps = pair_blocks_per_sm<float>();
+    int64_t grid = (int64_t)num_sms() * bps;
+    if (grid > G) grid = G;
+    auto k = k_pair<float, true>;
+    TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, queue, order);
+}
+
+void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s)
+{
+    if (G <= 0) return;
+    int64_t grid = G < (1ll << 30) ? G : (1ll << 30);
+    auto k = k_pair<double, false>;
+    TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, nullptr, nullptr);
+}
+
+template <class R>
+static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double *ncot,
+                     int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
+{
+    cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)T.n, s);
+    cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
+    if (G > 0) {
+        cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
+        int64_t grid = (int64_t)num_sms() * (nb > 0 ? nb : 1);
+        if (grid > G) grid = G;
+        auto k = k_vjp<R>;
+        TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, cot, gs, ncot, queue, order);
+    }
+    TP_LAUNCH(k_pushdown, 152 * 4, 256, 0, s, T, gs, ncot);
+    TP_LAUNCH(k_unsort3, grid_for(T.n, 256), 256, 0, s, T, gs, grad);
+}
+
+void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
+             const int32_t *order, int64_t G, cudaStream_t s)
+{
+    vjp_impl<float>(T, cot, grad, gs, ncot, queue, order, G, s);
+}
+
+void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
+             const int32_t *order, int64_t G, cudaStream_t s)
+{
+    vjp_impl<double>(T, cot, grad, gs, ncot, queue, order, G, s);
+}
+
+}  // namespace tp

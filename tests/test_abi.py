@@ -1,0 +1,57 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+function include/treepm_sr.h declares (no compute calls are made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "treepm_sr.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tp_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1211_4406_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["tp_build_tree", "tp_short_range_force", "tp_short_range_vjp",
+                     "tp_build_tree_batched", "tp_tree_free", "tp_tree_status"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1211_4406_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_status_strings_without_gpu(lib):
+    lib.tp_status_string.restype = ctypes.c_char_p
+    assert lib.tp_status_string(0) == b"ok"
+    assert lib.tp_status_string(-4) == b"capacity overflow"
+
+
+def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
+    from paper_1211_4406_gb300 import _lib
+    _lib.load()
+    h = ctypes.c_void_p()
+    p = _lib.params(r_cut=0.7)                                     # r_cut must be < 1/2
+    assert _lib.load().tp_build_tree(None, None, 10, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    p = _lib.params(r_cut=0.1)
+    assert _lib.load().tp_build_tree(None, None, -1, ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert _lib.load().tp_tree_free(None) == 0

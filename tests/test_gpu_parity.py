@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Bit-exact: Morton keys, permutation, octree nodes (topology, FP64 monopoles
+and boxes), groups and interaction lists.  Within tolerance (written below):
+forces on identical lists (FP32 rms <= 1e-6 and max <= 1e-4 relative; FP64
+rms <= 1e-12), the adjoint, and theta = 0.5 forces against the direct sum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1211_4406_gb300 import inputs
+from paper_1211_4406_gb300.api import Params, ShortRangeTree
+
+pytestmark = pytest.mark.gpu
+
+FP32_RMS, FP32_MAX = 1e-6, 1e-4       # FP32 vs FP64 on identical lists
+FP64_RMS = 1e-12
+TREE_RMS = 5e-3                       # theta = 0.5 vs the direct sum
+
+
+def rel_err(a, ref):
+    nr = np.linalg.norm(ref, axis=1)
+    den = np.maximum(nr, 1e-6 * np.median(nr)) if nr.size else nr
+    e = np.linalg.norm(a - ref, axis=1) / den
+    return (float(np.sqrt(np.mean(e ** 2))) if e.size else 0.0), (float(e.max()) if e.size else 0.0)
+
+
+def gpu_tree(box, precision="fp32", theta=None, n_crit=None, n_leaf=None):
+    pos = torch.tensor(box.pos, device="cuda")
+    mass = torch.tensor(box.mass, device="cuda")
+    p = Params(box.G, box.eps, box.r_cut, box.theta if theta is None else theta,
+               n_crit or box.n_crit, n_leaf or box.n_leaf, precision)
+    return ShortRangeTree(pos, mass, p)
+
+
+def oracle_tree(box, theta=None, n_crit=None, n_leaf=None):
+    t = oracle.OracleTree(box.pos, box.mass, n_leaf or box.n_leaf, n_crit or box.n_crit)
+    t.lists(box.r_cut, box.theta if theta is None else theta)
+    return t
+
+
+def assert_structure_equal(gt, ot):
+    keys, perm = gt.export_keys()
+    ex = ot.export()
+    assert np.array_equal(keys, ex.keys)
+    assert np.array_equal(perm, ex.perm)
+    ints, dbl = gt.export_nodes()
+    assert ints.shape[0] == ex.level.size
+    oints = np.stack([ex.level, ex.first, ex.count, ex.child, ex.nchild, ex.parent], axis=1)
+    assert np.array_equal(ints[:, :6], oints)
+    odbl = np.concatenate([ex.M[:, None], ex.com, ex.lo, ex.hi, ex.cen, ex.half], axis=1)
+    assert np.array_equal(dbl, odbl)                       # bit-exact FP64 monopoles and boxes
+    gi, gd = gt.export_groups()
+    assert np.array_equal(gi[:, 0], ex.gfirst) and np.array_equal(gi[:, 1], ex.gcount)
+    assert np.array_equal(gd, np.concatenate([ex.gcen, ex.ghalf], axis=1))
+    off, ent = gt.export_lists()
+    assert np.array_equal(off, ex.loff)
+    assert np.array_equal(ent.astype(np.int64), ex.ent)
+    return ex
+
+
+def small_boxes():
+    out = []
+    for n in [1, 2, 3, 7, 64, 65, 300, 4096]:
+        pos, mass = inputs.uniform_box(n, 500 + n)
+        out.append(inputs.Box(f"uniform{n}", pos, mass * np.linspace(0.5, 1.5, n), 1.0, 2e-3, 0.2, 0.5))
+    pos = np.tile([[0.3, 0.6, 0.9]], (100, 1))
+    out.append(inputs.Box("coincident", pos, np.full(100, 0.01), 1.0, 1e-3, 0.1, 0.5))
+    pos, mass = inputs.uniform_box(500, 7)
+    pos[:, 0] = np.where(pos[:, 0] < 0.5, pos[:, 0] * 0.01, 1 - pos[:, 0] * 0.01)   # hugs x = 0 = 1
+    out.append(inputs.Box("wrap", pos, mass, 1.0, 1e-3, 0.15, 0.5))
+    pos, mass = inputs.clustered_box(6000, 30, 77)
+    out.append(inputs.Box("clustered6k", pos, mass, 1.3, 5e-4, 0.08, 0.5, n_crit=32, n_leaf=4))
+    return out
+
+
+@pytest.mark.parametrize("box", small_boxes(), ids=lambda b: b.name)
+def test_structure_bit_exact_small(box):
+    gt = gpu_tree(box)
+    ot = oracle_tree(box)
+    assert_structure_equal(gt, ot)
+    gt.close()
+
+
+@pytest.mark.parametrize("box", small_boxes(), ids=lambda b: b.name)
+def test_forces_on_identical_lists_small(box):
+    ot = oracle_tree(box)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    g32 = gpu_tree(box, "fp32")
+    a32 = g32.force().double().cpu().numpy()
+    g64 = gpu_tree(box, "fp64")
+    a64 = g64.force().cpu().numpy()
+    if box.n > 1 and np.abs(ref).max() > 0:
+        rms32, max32 = rel_err(a32, ref)
+        rms64, _ = rel_err(a64, ref)
+        assert rms32 <= FP32_RMS and max32 <= FP32_MAX, (rms32, max32)
+        assert rms64 <= FP64_RMS, rms64
+    else:
+        assert np.all(a32 == 0) and np.all(a64 == 0)
+
+
+def test_uniform_32k_structure_and_forces():
+    box = inputs.config_box(1)
+    gt = gpu_tree(box)
+    ot = oracle_tree(box)
+    assert_structure_equal(gt, ot)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    rms, mx = rel_err(gt.force().double().cpu().numpy(), ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+    brute = oracle.brute_force(box.pos, box.mass, box.G, box.eps, box.r_cut)
+    rms_t, _ = rel_err(gt.force().double().cpu().numpy(), brute)
+    assert rms_t <= TREE_RMS
+    g64 = gpu_tree(box, "fp64")
+    assert rel_err(g64.force().cpu().numpy(), ref)[0] <= FP64_RMS
+
+
+def test_clustered_262k_structure_forces_and_tree_accuracy():
+    box = inputs.config_box(4)
+    gt = gpu_tree(box)
+    ot = oracle_tree(box)
+    assert_structure_equal(gt, ot)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    a = gt.force().double().cpu().numpy()
+    rms, mx = rel_err(a, ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+    idx = np.random.default_rng(1).choice(box.n, 2000, replace=False)
+    brute = oracle.brute_force_sample(box.pos, box.mass, box.G, box.eps, box.r_cut, idx)
+    assert rel_err(a[idx], brute)[0] <= TREE_RMS
+
+
+@pytest.mark.slow
+def test_clustered_2M_full_size():
+    """The benchmark workload at full size: bit-exact keys and lists, FP32
+    forces against the oracle's FP64 forces on identical lists."""
+    box = inputs.config_box(2)
+    gt = gpu_tree(box)
+    ot = oracle_tree(box)
+    assert_structure_equal(gt, ot)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    rms, mx = rel_err(gt.force().double().cpu().numpy(), ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+
+
+def test_vjp_against_oracle_adjoint():
+    box = inputs.config_box(4, n_override=32768)
+    w = inputs.cotangent(box.n, box.seed + 7)
+    ot = oracle_tree(box)
+    ref = ot.list_vjp(box.G, box.eps, box.r_cut, w.astype(np.float64))
+    for prec in ["fp32", "fp64"]:
+        gt = gpu_tree(box, prec)
+        cot = torch.tensor(w, device="cuda")
+        g = gt.vjp(cot).cpu().numpy()
+        scale = max(np.sqrt(np.mean(ref ** 2)), 1e-300)
+        tol = 1e-4 if prec == "fp32" else 1e-10
+        bad = np.abs(g - ref) > tol * np.maximum(np.abs(ref), scale)
+        assert not bad.any(), (prec, int(bad.sum()), float(np.abs(g - ref).max() / scale))
+
+
+def test_batched_boxes_match_per_box_oracle():
+    boxes = inputs.batched_boxes(8, scale=0.2)
+    pos = torch.tensor(np.concatenate([b.pos for b in boxes]), device="cuda")
+    mass = torch.tensor(np.concatenate([b.mass for b in boxes]), device="cuda")
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
+    prm = [Params(b.G, b.eps, b.r_cut, b.theta, b.n_crit, b.n_leaf, "fp32") for b in boxes]
+    gt = ShortRangeTree(pos, mass, prm, box_offsets=offs.tolist())
+    acc = gt.force().double().cpu().numpy()
+    for k, b in enumerate(boxes):
+        ref = oracle_tree(b).list_forces(b.G, b.eps, b.r_cut)
+        rms, mx = rel_err(acc[offs[k]:offs[k + 1]], ref)
+        assert rms <= FP32_RMS and mx <= FP32_MAX, (k, rms, mx)
+
+
+def test_empty_and_errors():
+    from paper_1211_4406_gb300._lib import TreeSRError
+    t = ShortRangeTree(torch.zeros((0, 3), dtype=torch.float64, device="cuda"), None, Params(r_cut=0.1))
+    assert t.force().shape == (0, 3)
+    assert t.stats()["n_groups"] == 0
+    t.close()
+    pos = torch.rand((100, 3), dtype=torch.float64, device="cuda")
+    pos[17, 1] = float("nan")
+    with pytest.raises(TreeSRError) as e:
+        ShortRangeTree(pos, None, Params(r_cut=0.1))
+    assert e.value.code == -6
+    with pytest.raises(TreeSRError):
+        ShortRangeTree(torch.rand((10, 3), dtype=torch.float64, device="cuda"), None, Params(r_cut=0.6))
+
+
+def test_eps_zero_and_coincident_pairs_are_finite():
+    pos = np.random.default_rng(3).random((2000, 3))
+    pos[1000:1010] = pos[5]
+    box = inputs.Box("eps0", pos, np.full(2000, 1 / 2000), 1.0, 0.0, 0.1, 0.5)
+    a = gpu_tree(box).force().double().cpu().numpy()
+    assert np.all(np.isfinite(a))
+    ref = oracle_tree(box).list_forces(box.G, box.eps, box.r_cut)
+    rms, mx = rel_err(a, ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX

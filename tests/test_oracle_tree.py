@@ -291,3 +291,19 @@ def test_list_vjp_matches_frozen_central_differences():
         t.refresh(pos)
         assert abs(vals[0] - vals[1]) <= 1e-6 * max(abs(vals[0]), rms)   # converged
         assert abs(grad[k, c] - vals[0]) <= 1e-5 * max(abs(vals[0]), rms)
+
+
+def test_group_ranges_partition_the_sums():
+    pos, mass = inputs.clustered_box(3000, 15, 41)
+    G, eps, rc = 1.0, 1e-3, 0.07
+    w = inputs.cotangent(3000, 42).astype(np.float64)
+    t, _ = build(pos, mass)
+    t.lists(rc, 0.5)
+    ng = t.sizes()[2]
+    cut = ng // 3
+    full = t.list_forces(G, eps, rc)
+    parts = t.list_forces_range(0, cut, G, eps, rc) + t.list_forces_range(cut, ng, G, eps, rc)
+    assert np.array_equal(full, parts)
+    gfull = t.list_vjp(G, eps, rc, w)
+    gparts = t.list_vjp_range(0, cut, G, eps, rc, w) + t.list_vjp_range(cut, ng, G, eps, rc, w)
+    assert np.allclose(gfull, gparts, rtol=1e-12, atol=1e-12 * np.abs(gfull).max())
