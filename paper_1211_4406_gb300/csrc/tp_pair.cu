@@ -47,38 +47,46 @@ template <> struct Arith<double> {
     }
 };
 
-// Eq. 3 in the nested form with the zeta branch folded in: xi = |d'|,
-// r2 = xi^2.  g = 1 + xi^3 (-8/5 + xi^2 (8/5 + xi (-1/2 + xi (-12/35 +
-// xi 3/20)))) - zeta^6 (3/35 + xi (18/35 + xi/5)), zeta = max(0, xi - 1).
+// Eq. 3 evaluated branch by branch.  The paper's branch-free nested form
+// (with the zeta = max(0, xi - 1) correction) is exact in FP64, but in FP32 its
+// O(1) terms cancel to O(1e-6) near xi = 2 (20 % relative error at xi = 1.9).
+// Here the interval [0,1] uses the expanded polynomial of Eq. 3 and [1,2] the
+// same polynomial factored as (2 - xi)^5 (7 xi^3 + 22 xi^2 + 10 xi + 4) / 140,
+// whose relative error stays at a few FP32 ulps all the way to the cutoff; the
+// two are selected per pair (both are evaluated, no divergence).
 template <class R>
-__device__ __forceinline__ R g_p3m(R xi, R r2, R &z2)
+__device__ __forceinline__ R g_p3m(R xi, R r2)
 {
     R p = R(3.0 / 20.0) * xi + R(-12.0 / 35.0);
     p = p * xi + R(-0.5);
     p = p * xi + R(8.0 / 5.0);
     p = p * r2 + R(-8.0 / 5.0);
-    R g = p * (r2 * xi) + R(1.0);
-    R zeta = xi - R(1.0);
-    zeta = zeta > R(0) ? zeta : R(0);
-    z2 = zeta * zeta;
-    R q = R(1.0 / 5.0) * xi + R(18.0 / 35.0);
-    q = q * xi + R(3.0 / 35.0);
-    return g - (z2 * z2 * z2) * q;
+    const R lo = p * (r2 * xi) + R(1.0);
+    const R u = R(2.0) - xi;
+    R h = R(7.0 / 140.0) * xi + R(22.0 / 140.0);
+    h = h * xi + R(10.0 / 140.0);
+    h = h * xi + R(4.0 / 140.0);
+    const R u2 = u * u;
+    const R hi = (u2 * u2 * u) * h;
+    return xi <= R(1.0) ? lo : hi;
 }
 
-// g'(xi)/xi from Eq. 3: -24/5 xi + 8 xi^3 - 3 xi^4 - 12/5 xi^5 + 6/5 xi^6
-// minus zeta^5 (8/5)(xi + 2) above xi = 1.
+// g'(xi)/xi of Eq. 3, branch by branch: -24/5 xi + 8 xi^3 - 3 xi^4 - 12/5 xi^5
+// + 6/5 xi^6 on [0,1]; -(2 - xi)^4 (2 xi^2 + 4 xi - 1) / 5 on [1,2].
 template <class R>
-__device__ __forceinline__ R gpx_p3m(R xi, R r2, R z2)
+__device__ __forceinline__ R gpx_p3m(R xi, R r2)
 {
     R p = R(6.0 / 5.0) * xi + R(-12.0 / 5.0);
     p = p * xi + R(-3.0);
     p = p * xi + R(8.0);
     p = p * r2 + R(-24.0 / 5.0);
     const R lo = p * xi;
-    const R zeta = xi - R(1.0) > R(0) ? xi - R(1.0) : R(0);
-    const R z5 = z2 * z2 * zeta;
-    return lo - z5 * (R(8.0 / 5.0) * xi + R(16.0 / 5.0));
+    const R u = R(2.0) - xi;
+    const R u2 = u * u;
+    R q = R(-2.0 / 5.0) * xi + R(-4.0 / 5.0);
+    q = q * xi + R(1.0 / 5.0);
+    const R hi = (u2 * u2) * q;
+    return xi <= R(1.0) ? lo : hi;
 }
 
 struct Group {
@@ -87,6 +95,7 @@ struct Group {
     int32_t ne;
     uint64_t X, Y, Z;
     const BoxPrm *P;
+    bool wrap;   // offsets of i and j may differ by more than half a box
 };
 
 __device__ __forceinline__ Group load_group(const TreeDev &T, int64_t g)
@@ -98,12 +107,30 @@ __device__ __forceinline__ Group load_group(const TreeDev &T, int64_t g)
     G.ne = T.lcnt[g];
     G.X = T.gX[g]; G.Y = T.gY[g]; G.Z = T.gZ[g];
     G.P = &T.box[T.gbox[g]];
+    // |x_i - c| <= h and |x_j - c| < h + r_cut per axis, so x_j - x_i computed
+    // from group-relative offsets is already the minimum image when
+    // 2h + r_cut < 1/2; otherwise (tiny boxes) pair offsets are taken from the
+    // integer images directly.
+    const double hm = fmax(T.ghx[g], fmax(T.ghy[g], T.ghz[g]));
+    G.wrap = 2.0 * hm + G.P->rcut >= 0.5 - 1e-9;
     return G;
 }
 
+// Shared-memory j tile: group-relative scaled offsets, or for groups that
+// span half the box the raw 64-bit images (their pair differences are taken
+// in integers, which is the exact minimum image).
 template <class R>
-__device__ __forceinline__ void stage_entry(const TreeDev &T, const Group &G, int32_t e, R sc, R *sx,
-                                            R *sy, R *sz, R *sm, int q)
+struct JTile {
+    union {
+        struct { R x[kTile], y[kTile], z[kTile]; } f;
+        struct { uint64_t x[kTile], y[kTile], z[kTile]; } u;
+    };
+    R m[kTile];
+};
+
+template <class R>
+__device__ __forceinline__ void stage_entry(const TreeDev &T, const Group &G, int32_t e, R sc,
+                                            JTile<R> &J, int q)
 {
     uint64_t ex, ey, ez;
     double mj;
@@ -113,10 +140,36 @@ __device__ __forceinline__ void stage_entry(const TreeDev &T, const Group &G, in
         const int32_t nd = -e - 1;
         ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = T.M[nd];
     }
-    sx[q] = Arith<R>::from_fixed(ex, G.X, sc);
-    sy[q] = Arith<R>::from_fixed(ey, G.Y, sc);
-    sz[q] = Arith<R>::from_fixed(ez, G.Z, sc);
-    sm[q] = (R)mj;
+    if (G.wrap) {
+        J.u.x[q] = ex; J.u.y[q] = ey; J.u.z[q] = ez;
+    } else {
+        J.f.x[q] = Arith<R>::from_fixed(ex, G.X, sc);
+        J.f.y[q] = Arith<R>::from_fixed(ey, G.Y, sc);
+        J.f.z[q] = Arith<R>::from_fixed(ez, G.Z, sc);
+    }
+    J.m[q] = (R)mj;
+}
+
+// The i particle: its scaled group-relative offset and its raw images.
+template <class R>
+struct IPart {
+    R x, y, z;
+    uint64_t X, Y, Z;
+};
+
+template <class R, bool WRAP>
+__device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPart<R> &I, R sc, R &dx,
+                                            R &dy, R &dz)
+{
+    if (WRAP) {
+        dx = Arith<R>::from_fixed(J.u.x[j], I.X, sc);
+        dy = Arith<R>::from_fixed(J.u.y[j], I.Y, sc);
+        dz = Arith<R>::from_fixed(J.u.z[j], I.Z, sc);
+    } else {
+        dx = J.f.x[j] - I.x;
+        dy = J.f.y[j] - I.y;
+        dz = J.f.z[j] - I.z;
+    }
 }
 
 template <class R>
@@ -148,6 +201,25 @@ __device__ __forceinline__ int64_t next_item(int32_t *queue, int64_t cur, int *s
     return it;
 }
 
+template <class R, bool WRAP>
+__device__ __forceinline__ void force_tile(const JTile<R> &J, int st, int nt, int ns, const IPart<R> &I,
+                                           R eps2, R sc, R &ax, R &ay, R &az)
+{
+    for (int j = st; j < nt; j += ns) {
+        R dx, dy, dz;
+        pair_offset<R, WRAP>(J, j, I, sc, dx, dy, dz);
+        const R r2 = dx * dx + dy * dy + dz * dz;
+        const R ri = Arith<R>::rsqrt(r2 + eps2);
+        const R x = Arith<R>::sqrt(r2);
+        const R g = g_p3m<R>(x, r2);
+        R f = J.m[j] * g * (ri * ri * ri);
+        f = (r2 < R(4) && r2 > R(0)) ? f : R(0);
+        ax += f * dx;
+        ay += f * dy;
+        az += f * dz;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Forward: a_i = G k^2 sum_j m_j d' g(|d'|) / (|d'|^2 + (k eps)^2)^{3/2}.
 // ---------------------------------------------------------------------------
@@ -155,8 +227,8 @@ template <class R, bool QUEUE>
 __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *queue,
                                                    const int32_t *order)
 {
-    __shared__ R sx[kTile], sy[kTile], sz[kTile], sm[kTile];
-    __shared__ R red[3][kThreads];
+    __shared__ JTile<R> J;
+    __shared__ double red[3][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
@@ -165,7 +237,6 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
         const int64_t g = order ? order[item] : item;
         const Group G = load_group(T, g);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
-        const R gk2 = (R)G.P->gk2;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
             const int ns = kThreads / nic;
@@ -173,46 +244,43 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
             const bool active = slot < nic * ns;
             const int il = active ? slot % nic : 0, st = active ? slot / nic : 0;
             const int32_t p = G.first + i0 + il;
-            const R xi = Arith<R>::from_fixed(T.X[p], G.X, sc);
-            const R yi = Arith<R>::from_fixed(T.Y[p], G.Y, sc);
-            const R zi = Arith<R>::from_fixed(T.Z[p], G.Z, sc);
-            R ax = 0, ay = 0, az = 0;
+            IPart<R> I;
+            I.X = T.X[p]; I.Y = T.Y[p]; I.Z = T.Z[p];
+            I.x = Arith<R>::from_fixed(I.X, G.X, sc);
+            I.y = Arith<R>::from_fixed(I.Y, G.Y, sc);
+            I.z = Arith<R>::from_fixed(I.Z, G.Z, sc);
+            // Two-level accumulation: each tile's terms (at most kTile / ns per
+            // thread) are summed in the working precision, tile sums in FP64.  A
+            // list of thousands of nearly cancelling terms summed wholly in FP32
+            // loses ~1e-5 relative; tile-sized partial sums keep it below 1e-6.
+            double sax = 0.0, say = 0.0, saz = 0.0;
             const int ne = bad ? 0 : G.ne;
             for (int t0 = 0; t0 < ne; t0 += kTile) {
                 const int nt = min(kTile, ne - t0);
                 __syncthreads();
                 for (int q = threadIdx.x; q < nt; q += kThreads)
-                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, sx, sy, sz, sm, q);
+                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
                 __syncthreads();
                 if (active) {
-                    for (int j = st; j < nt; j += ns) {
-                        const R dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        const R ri = Arith<R>::rsqrt(r2 + eps2);
-                        const R x = Arith<R>::sqrt(r2);
-                        R z2;
-                        const R g = g_p3m<R>(x, r2, z2);
-                        R f = sm[j] * g * (ri * ri * ri);
-                        f = (r2 < R(4) && r2 > R(0)) ? f : R(0);
-                        ax += f * dx;
-                        ay += f * dy;
-                        az += f * dz;
-                    }
+                    R ax = 0, ay = 0, az = 0;
+                    if (G.wrap) force_tile<R, true>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                    else force_tile<R, false>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                    sax += (double)ax; say += (double)ay; saz += (double)az;
                 }
             }
-            red[0][slot] = ax; red[1][slot] = ay; red[2][slot] = az;
+            red[0][slot] = sax; red[1][slot] = say; red[2][slot] = saz;
             __syncthreads();
             if (slot < nic) {
-                R sxx = 0, syy = 0, szz = 0;
+                double sxx = 0, syy = 0, szz = 0;
                 for (int s = 0; s < ns; s++) {
                     sxx += red[0][s * nic + slot];
                     syy += red[1][s * nic + slot];
                     szz += red[2][s * nic + slot];
                 }
                 const int64_t o = T.perm[G.first + i0 + slot];
-                acc[3 * o] = sxx * gk2;
-                acc[3 * o + 1] = syy * gk2;
-                acc[3 * o + 2] = szz * gk2;
+                acc[3 * o] = (R)(sxx * G.P->gk2);
+                acc[3 * o + 1] = (R)(syy * G.P->gk2);
+                acc[3 * o + 2] = (R)(szz * G.P->gk2);
             }
             __syncthreads();
         }
@@ -233,7 +301,7 @@ template <class R>
 __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, double *gs, double *ncot,
                                                   int32_t *queue, const int32_t *order)
 {
-    __shared__ R sx[kTile], sy[kTile], sz[kTile], sm[kTile];
+    __shared__ JTile<R> J;
     __shared__ R jx[kTile], jy[kTile], jz[kTile];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
@@ -254,37 +322,41 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
             const int il = (warp % nwi) * 32 + lane;
             const bool active = wactive && il < nic;
             const int32_t p = G.first + i0 + (active ? il : 0);
-            const R xi = Arith<R>::from_fixed(T.X[p], G.X, sc);
-            const R yi = Arith<R>::from_fixed(T.Y[p], G.Y, sc);
-            const R zi = Arith<R>::from_fixed(T.Z[p], G.Z, sc);
+            IPart<R> I;
+            I.X = T.X[p]; I.Y = T.Y[p]; I.Z = T.Z[p];
+            I.x = Arith<R>::from_fixed(I.X, G.X, sc);
+            I.y = Arith<R>::from_fixed(I.Y, G.Y, sc);
+            I.z = Arith<R>::from_fixed(I.Z, G.Z, sc);
             const int64_t o = T.perm[p];
             const R wx = active ? cot[3 * o] : R(0), wy = active ? cot[3 * o + 1] : R(0),
                     wz = active ? cot[3 * o + 2] : R(0);
-            R A = 0, Bx = 0, By = 0, Bz = 0;
+            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;   // tile sums in FP64
             const int ne = bad ? 0 : G.ne;
             for (int t0 = 0; t0 < ne; t0 += kTile) {
                 const int nt = min(kTile, ne - t0);
                 __syncthreads();
                 for (int q = threadIdx.x; q < nt; q += kThreads) {
-                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, sx, sy, sz, sm, q);
+                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
                     jx[q] = 0; jy[q] = 0; jz[q] = 0;
                 }
                 __syncthreads();
                 if (wactive) {
+                    R A = 0, Bx = 0, By = 0, Bz = 0;
                     for (int j = st; j < nt; j += ns) {
-                        const R dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
+                        R dx, dy, dz;
+                        if (G.wrap) pair_offset<R, true>(J, j, I, sc, dx, dy, dz);
+                        else pair_offset<R, false>(J, j, I, sc, dx, dy, dz);
                         const R r2 = dx * dx + dy * dy + dz * dz;
                         const R ri = Arith<R>::rsqrt(r2 + eps2);
                         const R x = Arith<R>::sqrt(r2);
-                        R z2;
-                        const R gv = g_p3m<R>(x, r2, z2);
-                        const R gp = gpx_p3m<R>(x, r2, z2);
+                        const R gv = g_p3m<R>(x, r2);
+                        const R gp = gpx_p3m<R>(x, r2);
                         const R ri2 = ri * ri, ri3 = ri2 * ri;
                         const R phi = gv * ri3;
                         const R psi = gp * ri3 - R(3) * phi * ri2;
                         const bool in = active && r2 < R(4) && r2 > R(0);
-                        const R alpha = in ? sm[j] * phi : R(0);
-                        const R beta = in ? sm[j] * psi * (dx * wx + dy * wy + dz * wz) : R(0);
+                        const R alpha = in ? J.m[j] * phi : R(0);
+                        const R beta = in ? J.m[j] * psi * (dx * wx + dy * wy + dz * wz) : R(0);
                         A += alpha;
                         Bx += beta * dx; By += beta * dy; Bz += beta * dz;
                         R vx = alpha * wx + beta * dx, vy = alpha * wy + beta * dy, vz = alpha * wz + beta * dz;
@@ -299,6 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
                             else { atomicAdd(&jx[j], vx); atomicAdd(&jy[j], vy); atomicAdd(&jz[j], vz); }
                         }
                     }
+                    sA += (double)A; sBx += (double)Bx; sBy += (double)By; sBz += (double)Bz;
                 }
                 __syncthreads();
                 for (int q = threadIdx.x; q < nt; q += kThreads) {
@@ -311,9 +384,9 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
             }
             if (active) {
                 // i side: dL/dx_i -= G k^3 (A w_i + B); streams meet in global atomics
-                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (double)(A * wx + Bx));
-                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (double)(A * wy + By));
-                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (double)(A * wz + Bz));
+                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)wx + sBx));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)wy + sBy));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)wz + sBz));
             }
             __syncthreads();
         }
