@@ -15,8 +15,9 @@ void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, u
 void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, void *scan_tmp, cudaStream_t s);
 void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_tmp, cudaStream_t s);
 void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s);
-void walk_count(TreeDev &T, int64_t G_cap, cudaStream_t s);
-void walk_write(TreeDev &T, int64_t G_cap, cudaStream_t s);
+void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
+void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
+void walk_write(TreeDev &T, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
                       cudaStream_t s);
@@ -122,8 +123,9 @@ struct tp_tree {
     std::vector<int64_t> box_off;
     std::vector<tp_params> prm;
     cudaStream_t last = nullptr;
-    // allocations: base (particles, workspace), nodes, groups, lists
-    Pool base, nodes, groups, lists;
+    // allocations: base (particles, workspace), nodes, groups, walk items, lists
+    Pool base, nodes, groups, items, lists;
+    int32_t split = 128;              // largest subtree a single walk task expands
     TreeDev D;
     // scratch
     uint64_t *key2 = nullptr;
@@ -137,7 +139,7 @@ struct tp_tree {
     unsigned long long *d_inter = nullptr;
     int32_t *d_maxnj = nullptr;
     // host copies of the sizes (valid after a synchronising build)
-    int64_t h_nodes = 0, h_groups = 0, h_entries = 0;
+    int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_entries = 0;
 };
 
 static tp_status cuda_status(cudaError_t e)
@@ -186,7 +188,21 @@ static bool alloc_groups(tp_tree *t, int64_t cap)
     D.gX = P.get<uint64_t>(c); D.gY = P.get<uint64_t>(c); D.gZ = P.get<uint64_t>(c);
     D.loff = P.get<int64_t>(c + 1);
     D.lcnt = P.get<int32_t>(c);
+    D.icnt = P.get<int32_t>(c);
+    D.ioff = P.get<int64_t>(c);
     t->order = P.get<int32_t>(c);
+    return P.ok;
+}
+
+static bool alloc_items(tp_tree *t, int64_t cap)
+{
+    Pool &P = t->items;
+    P.release();
+    TreeDev &D = t->D;
+    D.cap_items = cap;
+    size_t c = (size_t)cap;
+    D.item = P.get<int32_t>(c); D.igrp = P.get<int32_t>(c); D.icnt2 = P.get<int32_t>(c);
+    D.ipos = P.get<int64_t>(c);
     return P.ok;
 }
 
@@ -227,6 +243,11 @@ __global__ void k_clamp_groups(TreeDev T)
     }
 }
 
+__global__ void k_check_items(TreeDev T)
+{
+    if (*T.n_items > T.cap_items) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+}
+
 __global__ void k_check_entries(TreeDev T)
 {
     if (*T.n_entries > T.cap_entries) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
@@ -265,8 +286,19 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     }
     TP_LAUNCH(k_clamp_groups, 1, 1, 0, s, D);
     tp::build_groups(D, t->flag, t->gofs, s);
-    tp::walk_count(D, D.cap_groups, s);
-    tp::scan_i32_to_i64(D.lcnt, D.loff, 0, D.n_groups, D.n_entries, t->scan_tmp, s);
+    // walk: top items per group, then subtree tasks, then the entries
+    tp::walk_top_count(D, t->split, t->scan_tmp, s);
+    if (sync) {
+        tp_status e = cuda_status(cudaMemcpyAsync(&t->h_items, D.n_items, sizeof(int64_t),
+                                                  cudaMemcpyDeviceToHost, s));
+        if (e == TP_OK) e = cuda_status(cudaStreamSynchronize(s));
+        if (e != TP_OK) return e;
+        if (t->h_items > D.cap_items || D.item == nullptr) {
+            if (!alloc_items(t, t->h_items + t->h_items / 4 + 1024)) return TP_ERR_OOM;
+        }
+    }
+    TP_LAUNCH(k_check_items, 1, 1, 0, s, D);
+    tp::walk_items(D, t->split, t->scan_tmp, s);
     if (sync) {
         tp_status e = cuda_status(cudaMemcpyAsync(&t->h_entries, D.n_entries, sizeof(int64_t),
                                                   cudaMemcpyDeviceToHost, s));
@@ -277,7 +309,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
         }
     }
     TP_LAUNCH(k_check_entries, 1, 1, 0, s, D);
-    tp::walk_write(D, D.cap_groups, s);
+    tp::walk_write(D, s);
     return TP_OK;
 }
 
@@ -331,6 +363,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     t->flag = B.get<uint32_t>(nn); t->gofs = B.get<uint32_t>(nn);
     D.lstart = B.get<int64_t>(TP_NLEVELS + 1); D.lcount = B.get<int64_t>(TP_NLEVELS + 1);
     D.n_nodes = B.get<int64_t>(1); D.n_groups = B.get<int64_t>(1); D.n_entries = B.get<int64_t>(1);
+    D.n_items = B.get<int64_t>(1);
     D.n_ambig = B.get<unsigned long long>(1);
     D.status = B.get<int32_t>(1);
     t->queue = B.get<int32_t>(1);
@@ -372,7 +405,7 @@ tp_status tp_rebuild_tree(tp_tree *t, const double *pos, const double *mass, voi
     if (!t) return TP_ERR_INVALID_ARG;
     if (t->n > 0 && !is_device_ptr(pos)) return TP_ERR_INVALID_ARG;
     if (mass && !is_device_ptr(mass)) return TP_ERR_INVALID_ARG;
-    if (!t->D.gfirst || !t->D.ent) return TP_ERR_INVALID_ARG;
+    if (!t->D.gfirst || !t->D.ent || !t->D.item) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     t->last = s;
     tp_status e = run_build(t, pos, mass, s, false);
@@ -535,6 +568,7 @@ tp_status tp_tree_free(tp_tree *t)
     if (t->last) cudaStreamSynchronize(t->last);
     else cudaDeviceSynchronize();
     t->lists.release();
+    t->items.release();
     t->groups.release();
     t->nodes.release();
     t->base.release();

@@ -78,6 +78,13 @@ struct TreeDev {
     double *gcx, *gcy, *gcz, *ghx, *ghy, *ghz;
     uint32_t *gux, *guy, *guz, *ghux, *ghuy, *ghuz;
     uint64_t *gX, *gY, *gZ;
+    // walk items: subtree tasks and top-level monopoles, group-major, DFS order
+    int64_t cap_items;
+    int32_t *icnt;                    // [cap_groups] items per group
+    int64_t *ioff;                    // [cap_groups] first item of each group
+    int64_t *n_items;                 // device scalar
+    int32_t *item, *igrp, *icnt2;     // [cap_items] item, its group, its entry count
+    int64_t *ipos;                    // [cap_items] first entry of each item
     // lists
     int64_t *loff;                    // [cap_groups + 1]
     int32_t *lcnt;                    // [cap_groups]

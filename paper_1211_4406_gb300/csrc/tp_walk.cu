@@ -50,114 +50,205 @@ __device__ __forceinline__ double exact_dist2(double ax, double ay, double az, d
     return __dadd_rn(__dadd_rn(__dmul_rn(gp[0], gp[0]), __dmul_rn(gp[1], gp[1])), __dmul_rn(gp[2], gp[2]));
 }
 
-template <bool WRITE>
-__global__ void __launch_bounds__(kBlock) k_walk(TreeDev T, int64_t G_cap)
+// Walk modes.  TOP: from the box root, an opened node holding at most `split`
+// particles (or a leaf) is not descended but emitted as a task item (its node
+// id); accepted monopoles are emitted as final items -(id+1).  TASK: from a
+// task node to the end of its subtree (its skip pointer), emitting list entries.
+// The items of all groups, concatenated in group order and in depth-first order
+// within a group, expand to exactly the depth-first lists of the reference.
+enum { kTop = 0, kTask = 1 };
+
+struct WalkGroup {
+    uint32_t gx, gy, gz, hx, hy, hz;
+    int32_t g0, g1;
+    int64_t g;
+    const BoxPrm *P;
+};
+
+__device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g)
 {
-    const int64_t G = *T.n_groups < G_cap ? *T.n_groups : G_cap;
-    if (WRITE && *T.status == TP_ERR_LIST_OVERFLOW) return;   // lists would not fit
+    WalkGroup W;
+    W.g = g;
+    W.gx = T.gux[g]; W.gy = T.guy[g]; W.gz = T.guz[g];
+    W.hx = T.ghux[g]; W.hy = T.ghuy[g]; W.hz = T.ghuz[g];
+    W.g0 = T.gfirst[g];
+    W.g1 = W.g0 + T.gcount[g];
+    W.P = &T.box[T.gbox[g]];
+    return W;
+}
+
+// Depth-first walk from `start` until the preorder reaches `end` (-1: the end
+// of the tree).  Returns the number of items (kTop) or entries (kTask); with
+// out != nullptr writes them to out[0 .. out_n).
+template <int MODE>
+__device__ int32_t walk_dfs(const TreeDev &T, const WalkGroup &W, int32_t start, int32_t end,
+                            int32_t split, int32_t *out, int64_t out_n, unsigned long long &ambig)
+{
+    const uint64_t T_lo = W.P->T_lo, T_hi = W.P->T_hi;
+    int32_t cnt = 0;
+    int32_t nd = start;
+    int64_t budget = *T.n_nodes + 1;     // a preorder walk visits each node at most once
+    while (nd != end && nd >= 0) {
+        if (--budget < 0 || nd >= T.cap_nodes) {
+            tp_latch(T.status, TP_ERR_TIMEOUT);
+            break;
+        }
+        const WNode w = T.wn[nd];
+        const uint32_t ax = absdiff32(w.cx, W.gx), ay = absdiff32(w.cy, W.gy), az = absdiff32(w.cz, W.gz);
+        const uint64_t sx = (uint64_t)w.hx + W.hx, sy = (uint64_t)w.hy + W.hy, sz = (uint64_t)w.hz + W.hz;
+        const uint64_t dx = ax > sx ? ax - sx : 0, dy = ay > sy ? ay - sy : 0, dz = az > sz ? az - sz : 0;
+        const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
+        bool exact = false, prune;
+        double gap2d = 0.0, far2d = 0.0;
+        if (gap2 >= T_hi) {
+            prune = true;
+        } else if (gap2 < T_lo) {
+            prune = false;
+        } else {
+            exact = true;
+            ambig++;
+            gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd],
+                                T.gcx[W.g], T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g],
+                                &far2d);
+            prune = gap2d >= W.P->rc2;
+        }
+        if (prune) { nd = w.skip; continue; }
+        const bool overlap = w.first < W.g1 && W.g0 < w.first + w.count;
+        bool accept = false;
+        if (!overlap) {
+            if (!exact) {
+                const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
+                const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
+                const int A = far2 < T_lo ? 1 : (far2 >= T_hi ? 0 : -1);
+                const int B = gap2 >= W.P->TB_hi[w.level] ? 1 : (gap2 < W.P->TB_lo[w.level] ? 0 : -1);
+                if (A == 0 || B == 0) {
+                    accept = false;
+                } else if (A == 1 && B == 1) {
+                    accept = true;
+                } else {
+                    exact = true;
+                    ambig++;
+                    gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd],
+                                        T.gcx[W.g], T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g],
+                                        T.ghz[W.g], &far2d);
+                }
+            }
+            if (exact) {
+                const double l = ldexp(1.0, -w.level);
+                accept = far2d < W.P->rc2 && __dmul_rn(l, l) < __dmul_rn(W.P->th2, gap2d);
+            }
+        }
+        if (accept) {
+            if (out && cnt < out_n) out[cnt] = -(nd + 1);
+            cnt++;
+            nd = w.skip;
+            continue;
+        }
+        if (MODE == kTop && (w.child < 0 || w.count <= split)) {
+            if (out && cnt < out_n) out[cnt] = nd;       // a task: expand its subtree later
+            cnt++;
+            nd = w.skip;
+            continue;
+        }
+        if (w.child < 0) {
+            for (int32_t p = w.first; p < w.first + w.count; p++) {
+                const uint32_t qx = absdiff32((uint32_t)(T.X[p] >> 32), W.gx);
+                const uint32_t qy = absdiff32((uint32_t)(T.Y[p] >> 32), W.gy);
+                const uint32_t qz = absdiff32((uint32_t)(T.Z[p] >> 32), W.gz);
+                const uint64_t ex = qx > W.hx ? qx - W.hx : 0, ey = qy > W.hy ? qy - W.hy : 0,
+                               ez = qz > W.hz ? qz - W.hz : 0;
+                const uint64_t p2 = ex * ex + ey * ey + ez * ez;
+                bool keep;
+                if (p2 >= T_hi) {
+                    keep = false;
+                } else if (p2 < T_lo) {
+                    keep = true;
+                } else {
+                    ambig++;
+                    double f2;
+                    keep = exact_dist2(T.x[p], T.y[p], T.z[p], 0.0, 0.0, 0.0, T.gcx[W.g], T.gcy[W.g],
+                                       T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g], &f2) < W.P->rc2;
+                }
+                if (keep) {
+                    if (out && cnt < out_n) out[cnt] = p;
+                    cnt++;
+                }
+            }
+            nd = w.skip;
+        } else {
+            nd = w.child;
+        }
+    }
+    return cnt;
+}
+
+// Top walk of every group: item counts (WRITE = false) or items (WRITE = true).
+template <bool WRITE>
+__global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    if (WRITE && *T.status == TP_ERR_LIST_OVERFLOW) return;
     unsigned long long ambig = 0;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t b = T.gbox[g];
-        const BoxPrm &P = T.box[b];
-        const uint32_t gx = T.gux[g], gy = T.guy[g], gz = T.guz[g];
-        const uint32_t hx = T.ghux[g], hy = T.ghuy[g], hz = T.ghuz[g];
-        const int32_t g0 = T.gfirst[g], g1 = g0 + T.gcount[g];
-        const uint64_t T_lo = P.T_lo, T_hi = P.T_hi;
-        int64_t out = WRITE ? T.loff[g] : 0;
-        int64_t out_end = WRITE ? out + T.lcnt[g] : 0;
-        if (WRITE && out_end > T.cap_entries) out_end = T.cap_entries;
-        int32_t cnt = 0;
-        int32_t nd = b;                       // the box root
-        int64_t budget = *T.n_nodes + 1;      // a preorder walk visits each node at most once
-        while (nd >= 0) {
-            if (--budget < 0 || nd >= T.cap_nodes) {
-                tp_latch(T.status, TP_ERR_TIMEOUT);
-                break;
-            }
-            const WNode w = T.wn[nd];
-            const uint32_t ax = absdiff32(w.cx, gx), ay = absdiff32(w.cy, gy), az = absdiff32(w.cz, gz);
-            const uint64_t sx = (uint64_t)w.hx + hx, sy = (uint64_t)w.hy + hy, sz = (uint64_t)w.hz + hz;
-            const uint64_t dx = ax > sx ? ax - sx : 0, dy = ay > sy ? ay - sy : 0, dz = az > sz ? az - sz : 0;
-            const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
-            bool exact = false, prune;
-            double gap2d = 0.0, far2d = 0.0;
-            if (gap2 >= T_hi) {
-                prune = true;
-            } else if (gap2 < T_lo) {
-                prune = false;
-            } else {
-                exact = true;
-                ambig++;
-                gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd],
-                                    T.gcx[g], T.gcy[g], T.gcz[g], T.ghx[g], T.ghy[g], T.ghz[g], &far2d);
-                prune = gap2d >= P.rc2;
-            }
-            if (prune) { nd = w.skip; continue; }
-            const bool overlap = w.first < g1 && g0 < w.first + w.count;
-            bool accept = false;
-            if (!overlap) {
-                if (!exact) {
-                    const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
-                    const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
-                    const int A = far2 < T_lo ? 1 : (far2 >= T_hi ? 0 : -1);
-                    const int B = gap2 >= P.TB_hi[w.level] ? 1 : (gap2 < P.TB_lo[w.level] ? 0 : -1);
-                    if (A == 0 || B == 0) {
-                        accept = false;
-                    } else if (A == 1 && B == 1) {
-                        accept = true;
-                    } else {
-                        exact = true;
-                        ambig++;
-                        gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd],
-                                            T.hfz[nd], T.gcx[g], T.gcy[g], T.gcz[g], T.ghx[g], T.ghy[g],
-                                            T.ghz[g], &far2d);
-                    }
-                }
-                if (exact) {
-                    const double l = ldexp(1.0, -w.level);
-                    accept = far2d < P.rc2 && __dmul_rn(l, l) < __dmul_rn(P.th2, gap2d);
-                }
-            }
-            if (accept) {
-                if (WRITE && out < out_end) T.ent[out++] = -(nd + 1);
-                cnt++;
-                nd = w.skip;
-                continue;
-            }
-            if (w.child < 0) {
-                for (int32_t p = w.first; p < w.first + w.count; p++) {
-                    const uint32_t qx = absdiff32((uint32_t)(T.X[p] >> 32), gx);
-                    const uint32_t qy = absdiff32((uint32_t)(T.Y[p] >> 32), gy);
-                    const uint32_t qz = absdiff32((uint32_t)(T.Z[p] >> 32), gz);
-                    const uint64_t ex = qx > hx ? qx - hx : 0, ey = qy > hy ? qy - hy : 0,
-                                   ez = qz > hz ? qz - hz : 0;
-                    const uint64_t p2 = ex * ex + ey * ey + ez * ez;
-                    bool keep;
-                    if (p2 >= T_hi) {
-                        keep = false;
-                    } else if (p2 < T_lo) {
-                        keep = true;
-                    } else {
-                        ambig++;
-                        double f2;
-                        keep = exact_dist2(T.x[p], T.y[p], T.z[p], 0.0, 0.0, 0.0, T.gcx[g], T.gcy[g], T.gcz[g],
-                                           T.ghx[g], T.ghy[g], T.ghz[g], &f2) < P.rc2;
-                    }
-                    if (keep) {
-                        if (WRITE && out < out_end) T.ent[out++] = p;
-                        cnt++;
-                    }
-                }
-                nd = w.skip;
-            } else {
-                nd = w.child;
-            }
+        const WalkGroup W = load_walk_group(T, g);
+        if (!WRITE) {
+            T.icnt[g] = walk_dfs<kTop>(T, W, T.gbox[g], -1, split, nullptr, 0, ambig);
+        } else {
+            const int64_t o = T.ioff[g];
+            const int64_t n = T.icnt[g];
+            if (o + n > T.cap_items) continue;
+            const int32_t c = walk_dfs<kTop>(T, W, T.gbox[g], -1, split, T.item + o, n, ambig);
+            for (int64_t k = 0; k < c && k < n; k++) T.igrp[o + k] = (int32_t)g;
         }
-        if (!WRITE) T.lcnt[g] = cnt;
-        else if (out != T.loff[g] + cnt) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
     }
     if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
+}
+
+// Expansion of every item: entry counts (WRITE = false) or entries.
+template <bool WRITE>
+__global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T)
+{
+    const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
+    if (WRITE && *T.status == TP_ERR_LIST_OVERFLOW) return;
+    unsigned long long ambig = 0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < NI;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = T.item[it];
+        if (v < 0) {                                  // an accepted monopole
+            if (!WRITE) T.icnt2[it] = 1;
+            else if (T.ipos[it] < T.cap_entries) T.ent[T.ipos[it]] = v;
+            continue;
+        }
+        const WalkGroup W = load_walk_group(T, T.igrp[it]);
+        const int32_t end = T.wn[v].skip;
+        if (!WRITE) {
+            T.icnt2[it] = walk_dfs<kTask>(T, W, v, end, 0, nullptr, 0, ambig);
+        } else {
+            const int64_t o = T.ipos[it];
+            const int64_t n = T.icnt2[it];
+            if (o + n > T.cap_entries) continue;
+            walk_dfs<kTask>(T, W, v, end, 0, T.ent + o, n, ambig);
+        }
+    }
+    if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
+}
+
+// Per-group list offsets and counts from the item positions.
+__global__ void k_list_offsets(TreeDev T)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
+    const int64_t E = *T.n_entries;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i0 = T.ioff[g];
+        const int64_t i1 = g + 1 < G ? T.ioff[g + 1] : NI;
+        const int64_t e0 = i0 < NI ? T.ipos[i0] : E;
+        const int64_t e1 = i1 < NI ? T.ipos[i1] : E;
+        T.loff[g] = e0;
+        T.lcnt[g] = (int32_t)(e1 - e0);
+    }
 }
 
 __global__ void k_list_stats(TreeDev T, unsigned long long *inter, int32_t *max_nj)
@@ -184,16 +275,28 @@ __global__ void k_list_stats(TreeDev T, unsigned long long *inter, int32_t *max_
 
 namespace tp {
 
-void walk_count(TreeDev &T, int64_t G_cap, cudaStream_t s)
+// Item counts per group -> T.ioff (scan) -> *T.n_items.
+void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 {
-    if (G_cap <= 0) return;
-    TP_LAUNCH(k_walk<false>, grid_for(G_cap, kBlock), kBlock, 0, s, T, G_cap);
+    if (T.cap_groups <= 0) return;
+    TP_LAUNCH(k_walk_top<false>, grid_for(T.cap_groups, kBlock), kBlock, 0, s, T, split);
+    scan_i32_to_i64(T.icnt, T.ioff, 0, T.n_groups, T.n_items, scan_tmp, s);
 }
 
-void walk_write(TreeDev &T, int64_t G_cap, cudaStream_t s)
+// Items, their entry counts, and their positions (scan) -> *T.n_entries.
+void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 {
-    if (G_cap <= 0) return;
-    TP_LAUNCH(k_walk<true>, grid_for(G_cap, kBlock), kBlock, 0, s, T, G_cap);
+    if (T.cap_groups <= 0 || T.cap_items <= 0) return;
+    TP_LAUNCH(k_walk_top<true>, grid_for(T.cap_groups, kBlock), kBlock, 0, s, T, split);
+    TP_LAUNCH(k_walk_task<false>, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
+    scan_i32_to_i64(T.icnt2, T.ipos, 0, T.n_items, T.n_entries, scan_tmp, s);
+    TP_LAUNCH(k_list_offsets, grid_for(T.cap_groups, 256), 256, 0, s, T);
+}
+
+void walk_write(TreeDev &T, cudaStream_t s)
+{
+    if (T.cap_items <= 0) return;
+    TP_LAUNCH(k_walk_task<true>, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
 }
 
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s)
