@@ -27,6 +27,51 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
+// Packed FP32 pairs (two lanes of one 64-bit register): Blackwell executes
+// add/sub/mul/fma.f32x2 as one instruction, halving the issue slots of the
+// pair arithmetic.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 f2relu(f2 v)
+{
+    float a, b;
+    f2unpack(v, a, b);
+    return f2pack(fmaxf(a, 0.f), fmaxf(b, 0.f));
+}
+
 template <class R> struct Arith;
 
 template <> struct Arith<float> {
@@ -71,24 +116,6 @@ __device__ __forceinline__ R g_p3m(R xi, R r2)
     return xi <= R(1.0) ? lo : hi;
 }
 
-// g'(xi)/xi of Eq. 3, branch by branch: -24/5 xi + 8 xi^3 - 3 xi^4 - 12/5 xi^5
-// + 6/5 xi^6 on [0,1]; -(2 - xi)^4 (2 xi^2 + 4 xi - 1) / 5 on [1,2].
-template <class R>
-__device__ __forceinline__ R gpx_p3m(R xi, R r2)
-{
-    R p = R(6.0 / 5.0) * xi + R(-12.0 / 5.0);
-    p = p * xi + R(-3.0);
-    p = p * xi + R(8.0);
-    p = p * r2 + R(-24.0 / 5.0);
-    const R lo = p * xi;
-    const R u = R(2.0) - xi;
-    const R u2 = u * u;
-    R q = R(-2.0 / 5.0) * xi + R(-4.0 / 5.0);
-    q = q * xi + R(1.0 / 5.0);
-    const R hi = (u2 * u2) * q;
-    return xi <= R(1.0) ? lo : hi;
-}
-
 struct Group {
     int32_t first, ni;
     int64_t e0;
@@ -124,6 +151,9 @@ struct JTile {
     union {
         struct { R x[kTile], y[kTile], z[kTile]; } f;
         struct { uint64_t x[kTile], y[kTile], z[kTile]; } u;
+        // packed layout: entries 2p and 2p+1 share A[p] = {x0, x1, y0, y1} and
+        // B[p] = {z0, z1, m0, m1}, so two 128-bit loads feed two pairs
+        struct { float4 A[kTile / 2], B[kTile / 2]; } p;
     };
     R m[kTile];
 };
@@ -170,6 +200,85 @@ __device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPar
         dy = J.f.y[j] - I.y;
         dz = J.f.z[j] - I.z;
     }
+}
+
+__device__ __forceinline__ void stage_entry_packed(const TreeDev &T, const Group &G, int32_t e, float sc,
+                                                   JTile<float> &J, int q)
+{
+    uint64_t ex, ey, ez;
+    double mj;
+    if (e >= 0) {
+        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = T.m[e];
+    } else {
+        const int32_t nd = -e - 1;
+        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = T.M[nd];
+    }
+    float *A = reinterpret_cast<float *>(&J.p.A[q >> 1]);
+    float *B = reinterpret_cast<float *>(&J.p.B[q >> 1]);
+    const int l = q & 1;
+    A[l] = Arith<float>::from_fixed(ex, G.X, sc);
+    A[2 + l] = Arith<float>::from_fixed(ey, G.Y, sc);
+    B[l] = Arith<float>::from_fixed(ez, G.Z, sc);
+    B[2 + l] = (float)mj;
+}
+
+// Odd tiles get a partner entry of zero mass far outside the cutoff.
+__device__ __forceinline__ void stage_pad_packed(JTile<float> &J, int q)
+{
+    float *A = reinterpret_cast<float *>(&J.p.A[q >> 1]);
+    float *B = reinterpret_cast<float *>(&J.p.B[q >> 1]);
+    const int l = q & 1;
+    A[l] = 1.0e4f; A[2 + l] = 1.0e4f; B[l] = 1.0e4f; B[2 + l] = 0.f;
+}
+
+// Two pairs per step, packed.  Eq. 3 as g = u^5 h(xi) + v^6 c(xi) with
+// u = max(0, 2 - xi), v = max(0, 1 - xi), h = (7 xi^3 + 22 xi^2 + 10 xi + 4)/140
+// and c = (7 xi^2 + 18 xi + 3)/35: on [1,2] the first term alone is Eq. 3's
+// factored form, on [0,1] the second adds Eq. 3's difference between its two
+// branches, (1 - xi)^6 c(xi).  Both terms are non-negative (no cancellation in
+// FP32) and u = 0 makes g vanish exactly at and beyond the cutoff.
+__device__ __forceinline__ void force_tile_packed(const JTile<float> &J, int st, int npairs, int ns, float xi,
+                                                  float yi, float zi, float eps2, float &axs, float &ays,
+                                                  float &azs)
+{
+    const f2 X = f2pack(xi, xi), Y = f2pack(yi, yi), Z = f2pack(zi, zi);
+    const f2 E2 = f2pack(eps2, eps2), TWO = f2pack(2.f, 2.f), ONE = f2pack(1.f, 1.f);
+    const f2 H3 = f2pack(7.f / 140.f, 7.f / 140.f), H2 = f2pack(22.f / 140.f, 22.f / 140.f);
+    const f2 H1 = f2pack(10.f / 140.f, 10.f / 140.f), H0 = f2pack(4.f / 140.f, 4.f / 140.f);
+    const f2 C2 = f2pack(7.f / 35.f, 7.f / 35.f), C1 = f2pack(18.f / 35.f, 18.f / 35.f);
+    const f2 C0 = f2pack(3.f / 35.f, 3.f / 35.f);
+    f2 ax = f2pack(0.f, 0.f), ay = ax, az = ax;
+#pragma unroll 2
+    for (int p = st; p < npairs; p += ns) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&J.p.A[p]);
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&J.p.B[p]);
+        const f2 dx = f2sub(a.x, X), dy = f2sub(a.y, Y), dz = f2sub(b.x, Z);
+        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+        float r2a, r2b, s2a, s2b;
+        f2unpack(r2, r2a, r2b);
+        f2unpack(f2add(r2, E2), s2a, s2b);
+        const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+        const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+        const f2 u = f2relu(f2sub(TWO, x));
+        const f2 v = f2relu(f2sub(ONE, x));
+        f2 h = f2fma(H3, x, H2);
+        h = f2fma(h, x, H1);
+        h = f2fma(h, x, H0);
+        f2 c = f2fma(C2, x, C1);
+        c = f2fma(c, x, C0);
+        const f2 u2 = f2mul(u, u), v2 = f2mul(v, v);
+        const f2 u5 = f2mul(f2mul(u2, u2), u), v6 = f2mul(f2mul(v2, v2), v2);
+        const f2 g = f2fma(v6, c, f2mul(u5, h));
+        const f2 ri3 = f2mul(f2mul(ri, ri), ri);
+        const f2 f = f2mul(f2mul(b.y, g), ri3);
+        ax = f2fma(f, dx, ax);
+        ay = f2fma(f, dy, ay);
+        az = f2fma(f, dz, az);
+    }
+    float l, h;
+    f2unpack(ax, l, h); axs += l + h;
+    f2unpack(ay, l, h); ays += l + h;
+    f2unpack(az, l, h); azs += l + h;
 }
 
 template <class R>
@@ -255,16 +364,34 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
             // loses ~1e-5 relative; tile-sized partial sums keep it below 1e-6.
             double sax = 0.0, say = 0.0, saz = 0.0;
             const int ne = bad ? 0 : G.ne;
+            // packed FP32 path for ordinary groups with eps > 0; the scalar
+            // path covers box-spanning groups, eps = 0 and FP64
+            const bool packed = sizeof(R) == 4 && !G.wrap && eps2 > R(0);
             for (int t0 = 0; t0 < ne; t0 += kTile) {
                 const int nt = min(kTile, ne - t0);
                 __syncthreads();
-                for (int q = threadIdx.x; q < nt; q += kThreads)
-                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
+                if (packed) {
+                    for (int q = threadIdx.x; q < nt; q += kThreads)
+                        stage_entry_packed(T, G, T.ent[G.e0 + t0 + q], (float)sc,
+                                           *reinterpret_cast<JTile<float> *>(&J), q);
+                    if ((nt & 1) && threadIdx.x == 0) stage_pad_packed(*reinterpret_cast<JTile<float> *>(&J), nt);
+                } else {
+                    for (int q = threadIdx.x; q < nt; q += kThreads)
+                        stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
+                }
                 __syncthreads();
                 if (active) {
                     R ax = 0, ay = 0, az = 0;
-                    if (G.wrap) force_tile<R, true>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
-                    else force_tile<R, false>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                    if (packed) {
+                        float fx = 0.f, fy = 0.f, fz = 0.f;
+                        force_tile_packed(*reinterpret_cast<const JTile<float> *>(&J), st, (nt + 1) >> 1, ns,
+                                          (float)I.x, (float)I.y, (float)I.z, (float)eps2, fx, fy, fz);
+                        ax = fx; ay = fy; az = fz;
+                    } else if (G.wrap) {
+                        force_tile<R, true>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                    } else {
+                        force_tile<R, false>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                    }
                     sax += (double)ax; say += (double)ay; saz += (double)az;
                 }
             }
@@ -292,17 +419,40 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 //   J' = phi I + psi d' d'^T,  psi = (g'/xi)/s'^3 - 3 g/s'^5,
 //   v  = m_j J' w_i = alpha w_i + beta d',  alpha = m_j phi, beta = m_j psi (d'.w_i)
 // and dL/dx_i -= G k^3 v, dL/dx_j += G k^3 v (a node passes its share to its
-// centre-of-mass cotangent).  The i side accumulates A = sum alpha and
-// B = sum beta d' in registers; the j side needs the sum over the group's i for
-// each entry, so every warp holds one stream (32 distinct i) and reduces with
-// shuffles before one shared-memory add per warp and entry.
+// centre-of-mass cotangent).  Threads hold list entries (j) and loop over the
+// group's particles (i) held in shared memory, so the j side sums in
+// registers; the i side (A_i = sum alpha, B_i = sum beta d') is a full-warp
+// butterfly per i, added into FP64 shared accumulators.
 // ---------------------------------------------------------------------------
+
+// g and g'/xi in the cancellation-free form (u = max(0, 2 - xi),
+// v = max(0, 1 - xi)): g = u^5 (7 xi^3 + 22 xi^2 + 10 xi + 4)/140 + v^6 (7 xi^2
+// + 18 xi + 3)/35 and g'/xi = -u^4 (2 xi^2 + 4 xi - 1)/5 - (8/5) v^5 (xi + 2).
+// The second can lose ~2e-7 absolute near xi = 0, where it enters J only
+// multiplied by xi^2.
+template <class R>
+__device__ __forceinline__ void g_gpx(R x, R &g, R &gp)
+{
+    const R u = fmax(R(2) - x, R(0)), v = fmax(R(1) - x, R(0));
+    R h = R(7.0 / 140.0) * x + R(22.0 / 140.0);
+    h = h * x + R(10.0 / 140.0);
+    h = h * x + R(4.0 / 140.0);
+    R c = R(7.0 / 35.0) * x + R(18.0 / 35.0);
+    c = c * x + R(3.0 / 35.0);
+    const R u2 = u * u, u4 = u2 * u2, v2 = v * v, v4 = v2 * v2;
+    g = v4 * v2 * c + u4 * u * h;
+    R q = R(2.0 / 5.0) * x + R(4.0 / 5.0);
+    q = q * x + R(-1.0 / 5.0);
+    gp = -(u4 * q) - R(8.0 / 5.0) * (v4 * v) * (x + R(2));
+}
+
 template <class R>
 __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, double *gs, double *ncot,
                                                   int32_t *queue, const int32_t *order)
 {
-    __shared__ JTile<R> J;
-    __shared__ R jx[kTile], jy[kTile], jz[kTile];
+    __shared__ R ix[kThreads], iy[kThreads], iz[kThreads], iwx[kThreads], iwy[kThreads], iwz[kThreads];
+    __shared__ uint64_t iX[kThreads], iY[kThreads], iZ[kThreads];
+    __shared__ R part[kThreads / 32][4][kThreads];   // per-warp i-side sums of one tile
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
@@ -313,80 +463,98 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
         const Group G = load_group(T, g);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
         const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
+        const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
-            const int nwi = (nic + 31) >> 5;                 // warps per stream
-            const int ns = (kThreads >> 5) / nwi;            // streams
-            const bool wactive = warp < nwi * ns;
-            const int st = wactive ? warp / nwi : 0;
-            const int il = (warp % nwi) * 32 + lane;
-            const bool active = wactive && il < nic;
-            const int32_t p = G.first + i0 + (active ? il : 0);
-            IPart<R> I;
-            I.X = T.X[p]; I.Y = T.Y[p]; I.Z = T.Z[p];
-            I.x = Arith<R>::from_fixed(I.X, G.X, sc);
-            I.y = Arith<R>::from_fixed(I.Y, G.Y, sc);
-            I.z = Arith<R>::from_fixed(I.Z, G.Z, sc);
-            const int64_t o = T.perm[p];
-            const R wx = active ? cot[3 * o] : R(0), wy = active ? cot[3 * o + 1] : R(0),
-                    wz = active ? cot[3 * o + 2] : R(0);
-            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;   // tile sums in FP64
-            const int ne = bad ? 0 : G.ne;
-            for (int t0 = 0; t0 < ne; t0 += kTile) {
-                const int nt = min(kTile, ne - t0);
-                __syncthreads();
-                for (int q = threadIdx.x; q < nt; q += kThreads) {
-                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
-                    jx[q] = 0; jy[q] = 0; jz[q] = 0;
-                }
-                __syncthreads();
-                if (wactive) {
-                    R A = 0, Bx = 0, By = 0, Bz = 0;
-                    for (int j = st; j < nt; j += ns) {
-                        R dx, dy, dz;
-                        if (G.wrap) pair_offset<R, true>(J, j, I, sc, dx, dy, dz);
-                        else pair_offset<R, false>(J, j, I, sc, dx, dy, dz);
-                        const R r2 = dx * dx + dy * dy + dz * dz;
-                        const R ri = Arith<R>::rsqrt(r2 + eps2);
-                        const R x = Arith<R>::sqrt(r2);
-                        const R gv = g_p3m<R>(x, r2);
-                        const R gp = gpx_p3m<R>(x, r2);
-                        const R ri2 = ri * ri, ri3 = ri2 * ri;
-                        const R phi = gv * ri3;
-                        const R psi = gp * ri3 - R(3) * phi * ri2;
-                        const bool in = active && r2 < R(4) && r2 > R(0);
-                        const R alpha = in ? J.m[j] * phi : R(0);
-                        const R beta = in ? J.m[j] * psi * (dx * wx + dy * wy + dz * wz) : R(0);
-                        A += alpha;
-                        Bx += beta * dx; By += beta * dy; Bz += beta * dz;
-                        R vx = alpha * wx + beta * dx, vy = alpha * wy + beta * dy, vz = alpha * wz + beta * dz;
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            vx += __shfl_xor_sync(0xffffffffu, vx, off);
-                            vy += __shfl_xor_sync(0xffffffffu, vy, off);
-                            vz += __shfl_xor_sync(0xffffffffu, vz, off);
-                        }
-                        if (lane == 0) {
-                            if (nwi == 1) { jx[j] = vx; jy[j] = vy; jz[j] = vz; }
-                            else { atomicAdd(&jx[j], vx); atomicAdd(&jy[j], vy); atomicAdd(&jz[j], vz); }
-                        }
-                    }
-                    sA += (double)A; sBx += (double)Bx; sBy += (double)By; sBz += (double)Bz;
-                }
-                __syncthreads();
-                for (int q = threadIdx.x; q < nt; q += kThreads) {
-                    const int32_t e = T.ent[G.e0 + t0 + q];
-                    double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
-                    atomicAdd(dst, gk3 * (double)jx[q]);
-                    atomicAdd(dst + 1, gk3 * (double)jy[q]);
-                    atomicAdd(dst + 2, gk3 * (double)jz[q]);
-                }
+            if (threadIdx.x < nic) {
+                const int32_t p = G.first + i0 + threadIdx.x;
+                const uint64_t X = T.X[p], Y = T.Y[p], Z = T.Z[p];
+                iX[threadIdx.x] = X; iY[threadIdx.x] = Y; iZ[threadIdx.x] = Z;
+                ix[threadIdx.x] = Arith<R>::from_fixed(X, G.X, sc);
+                iy[threadIdx.x] = Arith<R>::from_fixed(Y, G.Y, sc);
+                iz[threadIdx.x] = Arith<R>::from_fixed(Z, G.Z, sc);
+                const int64_t o = T.perm[p];
+                iwx[threadIdx.x] = cot[3 * o]; iwy[threadIdx.x] = cot[3 * o + 1]; iwz[threadIdx.x] = cot[3 * o + 2];
             }
-            if (active) {
-                // i side: dL/dx_i -= G k^3 (A w_i + B); streams meet in global atomics
-                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)wx + sBx));
-                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)wy + sBy));
-                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)wz + sBz));
+            // thread t < nic owns particle i0 + t's i-side sums (FP64 across tiles)
+            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;
+            __syncthreads();
+            for (int t0 = 0; t0 < ne; t0 += kThreads) {
+                const int q = t0 + threadIdx.x;
+                const bool valid = q < ne;
+                int32_t e = 0;
+                uint64_t ex = 0, ey = 0, ez = 0;
+                R mj = 0;
+                if (valid) {
+                    e = T.ent[G.e0 + q];
+                    if (e >= 0) {
+                        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = (R)T.m[e];
+                    } else {
+                        const int32_t nd = -e - 1;
+                        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = (R)T.M[nd];
+                    }
+                }
+                const R xj = Arith<R>::from_fixed(ex, G.X, sc), yj = Arith<R>::from_fixed(ey, G.Y, sc),
+                        zj = Arith<R>::from_fixed(ez, G.Z, sc);
+                R vx = 0, vy = 0, vz = 0;
+                for (int k = 0; k < nic; k++) {
+                    R dx, dy, dz;
+                    if (G.wrap) {
+                        dx = Arith<R>::from_fixed(ex, iX[k], sc);
+                        dy = Arith<R>::from_fixed(ey, iY[k], sc);
+                        dz = Arith<R>::from_fixed(ez, iZ[k], sc);
+                    } else {
+                        dx = xj - ix[k]; dy = yj - iy[k]; dz = zj - iz[k];
+                    }
+                    const R wx = iwx[k], wy = iwy[k], wz = iwz[k];
+                    const R r2 = dx * dx + dy * dy + dz * dz;
+                    const R ri = Arith<R>::rsqrt(r2 + eps2);
+                    const R x = Arith<R>::sqrt(r2);
+                    R gv, gp;
+                    g_gpx<R>(x, gv, gp);
+                    const R ri2 = ri * ri, ri3 = ri2 * ri;
+                    const R phi = gv * ri3;
+                    const R psi = gp * ri3 - R(3) * phi * ri2;
+                    const bool in = valid && r2 > R(0);
+                    const R alpha = in ? mj * phi : R(0);
+                    const R beta = in ? mj * psi * (dx * wx + dy * wy + dz * wz) : R(0);
+                    vx += alpha * wx + beta * dx;
+                    vy += alpha * wy + beta * dy;
+                    vz += alpha * wz + beta * dz;
+                    R a = alpha, bx = beta * dx, by = beta * dy, bz = beta * dz;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, off);
+                        bx += __shfl_xor_sync(0xffffffffu, bx, off);
+                        by += __shfl_xor_sync(0xffffffffu, by, off);
+                        bz += __shfl_xor_sync(0xffffffffu, bz, off);
+                    }
+                    if (lane == 0) {
+                        part[warp][0][k] = a; part[warp][1][k] = bx;
+                        part[warp][2][k] = by; part[warp][3][k] = bz;
+                    }
+                }
+                if (valid) {
+                    double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
+                    atomicAdd(dst, gk3 * (double)vx);
+                    atomicAdd(dst + 1, gk3 * (double)vy);
+                    atomicAdd(dst + 2, gk3 * (double)vz);
+                }
+                __syncthreads();
+                if (threadIdx.x < nic) {
+                    const int nw = min(kThreads, ne - t0 + 31) >> 5;   // warps that held entries
+                    for (int w = 0; w < nw; w++) {
+                        sA += (double)part[w][0][threadIdx.x]; sBx += (double)part[w][1][threadIdx.x];
+                        sBy += (double)part[w][2][threadIdx.x]; sBz += (double)part[w][3][threadIdx.x];
+                    }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x < nic) {
+                const int32_t p = G.first + i0 + threadIdx.x;
+                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)iwx[threadIdx.x] + sBx));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)iwy[threadIdx.x] + sBy));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)iwz[threadIdx.x] + sBz));
             }
             __syncthreads();
         }
