@@ -285,9 +285,9 @@ def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64):
 def leapfrog(pos0, vel0, mass, G, eps, rcut, theta, dt, steps, n_leaf=8, n_crit=64,
              keep_trees=False):
     """Kick-drift-kick leapfrog with the short-range force only, rebuilding the
-    tree every force evaluation.  Returns (x_T, v_T, trees) where `trees` holds
+    tree every force evaluation.  Returns (x_T, v_T, a_T, trees); `trees` holds
     the oracle tree of each evaluation when keep_trees is set (for frozen-
-    structure finite differences)."""
+    structure finite differences and the adjoint)."""
     x = _f64(pos0).copy()
     v = _f64(vel0).copy()
     trees = []
@@ -301,12 +301,13 @@ def leapfrog(pos0, vel0, mass, G, eps, rcut, theta, dt, steps, n_leaf=8, n_crit=
         if keep_trees:
             trees.append(t)
         v = v + a * (0.5 * dt)
-    return x, v, trees
+    return x, v, a, trees
 
 
 def leapfrog_frozen(pos0, vel0, trees, G, eps, rcut, dt, steps):
     """The same integration with every force evaluation's structure frozen to
-    the given trees (monopoles re-taken from the current positions)."""
+    the given trees (monopoles re-taken from the current positions).
+    Returns (x_T, v_T, a_T)."""
     x = _f64(pos0).copy()
     v = _f64(vel0).copy()
 
@@ -320,4 +321,35 @@ def leapfrog_frozen(pos0, vel0, trees, G, eps, rcut, dt, steps):
         x = x + v * dt
         a = force(trees[s + 1])
         v = v + a * (0.5 * dt)
-    return x, v
+    return x, v, a
+
+
+def leapfrog_adjoint(pos0, vel0, trees, G, eps, rcut, dt, steps, g_xT, g_vT, g_aT):
+    """Reverse-mode derivative of leapfrog_frozen: given dL/dx_T, dL/dv_T and
+    dL/da_T returns (dL/dx_0, dL/dv_0).  Each step v_h = v + a dt/2,
+    x1 = x + v_h dt, a1 = F(x1), v1 = v_h + a1 dt/2 is reversed as
+    g_a1 += (dt/2) g_v1; g_x1 += VJP_F(x1)[g_a1]; g_vh = g_v1 + dt g_x1;
+    g_a = (dt/2) g_vh, with VJP_F the list adjoint of each frozen tree."""
+    xs = [_f64(pos0).copy()]
+    x = xs[0]
+    v = _f64(vel0).copy()
+    trees[0].refresh(x)
+    a = trees[0].list_forces(G, eps, rcut)
+    for s in range(steps):
+        v = v + a * (0.5 * dt)
+        x = x + v * dt
+        xs.append(x)
+        trees[s + 1].refresh(x)
+        a = trees[s + 1].list_forces(G, eps, rcut)
+        v = v + a * (0.5 * dt)
+    gx, gv, ga = _f64(g_xT).copy(), _f64(g_vT).copy(), _f64(g_aT).copy()
+    for s in range(steps, 0, -1):
+        ga = ga + 0.5 * dt * gv
+        trees[s].refresh(xs[s])
+        gx = gx + trees[s].list_vjp(G, eps, rcut, ga)
+        gvh = gv + dt * gx
+        ga = 0.5 * dt * gvh
+        gv = gvh
+    trees[0].refresh(xs[0])
+    gx = gx + trees[0].list_vjp(G, eps, rcut, ga)
+    return gx, gv

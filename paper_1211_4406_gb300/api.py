@@ -209,3 +209,34 @@ def measure_peak(kind: str, stream=None) -> float:
 
 def launch_count() -> int:
     return int(_lib.load().tp_launch_count())
+
+
+class CapturedStep:
+    """One whole hot-path step -- rebuild, force, adjoint -- captured once in
+    a CUDA graph and replayed with a single launch.  `pos` (and `mass`,
+    `cot`) are read in place at every replay; `acc` and `grad` are written.
+    The tree keeps the capacities of its allocating build: check
+    tree.status() after replays whose particles moved far."""
+
+    def __init__(self, tree: ShortRangeTree, pos: torch.Tensor, mass, cot: torch.Tensor,
+                 acc: torch.Tensor, grad: torch.Tensor, with_vjp: bool = True):
+        self.tree, self.pos, self.mass, self.cot, self.acc, self.grad = tree, pos, mass, cot, acc, grad
+        self.with_vjp = with_vjp
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._body()                       # warm-up outside the capture
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self._body()
+
+    def _body(self):
+        self.tree.rebuild(self.pos, self.mass)
+        self.tree.force(self.acc)
+        if self.with_vjp:
+            self.tree.vjp(self.cot, self.grad)
+
+    def replay(self):
+        self.graph.replay()

@@ -18,6 +18,8 @@ void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaSt
 void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_write(TreeDev &T, cudaStream_t s);
+void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
+               void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
                       cudaStream_t s);
@@ -134,7 +136,10 @@ struct tp_tree {
     uint32_t *flag = nullptr, *gofs = nullptr;
     uint32_t *nch = nullptr, *nofs = nullptr;
     int32_t *queue = nullptr;
-    int32_t *order = nullptr;
+    int32_t *order = nullptr;         // groups in LPT order for the work queue
+    uint64_t *lpt_key = nullptr, *lpt_key2 = nullptr;
+    uint32_t *lpt_val2 = nullptr;
+    void *lpt_tmp = nullptr;
     double *gs = nullptr, *ncot = nullptr;
     unsigned long long *d_inter = nullptr;
     int32_t *d_maxnj = nullptr;
@@ -190,7 +195,11 @@ static bool alloc_groups(tp_tree *t, int64_t cap)
     D.lcnt = P.get<int32_t>(c);
     D.icnt = P.get<int32_t>(c);
     D.ioff = P.get<int64_t>(c);
-    t->order = P.get<int32_t>(c);
+    t->lpt_key = P.get<uint64_t>(c);
+    t->lpt_key2 = P.get<uint64_t>(c);
+    t->order = reinterpret_cast<int32_t *>(P.get<uint32_t>(c));
+    t->lpt_val2 = P.get<uint32_t>(c);
+    t->lpt_tmp = P.get<char>(tp::radix_tmp_bytes(cap));
     return P.ok;
 }
 
@@ -310,6 +319,8 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     }
     TP_LAUNCH(k_check_entries, 1, 1, 0, s, D);
     tp::walk_write(D, s);
+    tp::lpt_order(D, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
+                  t->lpt_tmp, s);
     return TP_OK;
 }
 
@@ -421,7 +432,7 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
     if (t->n == 0) return TP_OK;
     if (t->precision == TP_FP32) {
         cudaMemsetAsync(acc, 0, sizeof(float) * 3 * (size_t)t->n, s);
-        tp::pair_forward_f32(t->D, (float *)acc, t->queue, nullptr, t->D.cap_groups, s);
+        tp::pair_forward_f32(t->D, (float *)acc, t->queue, t->order, t->D.cap_groups, s);
     } else {
         cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)t->n, s);
         tp::pair_forward_f64(t->D, (double *)acc, t->D.cap_groups, s);
@@ -437,9 +448,9 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
     t->last = s;
     if (t->n == 0) return TP_OK;
     if (t->precision == TP_FP32)
-        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, nullptr, t->D.cap_groups, s);
+        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
     else
-        tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, t->queue, nullptr, t->D.cap_groups, s);
+        tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
     return cuda_status(cudaGetLastError());
 }
 

@@ -656,9 +656,12 @@ static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double 
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
     if (G > 0) {
         cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
-        int64_t grid = (int64_t)num_sms() * (nb > 0 ? nb : 1);
+        static int nb = 0;                 // occupancy is queried once, outside any capture
+        if (nb == 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
+            if (nb <= 0) nb = 1;
+        }
+        int64_t grid = (int64_t)num_sms() * nb;
         if (grid > G) grid = G;
         auto k = k_vjp<R>;
         TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, cot, gs, ncot, queue, order);

@@ -234,6 +234,23 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T)
     if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
 }
 
+// LPT keys for the persistent work queue: groups in descending order of their
+// pair count n_i * n_j (ties by group index, the sort is stable).
+__global__ void k_lpt_keys(TreeDev T, uint64_t *key, uint32_t *val)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < T.cap_groups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t cost = 0;
+        if (g < G) {
+            cost = (uint64_t)T.gcount[g] * (uint64_t)T.lcnt[g];
+            if (cost > 0xffffffffull) cost = 0xffffffffull;
+        }
+        key[g] = g < G ? 0xffffffffull - cost : 0xffffffffull + 1;   // padding sorts last
+        val[g] = (uint32_t)g;
+    }
+}
+
 // Per-group list offsets and counts from the item positions.
 __global__ void k_list_offsets(TreeDev T)
 {
@@ -297,6 +314,15 @@ void walk_write(TreeDev &T, cudaStream_t s)
 {
     if (T.cap_items <= 0) return;
     TP_LAUNCH(k_walk_task<true>, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
+}
+
+// order[] = groups by descending cost; key/val/key2/val2 hold cap_groups each.
+void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
+               void *radix_tmp, cudaStream_t s)
+{
+    if (T.cap_groups <= 0) return;
+    TP_LAUNCH(k_lpt_keys, grid_for(T.cap_groups, 256), 256, 0, s, T, key, val);
+    radix_sort(key, val, key2, val2, T.cap_groups, 40, nullptr, 1, radix_tmp, s);
 }
 
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s)

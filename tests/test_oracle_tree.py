@@ -307,3 +307,25 @@ def test_group_ranges_partition_the_sums():
     gfull = t.list_vjp(G, eps, rc, w)
     gparts = t.list_vjp_range(0, cut, G, eps, rc, w) + t.list_vjp_range(cut, ng, G, eps, rc, w)
     assert np.allclose(gfull, gparts, rtol=1e-12, atol=1e-12 * np.abs(gfull).max())
+
+
+def test_leapfrog_adjoint_matches_frozen_central_differences():
+    pos, mass = inputs.clustered_box(2000, 10, 51)
+    G, eps, rc, theta, dt, steps = 1.0, 2e-3, 0.09, 0.5, 1e-3, 4
+    v0 = np.zeros_like(pos)
+    w = inputs.cotangent(2000, 52).astype(np.float64)
+    _, _, _, trees = oracle.leapfrog(pos, v0, mass, G, eps, rc, theta, dt, steps, keep_trees=True)
+    gx, _ = oracle.leapfrog_adjoint(pos, v0, trees, G, eps, rc, dt, steps,
+                                    np.zeros_like(pos), np.zeros_like(pos), w)
+    rms = np.sqrt(np.mean(gx ** 2))
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        k, c = rng.integers(2000), rng.integers(3)
+        h = 1e-3 * eps
+        p, m = pos.copy(), pos.copy()
+        p[k, c] += h
+        m[k, c] -= h
+        lp = np.sum(w * oracle.leapfrog_frozen(p, v0, trees, G, eps, rc, dt, steps)[2])
+        lm = np.sum(w * oracle.leapfrog_frozen(m, v0, trees, G, eps, rc, dt, steps)[2])
+        fd = (lp - lm) / (2 * h)
+        assert abs(gx[k, c] - fd) <= 1e-6 * max(abs(fd), rms)
