@@ -146,6 +146,30 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
 
 tp_status tp_tree_free(tp_tree *t);
 
+/* Largest particle count tp_short_range_force_noalloc accepts.              */
+#define TP_NOALLOC_MAX_N 65536
+
+/* Short-range accelerations of one small box without allocating device
+ * memory.  This entry point has no counterpart in the paper: it exists for
+ * callers that must not let a library call cudaMalloc -- an application whose
+ * device memory is carved from its own pool, or a latency-critical loop that
+ * cannot afford an allocation's implicit synchronisation.  Its scratch (the
+ * particles' fixed-point images and masses, 28 bytes per particle) is one
+ * statically sized device array of TP_NOALLOC_MAX_N entries (1.8 MB), which
+ * every GPU that loads the library holds until the process exits.
+ *   pos   device FP64 [n][3], finite; mass device FP64 [n] or NULL (1/n)
+ *   n     0 <= n <= TP_NOALLOC_MAX_N, else TP_ERR_INVALID_ARG
+ *   p     host; precision must be TP_FP32; theta, n_crit and n_leaf are not
+ *         used: the sum runs over all pairs (Eq. 2 with Eq. 3, exact cutoff)
+ *   acc   device FP32 [n][3], input order, overwritten
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call rewrites the scratch it reads, so nothing needs
+ * clearing, but all calls share the one array: calls that overlap on the GPU
+ * (on different streams, or from different threads) race.  Asynchronous.     */
+tp_status tp_short_range_force_noalloc(const double *pos, const double *mass, int64_t n,
+                                       const tp_params *p, float *acc, void *stream);
+
 /* Leapfrog helpers for the kick-drift-kick integrator (y += a * x):
  * y: device double [n]; x: device [n], float when x_is_f32 else double.     */
 tp_status tp_axpy(double *y, const void *x, int32_t x_is_f32, double a, int64_t n,

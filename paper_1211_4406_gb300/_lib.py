@@ -61,6 +61,7 @@ SIGNATURES = {
     "tp_axpy": ([_V, _V, _I32, _D, _I64, _V], C.c_int),
     "tp_scale": ([_V, _I32, _V, _D, _I64, _V], C.c_int),
     "tp_measure_peak": ([_I32, C.POINTER(_D), _V], C.c_int),
+    "tp_short_range_force_noalloc": ([_V, _V, _I64, C.POINTER(TPParams), _V, _V], C.c_int),
     "tp_launch_count": ([], _I64),
     "tp_status_string": ([C.c_int], C.c_char_p),
 }
