@@ -377,7 +377,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.n_items = B.get<int64_t>(1);
     D.n_ambig = B.get<unsigned long long>(1);
     D.status = B.get<int32_t>(1);
-    t->queue = B.get<int32_t>(1);
+    t->queue = B.get<int32_t>(4);
     t->gs = B.get<double>(3 * nn);
     t->d_inter = B.get<unsigned long long>(1);
     t->d_maxnj = B.get<int32_t>(1);
