@@ -17,6 +17,7 @@ void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_t
 void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s);
 void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
+void walk_expand(TreeDev &T, void *scan_tmp, cudaStream_t s);
 void walk_write(TreeDev &T, cudaStream_t s);
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
@@ -126,7 +127,7 @@ struct tp_tree {
     std::vector<tp_params> prm;
     cudaStream_t last = nullptr;
     // allocations: base (particles, workspace), nodes, groups, walk items, lists
-    Pool base, nodes, groups, items, lists;
+    Pool base, nodes, groups, items, pad, lists;
     int32_t split = 128;              // largest subtree a single walk task expands
     TreeDev D;
     // scratch
@@ -144,7 +145,7 @@ struct tp_tree {
     unsigned long long *d_inter = nullptr;
     int32_t *d_maxnj = nullptr;
     // host copies of the sizes (valid after a synchronising build)
-    int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_entries = 0;
+    int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_pad = 0, h_entries = 0;
 };
 
 static tp_status cuda_status(cudaError_t e)
@@ -212,6 +213,17 @@ static bool alloc_items(tp_tree *t, int64_t cap)
     size_t c = (size_t)cap;
     D.item = P.get<int32_t>(c); D.igrp = P.get<int32_t>(c); D.icnt2 = P.get<int32_t>(c);
     D.ipos = P.get<int64_t>(c);
+    D.ibpos = P.get<int64_t>(c);
+    D.ibound = P.get<int32_t>(c);
+    return P.ok;
+}
+
+static bool alloc_pad(tp_tree *t, int64_t cap)
+{
+    Pool &P = t->pad;
+    P.release();
+    t->D.cap_pad = cap;
+    t->D.pent = P.get<int32_t>((size_t)cap);
     return P.ok;
 }
 
@@ -255,6 +267,11 @@ __global__ void k_clamp_groups(TreeDev T)
 __global__ void k_check_items(TreeDev T)
 {
     if (*T.n_items > T.cap_items) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+}
+
+__global__ void k_check_pad(TreeDev T)
+{
+    if (*T.n_pad > T.cap_pad) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
 }
 
 __global__ void k_check_entries(TreeDev T)
@@ -308,6 +325,17 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     }
     TP_LAUNCH(k_check_items, 1, 1, 0, s, D);
     tp::walk_items(D, t->split, t->scan_tmp, s);
+    if (sync) {
+        tp_status e = cuda_status(cudaMemcpyAsync(&t->h_pad, D.n_pad, sizeof(int64_t),
+                                                  cudaMemcpyDeviceToHost, s));
+        if (e == TP_OK) e = cuda_status(cudaStreamSynchronize(s));
+        if (e != TP_OK) return e;
+        if (t->h_pad > D.cap_pad || D.pent == nullptr) {
+            if (!alloc_pad(t, t->h_pad + t->h_pad / 4 + 1024)) return TP_ERR_OOM;
+        }
+    }
+    TP_LAUNCH(k_check_pad, 1, 1, 0, s, D);
+    tp::walk_expand(D, t->scan_tmp, s);
     if (sync) {
         tp_status e = cuda_status(cudaMemcpyAsync(&t->h_entries, D.n_entries, sizeof(int64_t),
                                                   cudaMemcpyDeviceToHost, s));
@@ -375,6 +403,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.lstart = B.get<int64_t>(TP_NLEVELS + 1); D.lcount = B.get<int64_t>(TP_NLEVELS + 1);
     D.n_nodes = B.get<int64_t>(1); D.n_groups = B.get<int64_t>(1); D.n_entries = B.get<int64_t>(1);
     D.n_items = B.get<int64_t>(1);
+    D.n_pad = B.get<int64_t>(1);
     D.n_ambig = B.get<unsigned long long>(1);
     D.status = B.get<int32_t>(1);
     t->queue = B.get<int32_t>(4);
@@ -416,7 +445,7 @@ tp_status tp_rebuild_tree(tp_tree *t, const double *pos, const double *mass, voi
     if (!t) return TP_ERR_INVALID_ARG;
     if (t->n > 0 && !is_device_ptr(pos)) return TP_ERR_INVALID_ARG;
     if (mass && !is_device_ptr(mass)) return TP_ERR_INVALID_ARG;
-    if (!t->D.gfirst || !t->D.ent || !t->D.item) return TP_ERR_INVALID_ARG;
+    if (!t->D.gfirst || !t->D.ent || !t->D.item || !t->D.pent) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     t->last = s;
     tp_status e = run_build(t, pos, mass, s, false);
@@ -579,6 +608,7 @@ tp_status tp_tree_free(tp_tree *t)
     if (t->last) cudaStreamSynchronize(t->last);
     else cudaDeviceSynchronize();
     t->lists.release();
+    t->pad.release();
     t->items.release();
     t->groups.release();
     t->nodes.release();

@@ -85,6 +85,11 @@ struct TreeDev {
     int64_t *n_items;                 // device scalar
     int32_t *item, *igrp, *icnt2;     // [cap_items] item, its group, its entry count
     int64_t *ipos;                    // [cap_items] first entry of each item
+    int64_t *ibpos;                   // [cap_items] first slot of each item in the padded buffer
+    int32_t *ibound;                  // [cap_items] slot count: the task node's particle count
+    int64_t cap_pad;
+    int32_t *pent;                    // [cap_pad] entries of each item before compaction
+    int64_t *n_pad;                   // device scalar
     // lists
     int64_t *loff;                    // [cap_groups + 1]
     int32_t *lcnt;                    // [cap_groups]

@@ -311,47 +311,6 @@ __device__ __forceinline__ f2 nonzero_mask(f2 r2)
     return f2pack(fminf(a, 1.f), fminf(b, 1.f));
 }
 
-// Adjoint, i side: per pair alpha = m phi, beta = m psi (d.w_i); the thread's
-// particle accumulates A = sum alpha and B = sum beta d over entry pairs.
-__device__ __forceinline__ void vjp_i_tile_packed(const JTile<float> &J, int st, int npairs, int ns, float xi,
-                                                  float yi, float zi, float wx, float wy, float wz, float eps2,
-                                                  float &As, float &Bxs, float &Bys, float &Bzs)
-{
-    const f2 X = f2pack(xi, xi), Y = f2pack(yi, yi), Z = f2pack(zi, zi);
-    const f2 WX = f2pack(wx, wx), WY = f2pack(wy, wy), WZ = f2pack(wz, wz);
-    const f2 E2 = f2pack(eps2, eps2), THREE = f2pack(3.f, 3.f);
-    f2 A = f2pack(0.f, 0.f), Bx = A, By = A, Bz = A;
-    for (int p = st; p < npairs; p += ns) {
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&J.p.A[p]);
-        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&J.p.B[p]);
-        const f2 dx = f2sub(a.x, X), dy = f2sub(a.y, Y), dz = f2sub(b.x, Z);
-        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-        float r2a, r2b, s2a, s2b;
-        f2unpack(r2, r2a, r2b);
-        f2unpack(f2add(r2, E2), s2a, s2b);
-        const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-        const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
-        f2 g, gp;
-        g_gpx_packed(x, g, gp);
-        const f2 ri2 = f2mul(ri, ri), ri3 = f2mul(ri2, ri);
-        const f2 phi = f2mul(g, ri3);
-        const f2 psi = f2fma(f2mul(THREE, phi), f2mul(f2pack(-1.f, -1.f), ri2), f2mul(gp, ri3));
-        const f2 m = f2mul(b.y, nonzero_mask(r2));
-        const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
-        const f2 alpha = f2mul(m, phi);
-        const f2 beta = f2mul(f2mul(m, psi), dw);
-        A = f2add(A, alpha);
-        Bx = f2fma(beta, dx, Bx);
-        By = f2fma(beta, dy, By);
-        Bz = f2fma(beta, dz, Bz);
-    }
-    float l, h;
-    f2unpack(A, l, h); As += l + h;
-    f2unpack(Bx, l, h); Bxs += l + h;
-    f2unpack(By, l, h); Bys += l + h;
-    f2unpack(Bz, l, h); Bzs += l + h;
-}
-
 template <class R>
 __device__ __forceinline__ R scale_of(const BoxPrm &P);
 template <> __device__ __forceinline__ float scale_of<float>(const BoxPrm &P) { return P.scale; }
@@ -533,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
         const int64_t g = order ? order[item] : item;
         const Group G = load_group(T, g);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
-        if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_vjp_i / k_vjp_j take these
+        if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_vjp_fused takes these
         const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
         const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
@@ -633,86 +592,30 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
     }
 }
 
-// Adjoint, i side (FP32 packed, ordinary groups with eps > 0): the layout of
-// the forward kernel; dL/dx_i -= G k^3 (A_i w_i + B_i).
-__global__ void __launch_bounds__(kThreads) k_vjp_i(TreeDev T, const float *cot, double *gs, int32_t *queue,
-                                                    const int32_t *order)
+// Adjoint for ordinary groups with eps > 0 (FP32, packed): threads hold list
+// entries and loop over the group's particles two at a time, staged as
+// A = {x0, x1, y0, y1}, B = {z0, z1, wx0, wx1}, C = {wy0, wy1, wz0, wz1}.  Each
+// pair's alpha = m phi and beta = m psi (d.w_i) are computed once: the entry
+// sums its side, v = sum_i (alpha w_i + beta d), in registers; the particle
+// side, A_i = sum alpha and B_i = sum beta d, is a butterfly over the warp's
+// entries per particle pair, written to the warp's row and summed in FP64 by
+// the thread that owns the particle.
+__global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
+                                                        int32_t *queue, const int32_t *order)
 {
-    __shared__ JTile<float> J;
-    __shared__ double red[4][kThreads];
+    constexpr int kWarps = kThreads / 32;
+    __shared__ float4 IA[kThreads / 2], IB[kThreads / 2], IC[kThreads / 2];
+    __shared__ float part[kWarps][4][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
          item = next_item<true>(queue, item, &s_item)) {
         const int64_t g = order ? order[item] : item;
         const Group G = load_group(T, g);
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
-        const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
-        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
-            const int nic = min(kThreads, G.ni - i0);
-            const int ns = kThreads / nic;
-            const int slot = threadIdx.x;
-            const bool active = slot < nic * ns;
-            const int il = active ? slot % nic : 0, st = active ? slot / nic : 0;
-            const int32_t p = G.first + i0 + il;
-            const float xi = Arith<float>::from_fixed(T.X[p], G.X, sc);
-            const float yi = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
-            const float zi = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
-            const int64_t o = T.perm[p];
-            const float wx = cot[3 * o], wy = cot[3 * o + 1], wz = cot[3 * o + 2];
-            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;
-            const int ne = bad ? 0 : G.ne;
-            for (int t0 = 0; t0 < ne; t0 += kTile) {
-                const int nt = min(kTile, ne - t0);
-                __syncthreads();
-                for (int q = threadIdx.x; q < nt; q += kThreads)
-                    stage_entry_packed(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
-                if ((nt & 1) && threadIdx.x == 0) stage_pad_packed(J, nt);
-                __syncthreads();
-                if (active) {
-                    float A = 0.f, Bx = 0.f, By = 0.f, Bz = 0.f;
-                    vjp_i_tile_packed(J, st, (nt + 1) >> 1, ns, xi, yi, zi, wx, wy, wz, eps2, A, Bx, By, Bz);
-                    sA += A; sBx += Bx; sBy += By; sBz += Bz;
-                }
-            }
-            red[0][slot] = sA; red[1][slot] = sBx; red[2][slot] = sBy; red[3][slot] = sBz;
-            __syncthreads();
-            if (slot < nic) {
-                double A = 0, Bx = 0, By = 0, Bz = 0;
-                for (int s2 = 0; s2 < ns; s2++) {
-                    A += red[0][s2 * nic + slot]; Bx += red[1][s2 * nic + slot];
-                    By += red[2][s2 * nic + slot]; Bz += red[3][s2 * nic + slot];
-                }
-                const int32_t pp = G.first + i0 + slot;
-                const int64_t oo = T.perm[pp];
-                atomicAdd(gs + 3 * (int64_t)pp, -gk3 * (A * (double)cot[3 * oo] + Bx));
-                atomicAdd(gs + 3 * (int64_t)pp + 1, -gk3 * (A * (double)cot[3 * oo + 1] + By));
-                atomicAdd(gs + 3 * (int64_t)pp + 2, -gk3 * (A * (double)cot[3 * oo + 2] + Bz));
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// Adjoint, j side (FP32 packed): threads hold entries, the group's particles
-// are staged in pairs, A = {x0, x1, y0, y1}, B = {z0, z1, wx0, wx1},
-// C = {wy0, wy1, wz0, wz1}; each entry sums v = alpha w_i + beta d over the
-// group in registers and adds G k^3 v to its particle or node cotangent.
-__global__ void __launch_bounds__(kThreads) k_vjp_j(TreeDev T, const float *cot, double *gs, double *ncot,
-                                                    int32_t *queue, const int32_t *order)
-{
-    __shared__ float4 IA[kThreads / 2], IB[kThreads / 2], IC[kThreads / 2];
-    __shared__ int s_item;
-    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
-    const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
-    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
-         item = next_item<true>(queue, item, &s_item)) {
-        const int64_t g = order ? order[item] : item;
-        const Group G = load_group(T, g);
-        const float sc = G.P->scale, eps2 = G.P->eps2s;
-        if (G.wrap || !(eps2 > 0.f)) continue;
         const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
         const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
@@ -736,18 +639,22 @@ __global__ void __launch_bounds__(kThreads) k_vjp_j(TreeDev T, const float *cot,
                     B[2 + l] = 0.f; Cc[l] = 0.f; Cc[2 + l] = 0.f;
                 }
             }
+            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;
             __syncthreads();
             for (int t0 = 0; t0 < ne; t0 += kThreads) {
                 const int q = t0 + threadIdx.x;
-                if (q >= ne) break;
-                const int32_t e = T.ent[G.e0 + q];
-                uint64_t ex, ey, ez;
-                float mj;
-                if (e >= 0) {
-                    ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = (float)T.m[e];
-                } else {
-                    const int32_t nd = -e - 1;
-                    ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = (float)T.M[nd];
+                const bool valid = q < ne;
+                int32_t e = 0;
+                uint64_t ex = G.X, ey = G.Y, ez = G.Z;
+                float mj = 0.f;
+                if (valid) {
+                    e = T.ent[G.e0 + q];
+                    if (e >= 0) {
+                        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = (float)T.m[e];
+                    } else {
+                        const int32_t nd = -e - 1;
+                        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = (float)T.M[nd];
+                    }
                 }
                 const float xj = Arith<float>::from_fixed(ex, G.X, sc), yj = Arith<float>::from_fixed(ey, G.Y, sc),
                             zj = Arith<float>::from_fixed(ez, G.Z, sc);
@@ -773,17 +680,50 @@ __global__ void __launch_bounds__(kThreads) k_vjp_j(TreeDev T, const float *cot,
                     const f2 psi = f2fma(f2mul(THREE, phi), f2mul(f2pack(-1.f, -1.f), ri2), f2mul(gp, ri3));
                     const f2 m = f2mul(MJ, nonzero_mask(r2));
                     const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
-                    const f2 alpha = f2mul(m, phi);
+                    f2 alpha = f2mul(m, phi);
                     const f2 beta = f2mul(f2mul(m, psi), dw);
                     vx = f2fma(beta, dx, f2fma(alpha, WX, vx));
                     vy = f2fma(beta, dy, f2fma(alpha, WY, vy));
                     vz = f2fma(beta, dz, f2fma(alpha, WZ, vz));
+                    f2 bx = f2mul(beta, dx), by = f2mul(beta, dy), bz = f2mul(beta, dz);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        alpha = f2add(alpha, __shfl_xor_sync(0xffffffffu, alpha, off));
+                        bx = f2add(bx, __shfl_xor_sync(0xffffffffu, bx, off));
+                        by = f2add(by, __shfl_xor_sync(0xffffffffu, by, off));
+                        bz = f2add(bz, __shfl_xor_sync(0xffffffffu, bz, off));
+                    }
+                    if (lane == 0) {
+                        float lo, hi;
+                        f2unpack(alpha, lo, hi); part[warp][0][2 * pp] = lo; part[warp][0][2 * pp + 1] = hi;
+                        f2unpack(bx, lo, hi); part[warp][1][2 * pp] = lo; part[warp][1][2 * pp + 1] = hi;
+                        f2unpack(by, lo, hi); part[warp][2][2 * pp] = lo; part[warp][2][2 * pp + 1] = hi;
+                        f2unpack(bz, lo, hi); part[warp][3][2 * pp] = lo; part[warp][3][2 * pp + 1] = hi;
+                    }
                 }
-                float l, h;
-                double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
-                f2unpack(vx, l, h); atomicAdd(dst, gk3 * ((double)l + (double)h));
-                f2unpack(vy, l, h); atomicAdd(dst + 1, gk3 * ((double)l + (double)h));
-                f2unpack(vz, l, h); atomicAdd(dst + 2, gk3 * ((double)l + (double)h));
+                if (valid) {
+                    float l, h;
+                    double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
+                    f2unpack(vx, l, h); atomicAdd(dst, gk3 * ((double)l + (double)h));
+                    f2unpack(vy, l, h); atomicAdd(dst + 1, gk3 * ((double)l + (double)h));
+                    f2unpack(vz, l, h); atomicAdd(dst + 2, gk3 * ((double)l + (double)h));
+                }
+                __syncthreads();
+                if (threadIdx.x < nic) {
+                    const int nw = (min(kThreads, ne - t0) + 31) >> 5;   // warps that held entries
+                    for (int w = 0; w < nw; w++) {
+                        sA += (double)part[w][0][threadIdx.x]; sBx += (double)part[w][1][threadIdx.x];
+                        sBy += (double)part[w][2][threadIdx.x]; sBz += (double)part[w][3][threadIdx.x];
+                    }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x < nic) {
+                const int32_t p = G.first + i0 + threadIdx.x;
+                const int64_t o = T.perm[p];
+                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)cot[3 * o] + sBx));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)cot[3 * o + 1] + sBy));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)cot[3 * o + 2] + sBz));
             }
         }
     }
@@ -884,21 +824,19 @@ static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double 
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
     if (G > 0) {
         // occupancies are queried once, outside any capture
-        static int nb = 0, nbi = 0, nbj = 0;
+        static int nb = 0, nbf = 0;
         if (nb == 0) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbi, k_vjp_i, kThreads, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbj, k_vjp_j, kThreads, 0);
-            nb = nb > 0 ? nb : 1; nbi = nbi > 0 ? nbi : 1; nbj = nbj > 0 ? nbj : 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, k_vjp_fused, kThreads, 0);
+            nb = nb > 0 ? nb : 1; nbf = nbf > 0 ? nbf : 1;
         }
         auto grid_of = [&](int per_sm) {
             int64_t gr = (int64_t)num_sms() * per_sm;
             return (int)(gr > G ? G : gr);
         };
         if (sizeof(R) == 4) {
-            cudaMemsetAsync(queue, 0, 3 * sizeof(int32_t), s);
-            TP_LAUNCH(k_vjp_i, grid_of(nbi), kThreads, 0, s, T, (const float *)cot, gs, queue + 1, order);
-            TP_LAUNCH(k_vjp_j, grid_of(nbj), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 2,
+            cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+            TP_LAUNCH(k_vjp_fused, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1,
                       order);
         } else {
             cudaMemsetAsync(queue, 0, sizeof(int32_t), s);

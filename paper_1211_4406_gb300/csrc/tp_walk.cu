@@ -205,33 +205,56 @@ __global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
     if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
 }
 
-// Expansion of every item: entry counts (WRITE = false) or entries.
-template <bool WRITE>
+// Slots per item: a task expands to at most one entry per particle of its
+// subtree (every entry covers at least one distinct particle), a monopole item
+// to one entry.
+__global__ void k_item_bounds(TreeDev T)
+{
+    const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < NI;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = T.item[it];
+        T.ibound[it] = v < 0 ? 1 : T.wn[v].count;
+    }
+}
+
+// Expansion of every item into its padded slots; records the entry count.
 __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
-    if (WRITE && *T.status == TP_ERR_LIST_OVERFLOW) return;
+    if (*T.n_pad > T.cap_pad || *T.status == TP_ERR_LIST_OVERFLOW) return;
     unsigned long long ambig = 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < NI;
          it += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = T.item[it];
+        int32_t *out = T.pent + T.ibpos[it];
         if (v < 0) {                                  // an accepted monopole
-            if (!WRITE) T.icnt2[it] = 1;
-            else if (T.ipos[it] < T.cap_entries) T.ent[T.ipos[it]] = v;
+            out[0] = v;
+            T.icnt2[it] = 1;
             continue;
         }
         const WalkGroup W = load_walk_group(T, T.igrp[it]);
-        const int32_t end = T.wn[v].skip;
-        if (!WRITE) {
-            T.icnt2[it] = walk_dfs<kTask>(T, W, v, end, 0, nullptr, 0, ambig);
-        } else {
-            const int64_t o = T.ipos[it];
-            const int64_t n = T.icnt2[it];
-            if (o + n > T.cap_entries) continue;
-            walk_dfs<kTask>(T, W, v, end, 0, T.ent + o, n, ambig);
-        }
+        const int32_t n = walk_dfs<kTask>(T, W, v, T.wn[v].skip, 0, out, T.ibound[it], ambig);
+        if (n > T.ibound[it]) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+        T.icnt2[it] = n;
     }
-    if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
+    if (ambig) atomicAdd(T.n_ambig, ambig);
+}
+
+// Compaction of the padded slots into the lists: one warp per item.
+__global__ void k_compact(TreeDev T)
+{
+    const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
+    if (*T.n_entries > T.cap_entries || *T.status == TP_ERR_LIST_OVERFLOW) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = w0; it < NI; it += nw) {
+        const int32_t *src = T.pent + T.ibpos[it];
+        int32_t *dst = T.ent + T.ipos[it];
+        const int32_t n = T.icnt2[it];
+        for (int32_t k = lane; k < n; k += 32) dst[k] = src[k];
+    }
 }
 
 // LPT keys for the persistent work queue: groups in descending order of their
@@ -300,12 +323,20 @@ void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
     scan_i32_to_i64(T.icnt, T.ioff, 0, T.n_groups, T.n_items, scan_tmp, s);
 }
 
-// Items, their entry counts, and their positions (scan) -> *T.n_entries.
+// Items and their padded slot positions (scan) -> *T.n_pad.
 void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 {
     if (T.cap_groups <= 0 || T.cap_items <= 0) return;
     TP_LAUNCH(k_walk_top<true>, grid_for(T.cap_groups, kBlock), kBlock, 0, s, T, split);
-    TP_LAUNCH(k_walk_task<false>, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
+    TP_LAUNCH(k_item_bounds, grid_for(T.cap_items, 256), 256, 0, s, T);
+    scan_i32_to_i64(T.ibound, T.ibpos, 0, T.n_items, T.n_pad, scan_tmp, s);
+}
+
+// Task expansion into the padded slots, entry positions (scan) -> *T.n_entries.
+void walk_expand(TreeDev &T, void *scan_tmp, cudaStream_t s)
+{
+    if (T.cap_items <= 0) return;
+    TP_LAUNCH(k_walk_task, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
     scan_i32_to_i64(T.icnt2, T.ipos, 0, T.n_items, T.n_entries, scan_tmp, s);
     TP_LAUNCH(k_list_offsets, grid_for(T.cap_groups, 256), 256, 0, s, T);
 }
@@ -313,7 +344,7 @@ void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 void walk_write(TreeDev &T, cudaStream_t s)
 {
     if (T.cap_items <= 0) return;
-    TP_LAUNCH(k_walk_task<true>, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
+    TP_LAUNCH(k_compact, grid_for(32 * T.cap_items, 256), 256, 0, s, T);
 }
 
 // order[] = groups by descending cost; key/val/key2/val2 hold cap_groups each.
