@@ -233,6 +233,7 @@ static bool alloc_lists(tp_tree *t, int64_t cap)
     P.release();
     t->D.cap_entries = cap;
     t->D.ent = P.get<int32_t>((size_t)cap);
+    t->D.rec = P.get<float4>((size_t)cap);
     return P.ok;
 }
 

@@ -6,7 +6,8 @@
 //              level u8, M/S/com/lo/hi/cen/half f64, COM fixed-point u64,
 //              and a 48-byte WNode record the walk streams through
 //   groups     first/count/box i32, centre/half f64, u32 and u64 images
-//   lists      offsets i64 [G+1], entries i32
+//   lists      offsets i64 [G+1], entries i32, entry records float4 (group-
+//              relative scaled offset and mass, written by the walk)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -94,6 +95,8 @@ struct TreeDev {
     int64_t *loff;                    // [cap_groups + 1]
     int32_t *lcnt;                    // [cap_groups]
     int32_t *ent;
+    float4 *rec;                      // [cap_entries] per entry: offset from the group centre
+                                      // scaled by 2/r_cut (FP32 x, y, z) and mass (w)
     int64_t *n_entries;               // device scalar
     unsigned long long *n_ambig;      // device scalar
     int32_t *status;                  // first latched error

@@ -151,9 +151,6 @@ struct JTile {
     union {
         struct { R x[kTile], y[kTile], z[kTile]; } f;
         struct { uint64_t x[kTile], y[kTile], z[kTile]; } u;
-        // packed layout: entries 2p and 2p+1 share A[p] = {x0, x1, y0, y1} and
-        // B[p] = {z0, z1, m0, m1}, so two 128-bit loads feed two pairs
-        struct { float4 A[kTile / 2], B[kTile / 2]; } p;
     };
     R m[kTile];
 };
@@ -202,44 +199,15 @@ __device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPar
     }
 }
 
-__device__ __forceinline__ void stage_entry_packed(const TreeDev &T, const Group &G, int32_t e, float sc,
-                                                   JTile<float> &J, int q)
-{
-    uint64_t ex, ey, ez;
-    double mj;
-    if (e >= 0) {
-        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = T.m[e];
-    } else {
-        const int32_t nd = -e - 1;
-        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = T.M[nd];
-    }
-    float *A = reinterpret_cast<float *>(&J.p.A[q >> 1]);
-    float *B = reinterpret_cast<float *>(&J.p.B[q >> 1]);
-    const int l = q & 1;
-    A[l] = Arith<float>::from_fixed(ex, G.X, sc);
-    A[2 + l] = Arith<float>::from_fixed(ey, G.Y, sc);
-    B[l] = Arith<float>::from_fixed(ez, G.Z, sc);
-    B[2 + l] = (float)mj;
-}
-
-// Odd tiles get a partner entry of zero mass far outside the cutoff.
-__device__ __forceinline__ void stage_pad_packed(JTile<float> &J, int q)
-{
-    float *A = reinterpret_cast<float *>(&J.p.A[q >> 1]);
-    float *B = reinterpret_cast<float *>(&J.p.B[q >> 1]);
-    const int l = q & 1;
-    A[l] = 1.0e4f; A[2 + l] = 1.0e4f; B[l] = 1.0e4f; B[2 + l] = 0.f;
-}
-
 // Two pairs per step, packed.  Eq. 3 as g = u^5 h(xi) + v^6 c(xi) with
 // u = max(0, 2 - xi), v = max(0, 1 - xi), h = (7 xi^3 + 22 xi^2 + 10 xi + 4)/140
 // and c = (7 xi^2 + 18 xi + 3)/35: on [1,2] the first term alone is Eq. 3's
 // factored form, on [0,1] the second adds Eq. 3's difference between its two
 // branches, (1 - xi)^6 c(xi).  Both terms are non-negative (no cancellation in
 // FP32) and u = 0 makes g vanish exactly at and beyond the cutoff.
-__device__ __forceinline__ void force_tile_packed(const JTile<float> &J, int st, int npairs, int ns, float xi,
-                                                  float yi, float zi, float eps2, float &axs, float &ays,
-                                                  float &azs)
+__device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4 *SB, int st, int npairs, int ns,
+                                                  float xi, float yi, float zi, float eps2, float &axs,
+                                                  float &ays, float &azs)
 {
     const f2 X = f2pack(xi, xi), Y = f2pack(yi, yi), Z = f2pack(zi, zi);
     const f2 E2 = f2pack(eps2, eps2), TWO = f2pack(2.f, 2.f), ONE = f2pack(1.f, 1.f);
@@ -250,8 +218,8 @@ __device__ __forceinline__ void force_tile_packed(const JTile<float> &J, int st,
     f2 ax = f2pack(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll 2
     for (int p = st; p < npairs; p += ns) {
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&J.p.A[p]);
-        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&J.p.B[p]);
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&SA[p]);
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&SB[p]);
         const f2 dx = f2sub(a.x, X), dy = f2sub(a.y, Y), dz = f2sub(b.x, Z);
         const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
         float r2a, r2b, s2a, s2b;
@@ -376,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
         const int64_t g = order ? order[item] : item;
         const Group G = load_group(T, g);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
+        if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_pair_packed takes these
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
             const int ns = kThreads / nic;
@@ -394,30 +363,15 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
             // loses ~1e-5 relative; tile-sized partial sums keep it below 1e-6.
             double sax = 0.0, say = 0.0, saz = 0.0;
             const int ne = bad ? 0 : G.ne;
-            // packed FP32 path for ordinary groups with eps > 0; the scalar
-            // path covers box-spanning groups, eps = 0 and FP64
-            const bool packed = sizeof(R) == 4 && !G.wrap && eps2 > R(0);
             for (int t0 = 0; t0 < ne; t0 += kTile) {
                 const int nt = min(kTile, ne - t0);
                 __syncthreads();
-                if (packed) {
-                    for (int q = threadIdx.x; q < nt; q += kThreads)
-                        stage_entry_packed(T, G, T.ent[G.e0 + t0 + q], (float)sc,
-                                           *reinterpret_cast<JTile<float> *>(&J), q);
-                    if ((nt & 1) && threadIdx.x == 0) stage_pad_packed(*reinterpret_cast<JTile<float> *>(&J), nt);
-                } else {
-                    for (int q = threadIdx.x; q < nt; q += kThreads)
-                        stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
-                }
+                for (int q = threadIdx.x; q < nt; q += kThreads)
+                    stage_entry<R>(T, G, T.ent[G.e0 + t0 + q], sc, J, q);
                 __syncthreads();
                 if (active) {
                     R ax = 0, ay = 0, az = 0;
-                    if (packed) {
-                        float fx = 0.f, fy = 0.f, fz = 0.f;
-                        force_tile_packed(*reinterpret_cast<const JTile<float> *>(&J), st, (nt + 1) >> 1, ns,
-                                          (float)I.x, (float)I.y, (float)I.z, (float)eps2, fx, fy, fz);
-                        ax = fx; ay = fy; az = fz;
-                    } else if (G.wrap) {
+                    if (G.wrap) {
                         force_tile<R, true>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
                     } else {
                         force_tile<R, false>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
@@ -438,6 +392,78 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
                 acc[3 * o] = (R)(sxx * G.P->gk2);
                 acc[3 * o + 1] = (R)(syy * G.P->gk2);
                 acc[3 * o + 2] = (R)(szz * G.P->gk2);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The FP32 forward kernel for ordinary groups with eps > 0: packed pair math
+// fed by the walk's entry records (each thread stages one entry pair per tile
+// and loads the next tile's pair while the current one is computed).
+__global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
+                                                          const int32_t *order)
+{
+    __shared__ float4 SA[kTile / 2], SB[kTile / 2];
+    __shared__ double red[3][kThreads];
+    __shared__ int s_item;
+    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
+    const float4 pad = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
+         item = next_item<true>(queue, item, &s_item)) {
+        const int64_t g = order ? order[item] : item;
+        const Group G = load_group(T, g);
+        const float sc = G.P->scale, eps2 = G.P->eps2s;
+        if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
+        const int ne = bad ? 0 : G.ne;
+        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
+            const int nic = min(kThreads, G.ni - i0);
+            const int ns = kThreads / nic;
+            const int slot = threadIdx.x;
+            const bool active = slot < nic * ns;
+            const int il = active ? slot % nic : 0, st = active ? slot / nic : 0;
+            const int32_t p = G.first + i0 + il;
+            const float xi = Arith<float>::from_fixed(T.X[p], G.X, sc);
+            const float yi = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
+            const float zi = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
+            double sax = 0.0, say = 0.0, saz = 0.0;
+            float4 n0 = pad, n1 = pad;
+            if (ne > 0) {
+                const int nt = min(kTile, ne), q = 2 * (int)threadIdx.x;
+                if (q < nt) n0 = T.rec[G.e0 + q];
+                if (q + 1 < nt) n1 = T.rec[G.e0 + q + 1];
+            }
+            for (int t0 = 0; t0 < ne; t0 += kTile) {
+                const int nt = min(kTile, ne - t0);
+                __syncthreads();
+                SA[threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
+                SB[threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
+                __syncthreads();
+                if (t0 + kTile < ne) {
+                    const int t1 = t0 + kTile, nt1 = min(kTile, ne - t1), q = 2 * (int)threadIdx.x;
+                    n0 = q < nt1 ? T.rec[G.e0 + t1 + q] : pad;
+                    n1 = q + 1 < nt1 ? T.rec[G.e0 + t1 + q + 1] : pad;
+                }
+                if (active) {
+                    float ax = 0.f, ay = 0.f, az = 0.f;
+                    force_tile_packed(SA, SB, st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+                    sax += ax; say += ay; saz += az;
+                }
+            }
+            red[0][slot] = sax; red[1][slot] = say; red[2][slot] = saz;
+            __syncthreads();
+            if (slot < nic) {
+                double sxx = 0, syy = 0, szz = 0;
+                for (int s2 = 0; s2 < ns; s2++) {
+                    sxx += red[0][s2 * nic + slot];
+                    syy += red[1][s2 * nic + slot];
+                    szz += red[2][s2 * nic + slot];
+                }
+                const int64_t o = T.perm[G.first + i0 + slot];
+                acc[3 * o] = (float)(sxx * G.P->gk2);
+                acc[3 * o + 1] = (float)(syy * G.P->gk2);
+                acc[3 * o + 2] = (float)(szz * G.P->gk2);
             }
             __syncthreads();
         }
@@ -645,20 +671,12 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                 const int q = t0 + threadIdx.x;
                 const bool valid = q < ne;
                 int32_t e = 0;
-                uint64_t ex = G.X, ey = G.Y, ez = G.Z;
-                float mj = 0.f;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (valid) {
                     e = T.ent[G.e0 + q];
-                    if (e >= 0) {
-                        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; mj = (float)T.m[e];
-                    } else {
-                        const int32_t nd = -e - 1;
-                        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; mj = (float)T.M[nd];
-                    }
+                    r = T.rec[G.e0 + q];
                 }
-                const float xj = Arith<float>::from_fixed(ex, G.X, sc), yj = Arith<float>::from_fixed(ey, G.Y, sc),
-                            zj = Arith<float>::from_fixed(ez, G.Z, sc);
-                const f2 XJ = f2pack(xj, xj), YJ = f2pack(yj, yj), ZJ = f2pack(zj, zj), MJ = f2pack(mj, mj);
+                const f2 XJ = f2pack(r.x, r.x), YJ = f2pack(r.y, r.y), ZJ = f2pack(r.z, r.z), MJ = f2pack(r.w, r.w);
                 const f2 E2 = f2pack(eps2, eps2), THREE = f2pack(3.f, 3.f);
                 f2 vx = f2pack(0.f, 0.f), vy = vx, vz = vx;
                 for (int pp = 0; pp < npairs; pp++) {
@@ -800,12 +818,20 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
                       cudaStream_t s)
 {
     if (G <= 0) return;
-    cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-    static int bps = pair_blocks_per_sm<float>();
-    int64_t grid = (int64_t)num_sms() * bps;
-    if (grid > G) grid = G;
+    cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+    static int bps = 0, bpp = 0;          // occupancies, queried once outside any capture
+    if (bps == 0) {
+        bps = pair_blocks_per_sm<float>();
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, k_pair_packed, kThreads, 0);
+        bpp = bpp > 0 ? bpp : 1;
+    }
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    TP_LAUNCH(k_pair_packed, grid_of(bpp), kThreads, 0, s, T, acc, queue + 1, order);
     auto k = k_pair<float, true>;
-    TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, queue, order);
+    TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
 }
 
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s)

@@ -65,6 +65,24 @@ struct WalkGroup {
     const BoxPrm *P;
 };
 
+// An entry's record for the pair kernels: its offset from the group centre
+// (wrap-around difference of the 64-bit images, the exact minimum image)
+// scaled by k = 2/r_cut and rounded once to FP32, and its mass.
+__device__ __forceinline__ float4 entry_record(const TreeDev &T, uint64_t GX, uint64_t GY, uint64_t GZ, float sc,
+                                              int32_t e)
+{
+    uint64_t ex, ey, ez;
+    double m;
+    if (e >= 0) {
+        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; m = T.m[e];
+    } else {
+        const int32_t nd = -e - 1;
+        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; m = T.M[nd];
+    }
+    return make_float4(__ll2float_rn((long long)(ex - GX)) * sc, __ll2float_rn((long long)(ey - GY)) * sc,
+                       __ll2float_rn((long long)(ez - GZ)) * sc, (float)m);
+}
+
 __device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g)
 {
     WalkGroup W;
@@ -242,18 +260,46 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T)
 }
 
 // Compaction of the padded slots into the lists: one warp per item.
+// Compaction of the padded slots into the lists, with each entry's record.
+// A warp takes 32 consecutive items (lane l holds item base + l); their
+// entries are contiguous in the output, so the warp writes them as one run and
+// finds each entry's item by a binary search over the lanes' running counts.
 __global__ void k_compact(TreeDev T)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
     if (*T.n_entries > T.cap_entries || *T.status == TP_ERR_LIST_OVERFLOW) return;
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = w0; it < NI; it += nw) {
-        const int32_t *src = T.pent + T.ibpos[it];
-        int32_t *dst = T.ent + T.ipos[it];
-        const int32_t n = T.icnt2[it];
-        for (int32_t k = lane; k < n; k += 32) dst[k] = src[k];
+    for (int64_t base = 32 * w0; base < NI; base += 32 * nw) {
+        const int64_t it = base + lane;
+        const bool v = it < NI;
+        const int32_t cnt = v ? T.icnt2[it] : 0;
+        int32_t incl = cnt;                           // inclusive running count over the lanes
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t total = __shfl_sync(full, incl, 31);
+        const int64_t out0 = __shfl_sync(full, v ? T.ipos[it] : 0, 0);
+        const int64_t sbase = v ? T.ibpos[it] - (incl - cnt) : 0;
+        const int32_t g = v ? T.igrp[it] : 0;
+        const float sc = v ? T.box[T.gbox[g]].scale : 0.f;
+        for (int32_t k0 = 0; k0 < total; k0 += 32) {
+            const int32_t k = k0 + lane;
+            int j = 0;                                // lanes whose running count is <= k
+            for (int st = 16; st > 0; st >>= 1)
+                if (__shfl_sync(full, incl, j + st - 1) <= k) j += st;
+            const int64_t sb = __shfl_sync(full, sbase, j);
+            const int32_t gj = __shfl_sync(full, g, j);
+            const float scj = __shfl_sync(full, sc, j);
+            if (k < total) {
+                const int32_t e = T.pent[sb + k];
+                T.ent[out0 + k] = e;
+                T.rec[out0 + k] = entry_record(T, T.gX[gj], T.gY[gj], T.gZ[gj], scj, e);
+            }
+        }
     }
 }
 
@@ -344,7 +390,7 @@ void walk_expand(TreeDev &T, void *scan_tmp, cudaStream_t s)
 void walk_write(TreeDev &T, cudaStream_t s)
 {
     if (T.cap_items <= 0) return;
-    TP_LAUNCH(k_compact, grid_for(32 * T.cap_items, 256), 256, 0, s, T);
+    TP_LAUNCH(k_compact, grid_for(T.cap_items, 256), 256, 0, s, T);
 }
 
 // order[] = groups by descending cost; key/val/key2/val2 hold cap_groups each.
