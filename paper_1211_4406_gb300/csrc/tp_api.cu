@@ -17,7 +17,7 @@ void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_t
 void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s);
 void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
-void walk_expand(TreeDev &T, void *scan_tmp, cudaStream_t s);
+void walk_expand(TreeDev &T, unsigned long long *counter, void *scan_tmp, cudaStream_t s);
 void walk_write(TreeDev &T, cudaStream_t s);
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
@@ -336,7 +336,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
         }
     }
     TP_LAUNCH(k_check_pad, 1, 1, 0, s, D);
-    tp::walk_expand(D, t->scan_tmp, s);
+    tp::walk_expand(D, reinterpret_cast<unsigned long long *>(t->queue + 2), t->scan_tmp, s);
     if (sync) {
         tp_status e = cuda_status(cudaMemcpyAsync(&t->h_entries, D.n_entries, sizeof(int64_t),
                                                   cudaMemcpyDeviceToHost, s));

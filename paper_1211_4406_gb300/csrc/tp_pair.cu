@@ -279,6 +279,17 @@ __device__ __forceinline__ f2 nonzero_mask(f2 r2)
     return f2pack(fminf(a, 1.f), fminf(b, 1.f));
 }
 
+// hi + lo += x with the rounding error of the addition kept in lo (Knuth's
+// TwoSum), so a long running sum in FP32 stays as accurate as one in FP64.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
 template <class R>
 __device__ __forceinline__ R scale_of(const BoxPrm &P);
 template <> __device__ __forceinline__ float scale_of<float>(const BoxPrm &P) { return P.scale; }
@@ -399,8 +410,10 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 }
 
 // The FP32 forward kernel for ordinary groups with eps > 0: packed pair math
-// fed by the walk's entry records (each thread stages one entry pair per tile
-// and loads the next tile's pair while the current one is computed).
+// fed by the entry records (each thread stages one entry pair per tile and
+// loads the next tile's pair while the current one is computed).  Each tile's
+// FP32 partial enters a compensated FP32 sum, so the total over thousands of
+// entries keeps FP64-like accuracy without FP64 arithmetic in the loop.
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
@@ -427,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
             const float xi = Arith<float>::from_fixed(T.X[p], G.X, sc);
             const float yi = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
             const float zi = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
-            double sax = 0.0, say = 0.0, saz = 0.0;
+            float shx = 0.f, shy = 0.f, shz = 0.f, slx = 0.f, sly = 0.f, slz = 0.f;
             float4 n0 = pad, n1 = pad;
             if (ne > 0) {
                 const int nt = min(kTile, ne), q = 2 * (int)threadIdx.x;
@@ -448,10 +461,14 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
                 if (active) {
                     float ax = 0.f, ay = 0.f, az = 0.f;
                     force_tile_packed(SA, SB, st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
-                    sax += ax; say += ay; saz += az;
+                    two_sum_add(shx, slx, ax);
+                    two_sum_add(shy, sly, ay);
+                    two_sum_add(shz, slz, az);
                 }
             }
-            red[0][slot] = sax; red[1][slot] = say; red[2][slot] = saz;
+            red[0][slot] = (double)shx + (double)slx;
+            red[1][slot] = (double)shy + (double)sly;
+            red[2][slot] = (double)shz + (double)slz;
             __syncthreads();
             if (slot < nic) {
                 double sxx = 0, syy = 0, szz = 0;
@@ -622,20 +639,26 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // entries and loop over the group's particles two at a time, staged as
 // A = {x0, x1, y0, y1}, B = {z0, z1, wx0, wx1}, C = {wy0, wy1, wz0, wz1}.  Each
 // pair's alpha = m phi and beta = m psi (d.w_i) are computed once: the entry
-// sums its side, v = sum_i (alpha w_i + beta d), in registers; the particle
-// side, A_i = sum alpha and B_i = sum beta d, is a butterfly over the warp's
-// entries per particle pair, written to the warp's row and summed in FP64 by
-// the thread that owns the particle.
+// sums its side, v = sum_i (alpha w_i + beta d), in registers.  The particle
+// side, A_i = sum alpha and B_i = sum beta d, is summed over the warp's 32
+// entries for two particle pairs at once: their 16 values are reduce-scattered
+// (four halving exchanges and one final one, 16 shuffles in all) so that each
+// lane pair ends with one total, written to the warp's row; the thread that
+// owns the particle adds the rows and keeps a compensated FP32 sum across
+// tiles.
 __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order)
 {
     constexpr int kWarps = kThreads / 32;
+    constexpr unsigned kFull = 0xffffffffu;
     __shared__ float4 IA[kThreads / 2], IB[kThreads / 2], IC[kThreads / 2];
     __shared__ float part[kWarps][4][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // after the reduce-scatter below, lane holds the sum of value (lane >> 1) & 15
+    const int vidx = (lane >> 1) & 15, vP = vidx >> 3, vq = (vidx >> 1) & 3, vh = vidx & 1;
     for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
          item = next_item<true>(queue, item, &s_item)) {
         const int64_t g = order ? order[item] : item;
@@ -646,9 +669,9 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
         const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
-            const int npairs = (nic + 1) >> 1;
+            const int npe = (((nic + 1) >> 1) + 1) & ~1;      // particle pairs, rounded up to even
             __syncthreads();
-            if (threadIdx.x < 2 * npairs) {
+            if (threadIdx.x < 2 * npe) {
                 const int l = threadIdx.x & 1;
                 float *A = reinterpret_cast<float *>(&IA[threadIdx.x >> 1]);
                 float *B = reinterpret_cast<float *>(&IB[threadIdx.x >> 1]);
@@ -665,7 +688,8 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                     B[2 + l] = 0.f; Cc[l] = 0.f; Cc[2 + l] = 0.f;
                 }
             }
-            double sA = 0.0, sBx = 0.0, sBy = 0.0, sBz = 0.0;
+            // particle-side sums across tiles, compensated FP32 (hi + lo)
+            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
             __syncthreads();
             for (int t0 = 0; t0 < ne; t0 += kThreads) {
                 const int q = t0 + threadIdx.x;
@@ -677,61 +701,71 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                     r = T.rec[G.e0 + q];
                 }
                 const f2 XJ = f2pack(r.x, r.x), YJ = f2pack(r.y, r.y), ZJ = f2pack(r.z, r.z), MJ = f2pack(r.w, r.w);
-                const f2 E2 = f2pack(eps2, eps2), THREE = f2pack(3.f, 3.f);
+                const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
                 f2 vx = f2pack(0.f, 0.f), vy = vx, vz = vx;
-                for (int pp = 0; pp < npairs; pp++) {
-                    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&IA[pp]);
-                    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&IB[pp]);
-                    const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(&IC[pp]);
-                    const f2 dx = f2sub(XJ, a.x), dy = f2sub(YJ, a.y), dz = f2sub(ZJ, b.x);
-                    const f2 WX = b.y, WY = c.x, WZ = c.y;
-                    const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-                    float r2a, r2b, s2a, s2b;
-                    f2unpack(r2, r2a, r2b);
-                    f2unpack(f2add(r2, E2), s2a, s2b);
-                    const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-                    const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
-                    f2 gv, gp;
-                    g_gpx_packed(x, gv, gp);
-                    const f2 ri2 = f2mul(ri, ri), ri3 = f2mul(ri2, ri);
-                    const f2 phi = f2mul(gv, ri3);
-                    const f2 psi = f2fma(f2mul(THREE, phi), f2mul(f2pack(-1.f, -1.f), ri2), f2mul(gp, ri3));
-                    const f2 m = f2mul(MJ, nonzero_mask(r2));
-                    const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
-                    f2 alpha = f2mul(m, phi);
-                    const f2 beta = f2mul(f2mul(m, psi), dw);
-                    vx = f2fma(beta, dx, f2fma(alpha, WX, vx));
-                    vy = f2fma(beta, dy, f2fma(alpha, WY, vy));
-                    vz = f2fma(beta, dz, f2fma(alpha, WZ, vz));
-                    f2 bx = f2mul(beta, dx), by = f2mul(beta, dy), bz = f2mul(beta, dz);
+                for (int pp = 0; pp < npe; pp += 2) {
+                    float v[16];
 #pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        alpha = f2add(alpha, __shfl_xor_sync(0xffffffffu, alpha, off));
-                        bx = f2add(bx, __shfl_xor_sync(0xffffffffu, bx, off));
-                        by = f2add(by, __shfl_xor_sync(0xffffffffu, by, off));
-                        bz = f2add(bz, __shfl_xor_sync(0xffffffffu, bz, off));
+                    for (int P = 0; P < 2; P++) {
+                        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&IA[pp + P]);
+                        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&IB[pp + P]);
+                        const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(&IC[pp + P]);
+                        const f2 dx = f2sub(XJ, a.x), dy = f2sub(YJ, a.y), dz = f2sub(ZJ, b.x);
+                        const f2 WX = b.y, WY = c.x, WZ = c.y;
+                        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+                        float r2a, r2b, s2a, s2b;
+                        f2unpack(r2, r2a, r2b);
+                        f2unpack(f2add(r2, E2), s2a, s2b);
+                        const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+                        const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+                        f2 gv, gp;
+                        g_gpx_packed(x, gv, gp);
+                        const f2 ri2 = f2mul(ri, ri), ri3 = f2mul(ri2, ri);
+                        const f2 phi = f2mul(gv, ri3);
+                        const f2 psi = f2mul(ri3, f2fma(gv, f2mul(M3, ri2), gp));
+                        const f2 m = f2mul(MJ, nonzero_mask(r2));
+                        const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
+                        const f2 alpha = f2mul(m, phi);
+                        const f2 beta = f2mul(f2mul(m, psi), dw);
+                        vx = f2fma(beta, dx, f2fma(alpha, WX, vx));
+                        vy = f2fma(beta, dy, f2fma(alpha, WY, vy));
+                        vz = f2fma(beta, dz, f2fma(alpha, WZ, vz));
+                        f2unpack(alpha, v[8 * P + 0], v[8 * P + 1]);
+                        f2unpack(f2mul(beta, dx), v[8 * P + 2], v[8 * P + 3]);
+                        f2unpack(f2mul(beta, dy), v[8 * P + 4], v[8 * P + 5]);
+                        f2unpack(f2mul(beta, dz), v[8 * P + 6], v[8 * P + 7]);
                     }
-                    if (lane == 0) {
-                        float lo, hi;
-                        f2unpack(alpha, lo, hi); part[warp][0][2 * pp] = lo; part[warp][0][2 * pp + 1] = hi;
-                        f2unpack(bx, lo, hi); part[warp][1][2 * pp] = lo; part[warp][1][2 * pp + 1] = hi;
-                        f2unpack(by, lo, hi); part[warp][2][2 * pp] = lo; part[warp][2][2 * pp + 1] = hi;
-                        f2unpack(bz, lo, hi); part[warp][3][2 * pp] = lo; part[warp][3][2 * pp + 1] = hi;
+                    // reduce-scatter over the warp's 32 entries: each halving step
+                    // keeps the half of the values selected by one lane bit
+#pragma unroll
+                    for (int lvl = 0; lvl < 4; lvl++) {
+                        const int off = 16 >> lvl, half = 8 >> lvl;
+                        const bool upper = (lane & off) != 0;
+#pragma unroll
+                        for (int k = 0; k < half; k++) {
+                            const float send = upper ? v[k] : v[k + half];
+                            const float keep = upper ? v[k + half] : v[k];
+                            v[k] = keep + __shfl_xor_sync(kFull, send, off);
+                        }
                     }
+                    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                    if ((lane & 1) == 0) part[warp][vq][2 * (pp + vP) + vh] = v[0];
                 }
                 if (valid) {
                     float l, h;
                     double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
-                    f2unpack(vx, l, h); atomicAdd(dst, gk3 * ((double)l + (double)h));
-                    f2unpack(vy, l, h); atomicAdd(dst + 1, gk3 * ((double)l + (double)h));
-                    f2unpack(vz, l, h); atomicAdd(dst + 2, gk3 * ((double)l + (double)h));
+                    f2unpack(vx, l, h); atomicAdd(dst, gk3 * (double)(l + h));
+                    f2unpack(vy, l, h); atomicAdd(dst + 1, gk3 * (double)(l + h));
+                    f2unpack(vz, l, h); atomicAdd(dst + 2, gk3 * (double)(l + h));
                 }
                 __syncthreads();
                 if (threadIdx.x < nic) {
                     const int nw = (min(kThreads, ne - t0) + 31) >> 5;   // warps that held entries
-                    for (int w = 0; w < nw; w++) {
-                        sA += (double)part[w][0][threadIdx.x]; sBx += (double)part[w][1][threadIdx.x];
-                        sBy += (double)part[w][2][threadIdx.x]; sBz += (double)part[w][3][threadIdx.x];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        float t = 0.f;
+                        for (int w = 0; w < nw; w++) t += part[w][k][threadIdx.x];
+                        two_sum_add(sh[k], sl[k], t);
                     }
                 }
                 __syncthreads();
@@ -739,9 +773,12 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
             if (threadIdx.x < nic) {
                 const int32_t p = G.first + i0 + threadIdx.x;
                 const int64_t o = T.perm[p];
-                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)cot[3 * o] + sBx));
-                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)cot[3 * o + 1] + sBy));
-                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)cot[3 * o + 2] + sBz));
+                const double sA = (double)sh[0] + (double)sl[0];
+                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)cot[3 * o] + ((double)sh[1] + (double)sl[1])));
+                atomicAdd(gs + 3 * (int64_t)p + 1,
+                          -gk3 * (sA * (double)cot[3 * o + 1] + ((double)sh[2] + (double)sl[2])));
+                atomicAdd(gs + 3 * (int64_t)p + 2,
+                          -gk3 * (sA * (double)cot[3 * o + 2] + ((double)sh[3] + (double)sl[3])));
             }
         }
     }

@@ -1,8 +1,9 @@
 // tp_walk.cu -- per-group interaction lists (Barnes' modified algorithm,
 // Sec. II; the "tree traversal" row of Table I).
 //
-// One thread walks one group's tree depth first, without a stack, by the skip
-// pointers of the breadth-first node array.  At every node it decides
+// The walk visits a group's tree depth first (top stage: one thread per group,
+// stackless by the skip pointers of the breadth-first node array; task stage:
+// one warp per subtree, one lane per particle).  At every node it decides
 //   prune   periodic box-to-box gap d >= r_cut,
 //   accept  no overlap with the group, largest box-to-box distance < r_cut and
 //           l^2 < theta^2 d^2 (l = 2^-level): the node enters as a monopole,
@@ -50,13 +51,13 @@ __device__ __forceinline__ double exact_dist2(double ax, double ay, double az, d
     return __dadd_rn(__dadd_rn(__dmul_rn(gp[0], gp[0]), __dmul_rn(gp[1], gp[1])), __dmul_rn(gp[2], gp[2]));
 }
 
-// Walk modes.  TOP: from the box root, an opened node holding at most `split`
-// particles (or a leaf) is not descended but emitted as a task item (its node
-// id); accepted monopoles are emitted as final items -(id+1).  TASK: from a
-// task node to the end of its subtree (its skip pointer), emitting list entries.
-// The items of all groups, concatenated in group order and in depth-first order
-// within a group, expand to exactly the depth-first lists of the reference.
-enum { kTop = 0, kTask = 1 };
+// The walk runs in two stages.  Top: one thread per group walks from the box
+// root; an opened node holding at most `split` particles (or a leaf) is not
+// descended but emitted as a task item (its node id), an accepted monopole as a
+// final item -(id+1).  Task: each task expands to the list entries of its
+// subtree.  The items of all groups, concatenated in group order and in
+// depth-first order within a group, expand to exactly the depth-first lists of
+// the reference definition.
 
 struct WalkGroup {
     uint32_t gx, gy, gz, hx, hy, hz;
@@ -95,103 +96,88 @@ __device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g
     return W;
 }
 
-// Depth-first walk from `start` until the preorder reaches `end` (-1: the end
-// of the tree).  Returns the number of items (kTop) or entries (kTask); with
-// out != nullptr writes them to out[0 .. out_n).
-template <int MODE>
-__device__ int32_t walk_dfs(const TreeDev &T, const WalkGroup &W, int32_t start, int32_t end,
-                            int32_t split, int32_t *out, int64_t out_n, unsigned long long &ambig)
+enum { kPrune = 0, kAccept = 1, kOpen = 2 };
+
+// The decision at node nd (w = its walk record) for group W; namb counts the
+// decisions that needed the exact FP64 test.
+__device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W, int32_t nd, const WNode &w,
+                                           int &namb)
 {
     const uint64_t T_lo = W.P->T_lo, T_hi = W.P->T_hi;
+    const uint32_t ax = absdiff32(w.cx, W.gx), ay = absdiff32(w.cy, W.gy), az = absdiff32(w.cz, W.gz);
+    const uint64_t sx = (uint64_t)w.hx + W.hx, sy = (uint64_t)w.hy + W.hy, sz = (uint64_t)w.hz + W.hz;
+    const uint64_t dx = ax > sx ? ax - sx : 0, dy = ay > sy ? ay - sy : 0, dz = az > sz ? az - sz : 0;
+    const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
+    bool exact = false;
+    double gap2d = 0.0, far2d = 0.0;
+    if (gap2 >= T_hi) return kPrune;
+    if (gap2 >= T_lo) {
+        exact = true;
+        namb++;
+        gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd], T.gcx[W.g],
+                            T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g], &far2d);
+        if (gap2d >= W.P->rc2) return kPrune;
+    }
+    const bool overlap = w.first < W.g1 && W.g0 < w.first + w.count;
+    if (overlap) return kOpen;
+    if (!exact) {
+        const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
+        const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
+        const int A = far2 < T_lo ? 1 : (far2 >= T_hi ? 0 : -1);
+        const int B = gap2 >= W.P->TB_hi[w.level] ? 1 : (gap2 < W.P->TB_lo[w.level] ? 0 : -1);
+        if (A == 0 || B == 0) return kOpen;
+        if (A == 1 && B == 1) return kAccept;
+        namb++;
+        gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd], T.gcx[W.g],
+                            T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g], &far2d);
+    }
+    const double l = ldexp(1.0, -w.level);
+    return far2d < W.P->rc2 && __dmul_rn(l, l) < __dmul_rn(W.P->th2, gap2d) ? kAccept : kOpen;
+}
+
+// Whether particle p of an opened leaf enters the list: point-to-box gap < r_cut.
+__device__ __forceinline__ bool keep_particle(const TreeDev &T, const WalkGroup &W, int32_t p, int &namb)
+{
+    const uint32_t qx = absdiff32((uint32_t)(T.X[p] >> 32), W.gx);
+    const uint32_t qy = absdiff32((uint32_t)(T.Y[p] >> 32), W.gy);
+    const uint32_t qz = absdiff32((uint32_t)(T.Z[p] >> 32), W.gz);
+    const uint64_t ex = qx > W.hx ? qx - W.hx : 0, ey = qy > W.hy ? qy - W.hy : 0, ez = qz > W.hz ? qz - W.hz : 0;
+    const uint64_t p2 = ex * ex + ey * ey + ez * ez;
+    if (p2 >= W.P->T_hi) return false;
+    if (p2 < W.P->T_lo) return true;
+    namb++;
+    double f2;
+    return exact_dist2(T.x[p], T.y[p], T.z[p], 0.0, 0.0, 0.0, T.gcx[W.g], T.gcy[W.g], T.gcz[W.g], T.ghx[W.g],
+                       T.ghy[W.g], T.ghz[W.g], &f2) < W.P->rc2;
+}
+
+// Top walk of one group, depth first from the box root without a stack (skip
+// pointers).  Returns the number of items; with out != nullptr writes them to
+// out[0 .. out_n).
+__device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start, int32_t split, int32_t *out,
+                            int64_t out_n, unsigned long long &ambig)
+{
     int32_t cnt = 0;
     int32_t nd = start;
     int64_t budget = *T.n_nodes + 1;     // a preorder walk visits each node at most once
-    while (nd != end && nd >= 0) {
+    while (nd >= 0) {
         if (--budget < 0 || nd >= T.cap_nodes) {
             tp_latch(T.status, TP_ERR_TIMEOUT);
             break;
         }
         const WNode w = T.wn[nd];
-        const uint32_t ax = absdiff32(w.cx, W.gx), ay = absdiff32(w.cy, W.gy), az = absdiff32(w.cz, W.gz);
-        const uint64_t sx = (uint64_t)w.hx + W.hx, sy = (uint64_t)w.hy + W.hy, sz = (uint64_t)w.hz + W.hz;
-        const uint64_t dx = ax > sx ? ax - sx : 0, dy = ay > sy ? ay - sy : 0, dz = az > sz ? az - sz : 0;
-        const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
-        bool exact = false, prune;
-        double gap2d = 0.0, far2d = 0.0;
-        if (gap2 >= T_hi) {
-            prune = true;
-        } else if (gap2 < T_lo) {
-            prune = false;
-        } else {
-            exact = true;
-            ambig++;
-            gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd],
-                                T.gcx[W.g], T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g],
-                                &far2d);
-            prune = gap2d >= W.P->rc2;
-        }
-        if (prune) { nd = w.skip; continue; }
-        const bool overlap = w.first < W.g1 && W.g0 < w.first + w.count;
-        bool accept = false;
-        if (!overlap) {
-            if (!exact) {
-                const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
-                const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
-                const int A = far2 < T_lo ? 1 : (far2 >= T_hi ? 0 : -1);
-                const int B = gap2 >= W.P->TB_hi[w.level] ? 1 : (gap2 < W.P->TB_lo[w.level] ? 0 : -1);
-                if (A == 0 || B == 0) {
-                    accept = false;
-                } else if (A == 1 && B == 1) {
-                    accept = true;
-                } else {
-                    exact = true;
-                    ambig++;
-                    gap2d = exact_dist2(T.cenx[nd], T.ceny[nd], T.cenz[nd], T.hfx[nd], T.hfy[nd], T.hfz[nd],
-                                        T.gcx[W.g], T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g],
-                                        T.ghz[W.g], &far2d);
-                }
-            }
-            if (exact) {
-                const double l = ldexp(1.0, -w.level);
-                accept = far2d < W.P->rc2 && __dmul_rn(l, l) < __dmul_rn(W.P->th2, gap2d);
-            }
-        }
-        if (accept) {
+        int namb = 0;
+        const int d = decide_node(T, W, nd, w, namb);
+        ambig += namb;
+        if (d == kPrune) {
+            nd = w.skip;
+        } else if (d == kAccept) {
             if (out && cnt < out_n) out[cnt] = -(nd + 1);
             cnt++;
             nd = w.skip;
-            continue;
-        }
-        if (MODE == kTop && (w.child < 0 || w.count <= split)) {
+        } else if (w.child < 0 || w.count <= split) {
             if (out && cnt < out_n) out[cnt] = nd;       // a task: expand its subtree later
             cnt++;
-            nd = w.skip;
-            continue;
-        }
-        if (w.child < 0) {
-            for (int32_t p = w.first; p < w.first + w.count; p++) {
-                const uint32_t qx = absdiff32((uint32_t)(T.X[p] >> 32), W.gx);
-                const uint32_t qy = absdiff32((uint32_t)(T.Y[p] >> 32), W.gy);
-                const uint32_t qz = absdiff32((uint32_t)(T.Z[p] >> 32), W.gz);
-                const uint64_t ex = qx > W.hx ? qx - W.hx : 0, ey = qy > W.hy ? qy - W.hy : 0,
-                               ez = qz > W.hz ? qz - W.hz : 0;
-                const uint64_t p2 = ex * ex + ey * ey + ez * ez;
-                bool keep;
-                if (p2 >= T_hi) {
-                    keep = false;
-                } else if (p2 < T_lo) {
-                    keep = true;
-                } else {
-                    ambig++;
-                    double f2;
-                    keep = exact_dist2(T.x[p], T.y[p], T.z[p], 0.0, 0.0, 0.0, T.gcx[W.g], T.gcy[W.g],
-                                       T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g], &f2) < W.P->rc2;
-                }
-                if (keep) {
-                    if (out && cnt < out_n) out[cnt] = p;
-                    cnt++;
-                }
-            }
             nd = w.skip;
         } else {
             nd = w.child;
@@ -211,12 +197,12 @@ __global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
          g += (int64_t)gridDim.x * blockDim.x) {
         const WalkGroup W = load_walk_group(T, g);
         if (!WRITE) {
-            T.icnt[g] = walk_dfs<kTop>(T, W, T.gbox[g], -1, split, nullptr, 0, ambig);
+            T.icnt[g] = walk_top(T, W, T.gbox[g], split, nullptr, 0, ambig);
         } else {
             const int64_t o = T.ioff[g];
             const int64_t n = T.icnt[g];
             if (o + n > T.cap_items) continue;
-            const int32_t c = walk_dfs<kTop>(T, W, T.gbox[g], -1, split, T.item + o, n, ambig);
+            const int32_t c = walk_top(T, W, T.gbox[g], split, T.item + o, n, ambig);
             for (int64_t k = 0; k < c && k < n; k++) T.igrp[o + k] = (int32_t)g;
         }
     }
@@ -237,24 +223,91 @@ __global__ void k_item_bounds(TreeDev T)
 }
 
 // Expansion of every item into its padded slots; records the entry count.
-__global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T)
+// Each lane expands one item at a time by a stackless depth-first walk of the
+// task's subtree and takes its next item from a global counter as soon as it
+// is done, so lanes with short tasks do not wait for the warp's longest one.
+// Every loop iteration does one unit of work -- one node decision or one
+// particle test of an opened leaf -- so lanes at different stages of their
+// walks diverge by at most one branch per iteration.
+__global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long long *counter)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
     if (*T.n_pad > T.cap_pad || *T.status == TP_ERR_LIST_OVERFLOW) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     unsigned long long ambig = 0;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < NI;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = T.item[it];
-        int32_t *out = T.pent + T.ibpos[it];
-        if (v < 0) {                                  // an accepted monopole
-            out[0] = v;
-            T.icnt2[it] = 1;
-            continue;
+    int64_t it = -1;                       // the lane's item; -1 none
+    bool exhausted = false;
+    WalkGroup W{};
+    int32_t *out = nullptr;
+    int32_t nd = -1, end = -1, pcur = 0, pend = 0, cnt = 0, bound = 0;
+    int64_t budget = 0;
+    for (;;) {
+        const unsigned nm = __ballot_sync(full, it < 0 && !exhausted);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(nm));
+            base = __shfl_sync(full, base, leader);
+            if (it < 0 && !exhausted) {
+                const int64_t cand = (int64_t)base + __popc(nm & below);
+                if (cand < NI) {
+                    it = cand;
+                    const int32_t v = T.item[it];
+                    out = T.pent + T.ibpos[it];
+                    if (v < 0) {                       // an accepted monopole
+                        out[0] = v;
+                        T.icnt2[it] = 1;
+                        it = -1;
+                    } else {
+                        W = load_walk_group(T, T.igrp[it]);
+                        nd = v;
+                        end = T.wn[v].skip;
+                        pcur = pend = 0;
+                        cnt = 0;
+                        bound = T.ibound[it];
+                        budget = *T.n_nodes + 1;
+                    }
+                } else {
+                    exhausted = true;
+                }
+            }
         }
-        const WalkGroup W = load_walk_group(T, T.igrp[it]);
-        const int32_t n = walk_dfs<kTask>(T, W, v, T.wn[v].skip, 0, out, T.ibound[it], ambig);
-        if (n > T.ibound[it]) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
-        T.icnt2[it] = n;
+        if (__all_sync(full, exhausted)) break;
+        if (it < 0) continue;
+        if (pcur < pend) {                             // one particle of an opened leaf
+            int namb = 0;
+            if (keep_particle(T, W, pcur, namb)) {
+                if (cnt < bound) out[cnt] = pcur;
+                cnt++;
+            }
+            ambig += namb;
+            pcur++;
+        } else if (nd == end || nd < 0 || --budget < 0 || nd >= T.cap_nodes) {
+            if (budget < 0 || (nd != end && nd >= T.cap_nodes)) tp_latch(T.status, TP_ERR_TIMEOUT);
+            if (cnt > bound) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+            T.icnt2[it] = cnt;
+            it = -1;
+        } else {                                       // one node decision
+            const WNode w = T.wn[nd];
+            int namb = 0;
+            const int d = decide_node(T, W, nd, w, namb);
+            ambig += namb;
+            if (d == kPrune) {
+                nd = w.skip;
+            } else if (d == kAccept) {
+                if (cnt < bound) out[cnt] = -(nd + 1);
+                cnt++;
+                nd = w.skip;
+            } else if (w.child < 0) {
+                pcur = w.first;
+                pend = w.first + w.count;
+                nd = w.skip;
+            } else {
+                nd = w.child;
+            }
+        }
     }
     if (ambig) atomicAdd(T.n_ambig, ambig);
 }
@@ -379,10 +432,19 @@ void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 }
 
 // Task expansion into the padded slots, entry positions (scan) -> *T.n_entries.
-void walk_expand(TreeDev &T, void *scan_tmp, cudaStream_t s)
+void walk_expand(TreeDev &T, unsigned long long *counter, void *scan_tmp, cudaStream_t s)
 {
     if (T.cap_items <= 0) return;
-    TP_LAUNCH(k_walk_task, grid_for(T.cap_items, kBlock), kBlock, 0, s, T);
+    static int bps = 0;                    // occupancy, queried once outside any capture
+    if (bps == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_walk_task, kBlock, 0);
+        bps = bps > 0 ? bps : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    TP_LAUNCH(k_walk_task, (sms > 0 ? sms : 1) * bps, kBlock, 0, s, T, counter);
     scan_i32_to_i64(T.icnt2, T.ipos, 0, T.n_items, T.n_entries, scan_tmp, s);
     TP_LAUNCH(k_list_offsets, grid_for(T.cap_groups, 256), 256, 0, s, T);
 }
