@@ -103,6 +103,27 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (N > 1: one independent replica per rank)
+# ---------------------------------------------------------------------------
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of `values` over all ranks of the default process
+    group (the values themselves when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world, units_per_step, steps, total_ms):
+    """Units all ranks processed per second over the slowest rank's time:
+    every rank runs the same fixed per-rank workload (weak scaling)."""
+    return world * units_per_step * steps / (total_ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
 # the reference arm: the CPU FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
 def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None):
@@ -288,12 +309,9 @@ def run_ours(args, rank, world, local_rank):
     per_step_inter = 2 * inter
     tot_ms = sum(t_step)
     tot_e2e = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms, tot_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, tot_e2e = float(t[0]), float(t[1])
-    value = world * per_step_inter * args.steps / (tot_ms * 1e-3)
-    e2e_value = world * per_step_inter * args.steps / (tot_e2e * 1e-3)
+    tot_ms, tot_e2e = max_over_ranks([tot_ms, tot_e2e], device=dev)
+    value = whole_job_rate(world, per_step_inter, args.steps, tot_ms)
+    e2e_value = whole_job_rate(world, per_step_inter, args.steps, tot_e2e)
 
     if rank != 0:
         tree.close()
