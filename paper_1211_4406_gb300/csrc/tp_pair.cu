@@ -410,14 +410,15 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 }
 
 // The FP32 forward kernel for ordinary groups with eps > 0: packed pair math
-// fed by the entry records (each thread stages one entry pair per tile and
-// loads the next tile's pair while the current one is computed).  Each tile's
-// FP32 partial enters a compensated FP32 sum, so the total over thousands of
-// entries keeps FP64-like accuracy without FP64 arithmetic in the loop.
+// fed by the entry records.  Tiles are double buffered in shared memory: while
+// tile t is computed from one buffer, each thread stores its entry pair of tile
+// t+1 (loaded one tile earlier into registers) into the other buffer and loads
+// its pair of tile t+2, so one barrier per tile suffices.  Each tile's FP32
+// partial enters an FP64 sum per particle.
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
-    __shared__ float4 SA[kTile / 2], SB[kTile / 2];
+    __shared__ float4 SA[2][kTile / 2], SB[2][kTile / 2];
     __shared__ double red[3][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
@@ -440,35 +441,36 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
             const float xi = Arith<float>::from_fixed(T.X[p], G.X, sc);
             const float yi = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
             const float zi = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
-            float shx = 0.f, shy = 0.f, shz = 0.f, slx = 0.f, sly = 0.f, slz = 0.f;
+            double sax = 0.0, say = 0.0, saz = 0.0;
             float4 n0 = pad, n1 = pad;
+            auto fetch = [&](int t1) {
+                const int nt1 = min(kTile, ne - t1), q = 2 * (int)threadIdx.x;
+                n0 = q < nt1 ? T.rec[G.e0 + t1 + q] : pad;
+                n1 = q + 1 < nt1 ? T.rec[G.e0 + t1 + q + 1] : pad;
+            };
+            __syncthreads();
             if (ne > 0) {
-                const int nt = min(kTile, ne), q = 2 * (int)threadIdx.x;
-                if (q < nt) n0 = T.rec[G.e0 + q];
-                if (q + 1 < nt) n1 = T.rec[G.e0 + q + 1];
+                fetch(0);
+                SA[0][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
+                SB[0][threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
+                if (kTile < ne) fetch(kTile);
             }
-            for (int t0 = 0; t0 < ne; t0 += kTile) {
+            __syncthreads();
+            for (int t0 = 0, b = 0; t0 < ne; t0 += kTile, b ^= 1) {
                 const int nt = min(kTile, ne - t0);
-                __syncthreads();
-                SA[threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
-                SB[threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
-                __syncthreads();
-                if (t0 + kTile < ne) {
-                    const int t1 = t0 + kTile, nt1 = min(kTile, ne - t1), q = 2 * (int)threadIdx.x;
-                    n0 = q < nt1 ? T.rec[G.e0 + t1 + q] : pad;
-                    n1 = q + 1 < nt1 ? T.rec[G.e0 + t1 + q + 1] : pad;
-                }
                 if (active) {
                     float ax = 0.f, ay = 0.f, az = 0.f;
-                    force_tile_packed(SA, SB, st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
-                    two_sum_add(shx, slx, ax);
-                    two_sum_add(shy, sly, ay);
-                    two_sum_add(shz, slz, az);
+                    force_tile_packed(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+                    sax += ax; say += ay; saz += az;
                 }
+                if (t0 + kTile < ne) {
+                    SA[b ^ 1][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
+                    SB[b ^ 1][threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
+                    if (t0 + 2 * kTile < ne) fetch(t0 + 2 * kTile);
+                }
+                __syncthreads();
             }
-            red[0][slot] = (double)shx + (double)slx;
-            red[1][slot] = (double)shy + (double)sly;
-            red[2][slot] = (double)shz + (double)slz;
+            red[0][slot] = sax; red[1][slot] = say; red[2][slot] = saz;
             __syncthreads();
             if (slot < nic) {
                 double sxx = 0, syy = 0, szz = 0;
