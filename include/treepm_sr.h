@@ -146,6 +146,19 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
 
 tp_status tp_tree_free(tp_tree *t);
 
+/* Kernel timing, a measurement aid with no counterpart in the paper.  With
+ * enable != 0 the tree records CUDA events on the call's stream immediately
+ * before and after its main FP32 pair-kernel launch in tp_short_range_force
+ * and its main FP32 adjoint-kernel launch in tp_short_range_vjp (the kernels
+ * that handle the groups not spanning half the box, with eps > 0).  Creates
+ * the events on first use (TP_ERR_CUDA if that fails).  enable = 0 stops the
+ * recording.                                                                */
+tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable);
+/* Durations in ms of those two launches in the last force and vjp calls made
+ * with timing on; -1 for a call that recorded nothing (timing off, FP64 tree,
+ * n = 0).  Synchronises on the events.                                      */
+tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms);
+
 /* Largest particle count tp_short_range_force_noalloc accepts.              */
 #define TP_NOALLOC_MAX_N 65536
 

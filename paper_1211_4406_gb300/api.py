@@ -133,6 +133,17 @@ class ShortRangeTree:
     def status(self) -> int:
         return int(_lib.load().tp_tree_status(self.handle))
 
+    # -- kernel timing (events around the main pair and adjoint launches) ------
+    def set_kernel_timing(self, enable: bool = True) -> None:
+        _lib.check(_lib.load().tp_tree_set_kernel_timing(self.handle, 1 if enable else 0),
+                   "tp_tree_set_kernel_timing")
+
+    def kernel_ms(self) -> tuple[float, float]:
+        """(force, vjp) launch durations in ms of the last timed calls (-1: none)."""
+        f, v = C.c_double(), C.c_double()
+        _lib.check(_lib.load().tp_tree_kernel_ms(self.handle, C.byref(f), C.byref(v)), "tp_tree_kernel_ms")
+        return f.value, v.value
+
     # -- statistics and parity exports ----------------------------------------
     def stats(self) -> dict:
         st = _lib.TPStats()

@@ -23,10 +23,10 @@ void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_
                void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
-                      cudaStream_t s);
+                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s);
 void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s);
+             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
              const int32_t *order, int64_t G, cudaStream_t s);
 int num_sms();
@@ -146,6 +146,9 @@ struct tp_tree {
     int32_t *d_maxnj = nullptr;
     // host copies of the sizes (valid after a synchronising build)
     int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_pad = 0, h_entries = 0;
+    // kernel timing: events around the main forward / adjoint kernel launches
+    bool ktiming = false, kf_rec = false, kv_rec = false;
+    cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 static tp_status cuda_status(cudaError_t e)
@@ -462,7 +465,9 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
     if (t->n == 0) return TP_OK;
     if (t->precision == TP_FP32) {
         cudaMemsetAsync(acc, 0, sizeof(float) * 3 * (size_t)t->n, s);
-        tp::pair_forward_f32(t->D, (float *)acc, t->queue, t->order, t->D.cap_groups, s);
+        tp::pair_forward_f32(t->D, (float *)acc, t->queue, t->order, t->D.cap_groups, s,
+                             t->ktiming ? t->kev[0] : nullptr, t->ktiming ? t->kev[1] : nullptr);
+        t->kf_rec = t->ktiming;
     } else {
         cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)t->n, s);
         tp::pair_forward_f64(t->D, (double *)acc, t->D.cap_groups, s);
@@ -478,7 +483,11 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
     t->last = s;
     if (t->n == 0) return TP_OK;
     if (t->precision == TP_FP32)
-        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
+    {
+        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s,
+                    t->ktiming ? t->kev[2] : nullptr, t->ktiming ? t->kev[3] : nullptr);
+        t->kv_rec = t->ktiming && t->D.cap_groups > 0;
+    }
     else
         tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
     return cuda_status(cudaGetLastError());
@@ -603,11 +612,49 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries)
     return e;
 }
 
+tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable)
+{
+    if (!t) return TP_ERR_INVALID_ARG;
+    if (enable && !t->kev[0]) {
+        for (auto &e : t->kev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return TP_ERR_CUDA;
+            }
+    }
+    t->ktiming = enable != 0;
+    t->kf_rec = t->kv_rec = false;
+    return TP_OK;
+}
+
+tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms)
+{
+    if (!t || !force_ms || !vjp_ms) return TP_ERR_INVALID_ARG;
+    *force_ms = -1.0;
+    *vjp_ms = -1.0;
+    float ms = 0.f;
+    if (t->kf_rec) {
+        tp_status e = cuda_status(cudaEventSynchronize(t->kev[1]));
+        if (e == TP_OK) e = cuda_status(cudaEventElapsedTime(&ms, t->kev[0], t->kev[1]));
+        if (e != TP_OK) return e;
+        *force_ms = ms;
+    }
+    if (t->kv_rec) {
+        tp_status e = cuda_status(cudaEventSynchronize(t->kev[3]));
+        if (e == TP_OK) e = cuda_status(cudaEventElapsedTime(&ms, t->kev[2], t->kev[3]));
+        if (e != TP_OK) return e;
+        *vjp_ms = ms;
+    }
+    return TP_OK;
+}
+
 tp_status tp_tree_free(tp_tree *t)
 {
     if (!t) return TP_OK;
     if (t->last) cudaStreamSynchronize(t->last);
     else cudaDeviceSynchronize();
+    for (auto &e : t->kev)
+        if (e) cudaEventDestroy(e);
     t->lists.release();
     t->pad.release();
     t->items.release();

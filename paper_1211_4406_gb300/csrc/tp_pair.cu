@@ -250,9 +250,9 @@ __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4
 }
 
 // g and g'/xi for two pairs at once, in the cancellation-free forms
-// g = u^5 h + v^6 c and g'/xi = -u^4 q - (8/5) v^5 (xi + 2), with u = max(0,
+// g = u^5 h + v^6 c and g'/xi = u^4 q' - (8/5) v^5 (xi + 2), with u = max(0,
 // 2 - xi), v = max(0, 1 - xi), h = (7 xi^3 + 22 xi^2 + 10 xi + 4)/140,
-// c = (7 xi^2 + 18 xi + 3)/35, q = (2 xi^2 + 4 xi - 1)/5.
+// c = (7 xi^2 + 18 xi + 3)/35, q' = -(2 xi^2 + 4 xi - 1)/5.
 __device__ __forceinline__ void g_gpx_packed(f2 x, f2 &g, f2 &gp)
 {
     const f2 u = f2relu(f2sub(f2pack(2.f, 2.f), x));
@@ -262,21 +262,13 @@ __device__ __forceinline__ void g_gpx_packed(f2 x, f2 &g, f2 &gp)
     h = f2fma(h, x, f2pack(4.f / 140.f, 4.f / 140.f));
     f2 c = f2fma(f2pack(7.f / 35.f, 7.f / 35.f), x, f2pack(18.f / 35.f, 18.f / 35.f));
     c = f2fma(c, x, f2pack(3.f / 35.f, 3.f / 35.f));
-    f2 q = f2fma(f2pack(2.f / 5.f, 2.f / 5.f), x, f2pack(4.f / 5.f, 4.f / 5.f));
-    q = f2fma(q, x, f2pack(-1.f / 5.f, -1.f / 5.f));
+    f2 q = f2fma(f2pack(-2.f / 5.f, -2.f / 5.f), x, f2pack(-4.f / 5.f, -4.f / 5.f));
+    q = f2fma(q, x, f2pack(1.f / 5.f, 1.f / 5.f));
     const f2 u2 = f2mul(u, u), u4 = f2mul(u2, u2), v2 = f2mul(v, v), v4 = f2mul(v2, v2);
     const f2 v5 = f2mul(v4, v);
     g = f2fma(f2mul(v4, v2), c, f2mul(f2mul(u4, u), h));
-    const f2 t = f2mul(v5, f2add(x, f2pack(2.f, 2.f)));
-    gp = f2fma(f2pack(-8.f / 5.f, -8.f / 5.f), t, f2mul(f2pack(-1.f, -1.f), f2mul(u4, q)));
-}
-
-// 1 for r2 > 0, 0 for the pair of a particle with itself (or a coincident one).
-__device__ __forceinline__ f2 nonzero_mask(f2 r2)
-{
-    float a, b;
-    f2unpack(f2mul(r2, f2pack(1.0e38f, 1.0e38f)), a, b);
-    return f2pack(fminf(a, 1.f), fminf(b, 1.f));
+    const f2 xp = f2fma(x, f2pack(-8.f / 5.f, -8.f / 5.f), f2pack(-16.f / 5.f, -16.f / 5.f));
+    gp = f2fma(v5, xp, f2mul(u4, q));
 }
 
 // hi + lo += x with the rounding error of the addition kept in lo (Knuth's
@@ -702,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                     e = T.ent[G.e0 + q];
                     r = T.rec[G.e0 + q];
                 }
-                const f2 XJ = f2pack(r.x, r.x), YJ = f2pack(r.y, r.y), ZJ = f2pack(r.z, r.z), MJ = f2pack(r.w, r.w);
+                const f2 XJ = f2pack(r.x, r.x), YJ = f2pack(r.y, r.y), ZJ = f2pack(r.z, r.z);
                 const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
                 f2 vx = f2pack(0.f, 0.f), vy = vx, vz = vx;
                 for (int pp = 0; pp < npe; pp += 2) {
@@ -722,13 +714,12 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                         const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
                         f2 gv, gp;
                         g_gpx_packed(x, gv, gp);
-                        const f2 ri2 = f2mul(ri, ri), ri3 = f2mul(ri2, ri);
-                        const f2 phi = f2mul(gv, ri3);
-                        const f2 psi = f2mul(ri3, f2fma(gv, f2mul(M3, ri2), gp));
-                        const f2 m = f2mul(MJ, nonzero_mask(r2));
+                        const f2 ri2 = f2mul(ri, ri);
+                        // m_j / s'^3, zero for the particle itself (and coincident pairs)
+                        const f2 mr3 = f2mul(f2pack(r2a > 0.f ? r.w : 0.f, r2b > 0.f ? r.w : 0.f), f2mul(ri2, ri));
                         const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
-                        const f2 alpha = f2mul(m, phi);
-                        const f2 beta = f2mul(f2mul(m, psi), dw);
+                        const f2 alpha = f2mul(gv, mr3);                       // m phi
+                        const f2 beta = f2mul(f2mul(f2fma(gv, f2mul(M3, ri2), gp), mr3), dw);   // m psi (d.w)
                         vx = f2fma(beta, dx, f2fma(alpha, WX, vx));
                         vy = f2fma(beta, dy, f2fma(alpha, WY, vy));
                         vz = f2fma(beta, dz, f2fma(alpha, WZ, vz));
@@ -854,7 +845,7 @@ int num_sms()
 }
 
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
-                      cudaStream_t s)
+                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     if (G <= 0) return;
     cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
@@ -868,7 +859,9 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
     };
+    if (ev0) cudaEventRecord(ev0, s);
     TP_LAUNCH(k_pair_packed, grid_of(bpp), kThreads, 0, s, T, acc, queue + 1, order);
+    if (ev1) cudaEventRecord(ev1, s);
     auto k = k_pair<float, true>;
     TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
 }
@@ -883,7 +876,8 @@ void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s)
 
 template <class R>
 static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double *ncot,
-                     int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
+                     int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                     cudaEvent_t ev1 = nullptr)
 {
     cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)T.n, s);
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
@@ -901,8 +895,10 @@ static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double 
         };
         if (sizeof(R) == 4) {
             cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+            if (ev0) cudaEventRecord(ev0, s);
             TP_LAUNCH(k_vjp_fused, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1,
                       order);
+            if (ev1) cudaEventRecord(ev1, s);
         } else {
             cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
         }
@@ -914,9 +910,9 @@ static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double 
 }
 
 void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s)
+             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
 {
-    vjp_impl<float>(T, cot, grad, gs, ncot, queue, order, G, s);
+    vjp_impl<float>(T, cot, grad, gs, ncot, queue, order, G, s, ev0, ev1);
 }
 
 void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,

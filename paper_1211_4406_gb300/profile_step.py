@@ -7,16 +7,87 @@ profilers (ncu launch lists and single-kernel captures).
 r_cut = 3/128); smaller n keeps the recipe (halo count, r_cut and eps scale
 with n).  The allocating build runs first; each step is rebuild + force +
 adjoint (or only the force / only the adjoint).
+
+  python -m paper_1211_4406_gb300.profile_step --record-traffic CSV --n N
+
+reads an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum /
+gpu__time_duration.sum for the pair kernels (taken on this command with --n N)
+and writes the per-launch DRAM traffic, with the digest of the device code it
+was measured on, to profiles/kernel_traffic.json.
 """
 from __future__ import annotations
 
 import argparse
-
-import torch
+import csv
+import hashlib
+import json
+import os
 
 from . import build as _build
 from . import inputs
-from .api import Params, ShortRangeTree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+TRAFFIC_KERNELS = ("k_pair_packed", "k_vjp_fused")
+
+
+def kernel_source_digest() -> str:
+    """SHA-256 of the pair kernels' device code: the shared header and the
+    part of tp_pair.cu before its host launch functions."""
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    h = hashlib.sha256()
+    h.update(open(os.path.join(csrc, "tp_common.cuh"), "rb").read())
+    src = open(os.path.join(csrc, "tp_pair.cu"), "rb").read()
+    cut = src.find(b"\nnamespace tp {")
+    h.update(src if cut < 0 else src[:cut])
+    return h.hexdigest()
+
+
+def record_traffic(csv_path: str, n: int) -> dict:
+    rows = list(csv.reader(open(csv_path)))
+    hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    hdr = rows[hi]
+    ki, mi, ni = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Name")
+    per = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= mi:
+            continue
+        name = r[ki].split("(")[0].replace("<unnamed>::", "")
+        if name not in TRAFFIC_KERNELS:
+            continue
+        d = per.setdefault((name, r[0]), {})
+        d[r[ni]] = float(r[mi].replace(",", ""))
+    out = {}
+    for (name, _), d in per.items():
+        k = out.setdefault(name, {"launches": 0, "dram_bytes": 0.0, "ns": 0.0})
+        k["launches"] += 1
+        k["dram_bytes"] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
+        k["ns"] += d.get("gpu__time_duration.sum", 0.0)
+    rec = {"n": n, "digest": kernel_source_digest(),
+           "kernels": {k: {"bytes_per_launch": v["dram_bytes"] / v["launches"],
+                           "ncu_ms_per_launch": v["ns"] / v["launches"] / 1e6}
+                       for k, v in out.items()},
+           "command": ("ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                       "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused\" -c 2 --csv --log-file "
+                       f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1")}
+    os.makedirs(os.path.dirname(TRAFFIC_JSON), exist_ok=True)
+    with open(TRAFFIC_JSON, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` at particle count n, or None when no
+    capture exists for n or the device code has changed since it was taken."""
+    try:
+        rec = json.load(open(TRAFFIC_JSON))
+    except (OSError, ValueError):
+        return None
+    if rec.get("n") != n or rec.get("digest") != kernel_source_digest():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("bytes_per_launch")
 
 
 def main():
@@ -24,7 +95,14 @@ def main():
     ap.add_argument("--n", type=int, default=128 ** 3)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--what", default="step", choices=["step", "force", "vjp"])
+    ap.add_argument("--record-traffic", metavar="CSV")
     args = ap.parse_args()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.n)))
+        return
+    import torch
+
+    from .api import Params, ShortRangeTree
     _build.build()
     box = inputs.config_box(2, n_override=args.n)
     pos = torch.tensor(box.pos, device="cuda")
