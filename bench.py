@@ -382,6 +382,193 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _timed_replays(fn, steps, flush, stream):
+    """Per-call device times (ms) of fn() over `steps` calls, L2 flushed before each."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    return out
+
+
+def run_batched(args, rank, world, local_rank):
+    """64 independent periodic boxes (sizes log-uniform in [16^3, 96^3], even
+    boxes uniform, odd boxes clustered), n_crit per box from the autotuner, the
+    whole step (rebuild + FP32 force + FP32 adjoint of every box) captured in
+    one CUDA graph and timed as one replay."""
+    import torch
+
+    from paper_1211_4406_gb300 import autotune
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import CapturedStep, Params, ShortRangeTree, launch_count
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    boxes = inputs.batched_boxes(64)
+    kinds = ["uniform" if b % 2 == 0 else "clustered" for b in range(64)]
+    base = [Params(b.G, b.eps, b.r_cut, b.theta, 64, 8, "fp32") for b in boxes]
+    t0 = time.perf_counter()
+    ncrit = autotune.tune_boxes(boxes, kinds, base, reps=2)
+    t_tune = time.perf_counter() - t0
+    prm = [Params(b.G, b.eps, b.r_cut, b.theta, c, 8, "fp32") for b, c in zip(boxes, ncrit)]
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
+    pos_h = torch.tensor(np.concatenate([b.pos for b in boxes])).pin_memory()
+    mass_h = torch.tensor(np.concatenate([b.mass for b in boxes])).pin_memory()
+    cot_h = torch.tensor(np.concatenate([inputs.cotangent(b.n, b.seed + 7) for b in boxes])).pin_memory()
+    pos, mass, cot = pos_h.to(dev), mass_h.to(dev), cot_h.to(dev)
+    tree = ShortRangeTree(pos, mass, prm, box_offsets=offs.tolist())
+    st = tree.stats()
+    n = tree.n
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    l0 = launch_count()
+    step = CapturedStep(tree, pos, mass, cot, acc, grad)      # warm-up body + captured body
+    per_replay = (launch_count() - l0) // 2
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    if tree.status() != 0:
+        raise RuntimeError("tree status after warm-up replays")
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    ms = _timed_replays(step.replay, args.steps, flush, stream)
+    clk = clocks.stop()
+    if tree.status() != 0:
+        raise RuntimeError("tree status after the timed replays")
+    acc_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    grad_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+
+    def e2e():
+        pos.copy_(pos_h, non_blocking=True)
+        mass.copy_(mass_h, non_blocking=True)
+        cot.copy_(cot_h, non_blocking=True)
+        step.replay()
+        acc_h.copy_(acc, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    e2e_ms = _timed_replays(e2e, args.steps, flush, stream)
+    inter = int(st["n_interactions"])
+    tot_ms, tot_e2e = max_over_ranks([sum(ms), sum(e2e_ms)], device=dev)
+    value = whole_job_rate(world, 2 * inter, args.steps, tot_ms)
+    e2e_value = whole_job_rate(world, 2 * inter, args.steps, tot_e2e)
+    tree.close()
+    if rank != 0:
+        return
+    hist = {}
+    for c in ncrit:
+        hist[str(c)] = hist.get(str(c), 0) + 1
+    line = {
+        "metric": METRIC.replace("clustered 2M box", "64 batched boxes"), "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched-64", "nbox": 64, "n_total": int(n), "n_min": int(min(b.n for b in boxes)),
+                   "n_max": int(max(b.n for b in boxes)), "kinds": "even uniform, odd clustered",
+                   "r_cut": "3/N_b^(1/3)", "eps": "1/(50 N_b^(1/3))", "theta": 0.5,
+                   "n_crit_autotuned": hist, "graph": "rebuild + force + adjoint of all boxes in one replay",
+                   "l2": "flushed (256 MiB write) before every timed replay"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": pos_h.numel() * 8 + mass_h.numel() * 8
+                + cot_h.numel() * 4, "d2h_bytes_per_step": acc_h.numel() * 4 + grad_h.numel() * 8,
+                "ms_per_step": tot_e2e / args.steps},
+        "gpu_launches": per_replay * args.steps, "clocks": clk,
+        "autotune_s": t_tune,
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "mean_ni",
+                                    "mean_nj", "max_nj", "nbox")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_uniform_fp64(args, rank, world, local_rank):
+    """The plain FP64 path (FP64 pair arithmetic, same tree and lists) on the
+    uniform 32^3 box: rebuild + FP64 force + FP64 adjoint per step, with the
+    FP32 path's step time on the same box beside it."""
+    import torch
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    box = inputs.config_box(1)
+    pos_h = torch.tensor(box.pos).pin_memory()
+    mass_h = torch.tensor(box.mass).pin_memory()
+    cot_h = torch.tensor(inputs.cotangent(box.n, box.seed + 7)).pin_memory()
+    pos, mass = pos_h.to(dev), mass_h.to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for prec, adt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        tree = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit,
+                                                box.n_leaf, prec))
+        cot = cot_h.to(dev).to(adt)
+        acc = torch.empty((box.n, 3), dtype=adt, device=dev)
+        grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
+
+        def step():
+            tree.rebuild(pos, mass)
+            tree.force(acc)
+            tree.vjp(cot, grad)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        l0 = launch_count()
+        ms = _timed_replays(step, args.steps, flush, stream)
+        res[prec] = {"ms": ms, "launches": launch_count() - l0, "stats": tree.stats(),
+                     "status": tree.status()}
+        if prec == "fp64":
+            def e2e():
+                pos.copy_(pos_h, non_blocking=True)
+                mass.copy_(mass_h, non_blocking=True)
+                cot.copy_(cot_h.to(adt), non_blocking=True)
+                step()
+                acc.cpu()
+                grad.cpu()
+            res["e2e_ms"] = _timed_replays(e2e, args.steps, flush, stream)
+        tree.close()
+        if res[prec]["status"] != 0:
+            raise RuntimeError(f"{prec} tree status {res[prec]['status']}")
+    inter = int(res["fp64"]["stats"]["n_interactions"])
+    tot_ms, tot_e2e = max_over_ranks([sum(res["fp64"]["ms"]), sum(res["e2e_ms"])], device=dev)
+    value = whole_job_rate(world, 2 * inter, args.steps, tot_ms)
+    if rank != 0:
+        return
+    st = res["fp64"]["stats"]
+    fp32_ms = sum(res["fp32"]["ms"]) / args.steps
+    line = {
+        "metric": "short-range interactions/s (plain FP64 forward + adjoint, uniform 32^3 box)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "uniform-32k", "n": box.n, "r_cut": "3/32", "eps": "1/1600", "theta": 0.5,
+                   "n_crit": box.n_crit, "n_leaf": box.n_leaf, "seed": box.seed,
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "e2e": {"value": whole_job_rate(world, 2 * inter, args.steps, tot_e2e), "unit": UNIT,
+                "h2d_bytes_per_step": box.n * (24 + 8 + 24), "d2h_bytes_per_step": box.n * (24 + 24),
+                "ms_per_step": tot_e2e / args.steps},
+        "gpu_launches": res["fp64"]["launches"],
+        "fp32_step_ms": fp32_ms, "fp32_over_fp64_step_speedup": (tot_ms / args.steps) / fp32_ms,
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "mean_ni",
+                                    "mean_nj", "max_nj")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,11 +576,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="clustered-2M", choices=list(WORKLOADS),
+                    help="clustered-2M (the default line); batched-64: 64 independent boxes, "
+                         "autotuned n_crit, the whole step as one CUDA-graph replay; uniform-32k: "
+                         "the plain FP64 path on the uniform 32^3 box")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.workload != "clustered-2M":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  f"the oracle arm is timed on the clustered-2M workload only"}))
+            return
         run_reference(args, rank, world)
         return
     if world > 1:
@@ -402,7 +598,7 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        WORKLOADS[args.workload](args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -3,7 +3,7 @@
 Bit-exact: Morton keys, permutation, octree nodes (topology, FP64 monopoles
 and boxes), groups and interaction lists.  Within tolerance (written below):
 forces on identical lists (FP32 rms <= 1e-6 and max <= 1e-4 relative; FP64
-rms <= 1e-12), the adjoint, and theta = 0.5 forces against the direct sum.
+rms <= 1e-8), the adjoint, and theta = 0.5 forces against the direct sum.
 """
 import numpy as np
 import pytest
