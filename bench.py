@@ -566,7 +566,113 @@ def run_uniform_fp64(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64}
+def run_large(args, rank, world, local_rank):
+    """The throughput workload at the paper's per-node load: N = 512^3
+    clustered particles (10^5 NFW halos), r_cut = 3/512, eps = 1/25600,
+    theta = 0.5, FP32 forward + adjoint.  Its lists (~1.2e10 entries) do not
+    fit in device memory, so the tree runs in chunked mode (windows of groups
+    with bounded list memory, planned once per step)."""
+    import torch
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    box = inputs.config_box(5)
+    w = inputs.cotangent(box.n, box.seed + 7)
+    t_gen = time.perf_counter() - t0
+    pos_h = torch.from_numpy(box.pos).pin_memory()
+    mass_h = torch.from_numpy(box.mass).pin_memory()
+    cot_h = torch.from_numpy(w).pin_memory()
+    pos, mass, cot = pos_h.to(dev), mass_h.to(dev), cot_h.to(dev)
+    t0 = time.perf_counter()
+    tree = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf,
+                                            "fp32"))
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    st = tree.stats()
+    acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        tree.rebuild(pos, mass)
+        tree.force(acc)
+        tree.vjp(cot, grad)
+    torch.cuda.synchronize()
+    if tree.status() != 0:
+        raise RuntimeError(f"tree status {tree.status()} after warm-up")
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    l0 = launch_count()
+    phases = []
+    for _ in range(args.steps):
+        e = [ev() for _ in range(4)]
+        e[0].record(stream)
+        tree.rebuild(pos, mass)
+        e[1].record(stream)
+        tree.force(acc)
+        e[2].record(stream)
+        tree.vjp(cot, grad)
+        e[3].record(stream)
+        e[3].synchronize()
+        phases.append([e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])])
+    launches = launch_count() - l0
+    clk = clocks.stop()
+    if tree.status() != 0:
+        raise RuntimeError("tree status after the timed steps")
+    st = tree.stats()
+    acc_h = torch.empty((box.n, 3), dtype=torch.float32).pin_memory()
+    grad_h = torch.empty((box.n, 3), dtype=torch.float64).pin_memory()
+
+    def e2e():
+        pos.copy_(pos_h, non_blocking=True)
+        mass.copy_(mass_h, non_blocking=True)
+        cot.copy_(cot_h, non_blocking=True)
+        tree.rebuild(pos, mass)
+        tree.force(acc)
+        tree.vjp(cot, grad)
+        acc_h.copy_(acc, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    e2e_ms = _timed_replays(e2e, 1, flush, stream)
+    inter = int(st["n_interactions"])
+    step_ms = [sum(p) for p in phases]
+    tot_ms, tot_e2e = max_over_ranks([sum(step_ms), sum(e2e_ms) * args.steps], device=dev)
+    value = whole_job_rate(world, 2 * inter, args.steps, tot_ms)
+    tree.close()
+    if rank != 0:
+        return
+    mean = lambda i: sum(p[i] for p in phases) / len(phases)
+    line = {
+        "metric": METRIC.replace("clustered 2M box", "clustered 134M box"), "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "clustered-134M", "n": box.n, "halos": 100000, "r_cut": "3/512",
+                   "eps": "1/25600", "theta": 0.5, "n_crit": box.n_crit, "n_leaf": box.n_leaf, "seed": box.seed,
+                   "lists": f"chunked: {st['n_windows']} windows of groups",
+                   "l2": "inputs (4.3 GB of positions and masses) larger than L2"},
+        "e2e": {"value": whole_job_rate(world, 2 * inter, args.steps, tot_e2e), "unit": UNIT,
+                "h2d_bytes_per_step": box.n * (24 + 8 + 12), "d2h_bytes_per_step": box.n * (12 + 24),
+                "ms_per_step": tot_e2e / args.steps},
+        "gpu_launches": launches, "clocks": clk,
+        "phases_ms": {"build": mean(0), "force_fp32": mean(1), "vjp_fp32": mean(2)},
+        "forward_interactions_per_s": inter / (mean(1) * 1e-3),
+        "adjoint_interactions_per_s": inter / (mean(2) * 1e-3),
+        "setup_s": {"generate_inputs": t_gen, "allocating_build": t_build},
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "mean_ni",
+                                    "mean_nj", "max_nj", "n_windows")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64,
+             "clustered-134M": run_large}
 
 
 def main():
@@ -579,7 +685,8 @@ def main():
     ap.add_argument("--workload", default="clustered-2M", choices=list(WORKLOADS),
                     help="clustered-2M (the default line); batched-64: 64 independent boxes, "
                          "autotuned n_crit, the whole step as one CUDA-graph replay; uniform-32k: "
-                         "the plain FP64 path on the uniform 32^3 box")
+                         "the plain FP64 path on the uniform 32^3 box; clustered-134M: "
+                         "the 512^3 throughput box (chunked lists)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

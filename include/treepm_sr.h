@@ -66,21 +66,39 @@ typedef enum { TP_FP64 = 0, TP_FP32 = 1 } tp_precision;
  *   n_leaf  a tree node holding more than n_leaf particles is split, 1..64
  *   precision  TP_FP32 (pair arithmetic in FP32 on group-relative
  *           coordinates) or TP_FP64 (plain FP64 reference path)
- *   flags   reserved, must be 0                                              */
+ *   flags   0 or TP_FLAG_CHUNKED                                             */
 typedef struct {
     double G, eps, r_cut, theta;
     int32_t n_crit, n_leaf, precision, flags;
 } tp_params;
 
+/* Bounded list memory (a property of this implementation; the paper builds
+ * each group's list as it goes).  Normally every group's interaction list is
+ * kept on the device (20 bytes per entry).  In chunked mode the walk and the
+ * pair kernels run over windows of consecutive groups whose lists fit a fixed
+ * budget of 2^29 entries (about 11 GB), so a box whose lists would not fit in
+ * device memory can still be evaluated; the lists are not kept between calls
+ * (tp_export_lists returns TP_ERR_INVALID_ARG), every force/vjp call re-walks
+ * each window, and a force/vjp call after tp_rebuild_tree synchronises the
+ * stream once to plan the windows (so it cannot be captured in a CUDA graph).
+ * The build switches to chunked mode by itself when the lists would need more
+ * than 2^30 entries; setting TP_FLAG_CHUNKED in any box's flags forces it (with
+ * windows of about a quarter of the lists, which also exercises the mode on
+ * small boxes).  Results are the same as with whole lists.                  */
+#define TP_FLAG_CHUNKED 1
+
 typedef struct tp_tree tp_tree; /* opaque, library-owned */
 
 /* Statistics of a built tree (Table I reports the same quantities).
- * n_interactions = sum over groups of n_i * n_j, the paper's count.        */
+ * n_interactions = sum over groups of n_i * n_j, the paper's count.  In
+ * chunked mode the list quantities are those of the last build or force
+ * call.                                                                     */
 typedef struct {
     int64_t n, n_nodes, n_groups, n_entries, n_interactions;
     int64_t n_ambiguous;   /* walk decisions settled by the exact FP64 test  */
     double mean_ni, mean_nj;
     int32_t max_nj, nbox;
+    int64_t n_windows;     /* group windows of chunked mode; 1 otherwise     */
 } tp_stats;
 
 /* Build the tree of one box: Morton keys, sort, octree, monopoles, groups

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libtreepm_sr.so")
 TP_OK = 0
 TP_FP64 = 0
 TP_FP32 = 1
+TP_FLAG_CHUNKED = 1
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device out of memory",
           -4: "capacity overflow", -5: "device wait timed out", -6: "non-finite position",
           -7: "no CUDA device"}
@@ -30,7 +31,7 @@ class TPStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_nodes", C.c_int64), ("n_groups", C.c_int64),
                 ("n_entries", C.c_int64), ("n_interactions", C.c_int64), ("n_ambiguous", C.c_int64),
                 ("mean_ni", C.c_double), ("mean_nj", C.c_double), ("max_nj", C.c_int32),
-                ("nbox", C.c_int32)]
+                ("nbox", C.c_int32), ("n_windows", C.c_int64)]
 
 
 class TreeSRError(RuntimeError):

@@ -41,10 +41,13 @@ class Params:
     n_crit: int = 64
     n_leaf: int = 8
     precision: str = "fp32"
+    chunked: bool = False     # force the bounded-list-memory mode (TP_FLAG_CHUNKED)
 
     def c(self) -> _lib.TPParams:
-        return _lib.params(self.G, self.eps, self.r_cut, self.theta, self.n_crit, self.n_leaf,
-                           self.precision)
+        p = _lib.params(self.G, self.eps, self.r_cut, self.theta, self.n_crit, self.n_leaf,
+                        self.precision)
+        p.flags = _lib.TP_FLAG_CHUNKED if self.chunked else 0
+        return p
 
 
 class ShortRangeTree:

@@ -19,6 +19,13 @@ void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
 void walk_expand(TreeDev &T, unsigned long long *counter, void *scan_tmp, cudaStream_t s);
 void walk_write(TreeDev &T, cudaStream_t s);
+void walk_top_scan(TreeDev &T, void *scan_tmp, cudaStream_t s);
+void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s);
+void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
+                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
+                   const int32_t *order, int64_t G, cudaStream_t s);
+void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s);
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
@@ -146,6 +153,11 @@ struct tp_tree {
     int32_t *d_maxnj = nullptr;
     // host copies of the sizes (valid after a synchronising build)
     int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_pad = 0, h_entries = 0;
+    // chunked mode: windows [first group, group count) with lists of bounded size
+    bool chunked = false, force_chunked = false, windows_stale = true;
+    std::vector<int64_t> win_first, win_count;
+    int64_t *d_wsz = nullptr;         // [kMaxWindows] device copies of the window sizes
+    int64_t *d_etot = nullptr;        // entries summed over the windows
     // kernel timing: events around the main forward / adjoint kernel launches
     bool ktiming = false, kf_rec = false, kv_rec = false;
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -197,6 +209,7 @@ static bool alloc_groups(tp_tree *t, int64_t cap)
     D.gX = P.get<uint64_t>(c); D.gY = P.get<uint64_t>(c); D.gZ = P.get<uint64_t>(c);
     D.loff = P.get<int64_t>(c + 1);
     D.lcnt = P.get<int32_t>(c);
+    D.gpad = P.get<int32_t>(c);
     D.icnt = P.get<int32_t>(c);
     D.ioff = P.get<int64_t>(c);
     t->lpt_key = P.get<uint64_t>(c);
@@ -256,7 +269,7 @@ static tp_status validate(const tp_params &p)
     if (!std::isfinite(p.G)) return TP_ERR_INVALID_ARG;
     if (p.n_crit < 1 || p.n_crit > 4096 || p.n_leaf < 1 || p.n_leaf > 64) return TP_ERR_INVALID_ARG;
     if (p.precision != TP_FP32 && p.precision != TP_FP64) return TP_ERR_INVALID_ARG;
-    if (p.flags != 0) return TP_ERR_INVALID_ARG;
+    if (p.flags != 0 && p.flags != TP_FLAG_CHUNKED) return TP_ERR_INVALID_ARG;
     return TP_OK;
 }
 
@@ -282,6 +295,141 @@ __global__ void k_check_entries(TreeDev T)
 {
     if (*T.n_entries > T.cap_entries) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
     if (*T.n_groups > T.cap_groups) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+}
+
+// ---------------------------------------------------------------------------
+// Chunked mode.  A window of consecutive groups is evaluated through a view of
+// the tree whose group arrays start at the window's first group and whose
+// group count is the window's size, so every walk and pair kernel runs on it
+// unchanged, with its items, padded slots and lists reusing the same buffers.
+constexpr int64_t kChunkSlots = 1ll << 30;   // whole lists above this many padded slots: chunked
+constexpr int64_t kWindowSlots = 1ll << 29;  // padded-slot budget of one window
+constexpr int kMaxWindows = 1 << 16;
+
+static TreeDev window_view(const TreeDev &D, int64_t g0, int64_t ng, int64_t *d_ng)
+{
+    TreeDev V = D;
+    V.gfirst += g0; V.gcount += g0; V.gbox += g0;
+    V.gcx += g0; V.gcy += g0; V.gcz += g0; V.ghx += g0; V.ghy += g0; V.ghz += g0;
+    V.gux += g0; V.guy += g0; V.guz += g0; V.ghux += g0; V.ghuy += g0; V.ghuz += g0;
+    V.gX += g0; V.gY += g0; V.gZ += g0;
+    V.gpad += g0; V.loff += g0; V.lcnt += g0; V.icnt += g0; V.ioff += g0;
+    V.n_groups = d_ng;
+    V.cap_groups = ng;
+    return V;
+}
+
+// Greedy windows over the groups' item counts and padded-slot bounds (from
+// the count pass of the top walk): consecutive groups while both sums stay
+// within the budgets; a group that alone exceeds them gets a window of its own
+// (its walk then latches TP_ERR_LIST_OVERFLOW).  Synchronises.
+static tp_status plan_windows(tp_tree *t, cudaStream_t s, int64_t slot_budget, int64_t item_budget,
+                              int64_t *max_slots, int64_t *max_items)
+{
+    TreeDev &D = t->D;
+    int64_t G = 0;
+    tp_status e = cuda_status(cudaMemcpyAsync(&G, D.n_groups, sizeof(G), cudaMemcpyDeviceToHost, s));
+    if (e == TP_OK) e = cuda_status(cudaStreamSynchronize(s));
+    if (e != TP_OK) return e;
+    if (G > D.cap_groups) G = D.cap_groups;
+    std::vector<int32_t> ic((size_t)(G > 0 ? G : 1)), gp((size_t)(G > 0 ? G : 1));
+    if (G > 0) {
+        e = cuda_status(cudaMemcpy(ic.data(), D.icnt, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
+        if (e == TP_OK) e = cuda_status(cudaMemcpy(gp.data(), D.gpad, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
+        if (e != TP_OK) return e;
+    }
+    t->win_first.clear();
+    t->win_count.clear();
+    int64_t g0 = 0, slots = 0, items = 0, ms = 0, mi = 0;
+    for (int64_t g = 0; g <= G; g++) {
+        const bool close = g == G || (g > g0 && (slots + gp[g] > slot_budget || items + ic[g] > item_budget));
+        if (close && g > g0) {
+            t->win_first.push_back(g0);
+            t->win_count.push_back(g - g0);
+            ms = slots > ms ? slots : ms;
+            mi = items > mi ? items : mi;
+            g0 = g;
+            slots = items = 0;
+        }
+        if (g < G) {
+            slots += gp[g];
+            items += ic[g];
+        }
+    }
+    if ((int64_t)t->win_count.size() > kMaxWindows) return TP_ERR_LIST_OVERFLOW;
+    if (!t->win_count.empty()) {
+        e = cuda_status(cudaMemcpyAsync(t->d_wsz, t->win_count.data(), sizeof(int64_t) * t->win_count.size(),
+                                        cudaMemcpyHostToDevice, s));
+        if (e != TP_OK) return e;
+    }
+    if (max_slots) *max_slots = ms;
+    if (max_items) *max_items = mi;
+    t->windows_stale = false;
+    return TP_OK;
+}
+
+__global__ void k_add_entries(TreeDev V, int64_t *tot) { *tot += *V.n_entries; }
+
+// The walk of one window: items, tasks, lists and records, LPT order; list
+// statistics accumulate into the tree's counters.
+static void walk_window(tp_tree *t, TreeDev &V, cudaStream_t s)
+{
+    tp::walk_top_scan(V, t->scan_tmp, s);
+    TP_LAUNCH(k_check_items, 1, 1, 0, s, V);
+    tp::walk_items(V, t->split, t->scan_tmp, s);
+    TP_LAUNCH(k_check_pad, 1, 1, 0, s, V);
+    tp::walk_expand(V, reinterpret_cast<unsigned long long *>(t->queue + 2), t->scan_tmp, s);
+    TP_LAUNCH(k_check_entries, 1, 1, 0, s, V);
+    tp::walk_write(V, s);
+    tp::lpt_order(V, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
+                  t->lpt_tmp, s);
+    tp::list_stats(V, t->d_inter, t->d_maxnj, s);
+    TP_LAUNCH(k_add_entries, 1, 1, 0, s, V, t->d_etot);
+}
+
+static void reset_list_stats(tp_tree *t, cudaStream_t s)
+{
+    cudaMemsetAsync(t->d_inter, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(t->d_maxnj, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(t->d_etot, 0, sizeof(int64_t), s);
+}
+
+// Runs `body(view)` for every window (planning them first when the positions
+// changed since they were planned).
+template <class F>
+static tp_status for_each_window(tp_tree *t, cudaStream_t s, F body)
+{
+    if (t->windows_stale) {
+        tp_status e = plan_windows(t, s, t->D.cap_pad, t->D.cap_items, nullptr, nullptr);
+        if (e != TP_OK) return e;
+    }
+    reset_list_stats(t, s);
+    for (size_t w = 0; w < t->win_count.size(); w++) {
+        TreeDev V = window_view(t->D, t->win_first[w], t->win_count[w], t->d_wsz + w);
+        walk_window(t, V, s);
+        body(V);
+    }
+    return TP_OK;
+}
+
+// The allocating build's walk in chunked mode: plan windows of about
+// `budget` padded slots, size the item / slot / list buffers for the largest,
+// and walk every window once (capacity check and statistics).
+static tp_status build_chunked(tp_tree *t, cudaStream_t s, int64_t budget)
+{
+    TreeDev &D = t->D;
+    int64_t ms = 0, mi = 0;
+    tp_status e = plan_windows(t, s, budget, INT64_MAX, &ms, &mi);
+    if (e != TP_OK) return e;
+    if (mi > D.cap_items || D.item == nullptr)
+        if (!alloc_items(t, mi + 1024)) return TP_ERR_OOM;
+    if (ms > D.cap_pad || D.pent == nullptr)
+        if (!alloc_pad(t, ms + 1024)) return TP_ERR_OOM;
+    if (ms > D.cap_entries || D.ent == nullptr)
+        if (!alloc_lists(t, ms + 1024)) return TP_ERR_OOM;
+    e = for_each_window(t, s, [](TreeDev &) {});
+    if (e != TP_OK) return e;
+    return cuda_status(cudaStreamSynchronize(s));
 }
 
 // Launch everything after the keys: topology, groups, walk.  With `sync`
@@ -318,6 +466,31 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     tp::build_groups(D, t->flag, t->gofs, s);
     // walk: top items per group, then subtree tasks, then the entries
     tp::walk_top_count(D, t->split, t->scan_tmp, s);
+    if (!sync && t->chunked) {             // the next force/vjp call plans the windows
+        t->windows_stale = true;
+        return TP_OK;
+    }
+    if (sync) {
+        // whole lists, or windows of them when they would not fit
+        int64_t G = t->h_groups < D.cap_groups ? t->h_groups : D.cap_groups;
+        std::vector<int32_t> gp((size_t)(G > 0 ? G : 1));
+        if (G > 0) {
+            tp_status e = cuda_status(cudaMemcpyAsync(gp.data(), D.gpad, sizeof(int32_t) * G,
+                                                      cudaMemcpyDeviceToHost, s));
+            if (e == TP_OK) e = cuda_status(cudaStreamSynchronize(s));
+            if (e != TP_OK) return e;
+        }
+        int64_t total = 0, largest = 0;
+        for (int64_t g = 0; g < G; g++) {
+            total += gp[g];
+            largest = gp[g] > largest ? gp[g] : largest;
+        }
+        t->chunked = t->force_chunked || total > kChunkSlots;
+        if (t->chunked) {
+            int64_t budget = t->force_chunked ? total / 4 + 1 : kWindowSlots;
+            return build_chunked(t, s, budget > largest ? budget : largest);
+        }
+    }
     if (sync) {
         tp_status e = cuda_status(cudaMemcpyAsync(&t->h_items, D.n_items, sizeof(int64_t),
                                                   cudaMemcpyDeviceToHost, s));
@@ -385,6 +558,8 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     t->precision = per_box[0].precision;
     t->box_off.assign(box_offsets, box_offsets + nbox + 1);
     t->prm.assign(per_box, per_box + nbox);
+    for (int b = 0; b < nbox; b++)
+        if (per_box[b].flags & TP_FLAG_CHUNKED) t->force_chunked = true;
     t->last = s;
     TreeDev &D = t->D;
     std::memset(&D, 0, sizeof(D));
@@ -414,6 +589,8 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     t->gs = B.get<double>(3 * nn);
     t->d_inter = B.get<unsigned long long>(1);
     t->d_maxnj = B.get<int32_t>(1);
+    t->d_etot = B.get<int64_t>(1);
+    t->d_wsz = B.get<int64_t>(kMaxWindows);
     if (!B.ok) {
         tp_tree_free(t);
         return TP_ERR_OOM;
@@ -463,6 +640,19 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     t->last = s;
     if (t->n == 0) return TP_OK;
+    if (t->chunked) {
+        const bool f32 = t->precision == TP_FP32;
+        cudaMemsetAsync(acc, 0, (f32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)t->n, s);
+        t->kf_rec = false;
+        tp_status e = for_each_window(t, s, [&](TreeDev &V) {
+            if (f32)
+                tp::pair_forward_f32(V, (float *)acc, t->queue, t->order, V.cap_groups, s, nullptr, nullptr);
+            else
+                tp::pair_forward_f64(V, (double *)acc, V.cap_groups, s);
+        });
+        if (e != TP_OK) return e;
+        return cuda_status(cudaGetLastError());
+    }
     if (t->precision == TP_FP32) {
         cudaMemsetAsync(acc, 0, sizeof(float) * 3 * (size_t)t->n, s);
         tp::pair_forward_f32(t->D, (float *)acc, t->queue, t->order, t->D.cap_groups, s,
@@ -482,6 +672,21 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
     cudaStream_t s = (cudaStream_t)stream;
     t->last = s;
     if (t->n == 0) return TP_OK;
+    if (t->chunked) {
+        const bool f32 = t->precision == TP_FP32;
+        t->kv_rec = false;
+        tp::vjp_begin(t->D, t->gs, t->ncot, s);
+        tp_status e = for_each_window(t, s, [&](TreeDev &V) {
+            if (f32)
+                tp::vjp_pairs_f32(V, (const float *)cot, t->gs, t->ncot, t->queue, t->order, V.cap_groups, s,
+                                  nullptr, nullptr);
+            else
+                tp::vjp_pairs_f64(V, (const double *)cot, t->gs, t->ncot, t->queue, t->order, V.cap_groups, s);
+        });
+        if (e != TP_OK) return e;
+        tp::vjp_end(t->D, grad, t->gs, t->ncot, s);
+        return cuda_status(cudaGetLastError());
+    }
     if (t->precision == TP_FP32)
     {
         tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s,
@@ -508,9 +713,11 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
 {
     if (!t || !out) return TP_ERR_INVALID_ARG;
     cudaStream_t s = t->last;
-    cudaMemsetAsync(t->d_inter, 0, sizeof(unsigned long long), s);
-    cudaMemsetAsync(t->d_maxnj, 0, sizeof(int32_t), s);
-    if (t->D.gfirst) tp::list_stats(t->D, t->d_inter, t->d_maxnj, s);
+    if (!t->chunked) {
+        cudaMemsetAsync(t->d_inter, 0, sizeof(unsigned long long), s);
+        cudaMemsetAsync(t->d_maxnj, 0, sizeof(int32_t), s);
+        if (t->D.gfirst) tp::list_stats(t->D, t->d_inter, t->d_maxnj, s);
+    }
     unsigned long long inter = 0, amb = 0;
     int32_t mx = 0;
     int64_t nn = 0, ng = 0, ne = 0;
@@ -519,7 +726,7 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
     cudaMemcpyAsync(&mx, t->d_maxnj, sizeof(mx), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&nn, t->D.n_nodes, sizeof(nn), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&ng, t->D.n_groups, sizeof(ng), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&ne, t->D.n_entries, sizeof(ne), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&ne, t->chunked ? t->d_etot : t->D.n_entries, sizeof(ne), cudaMemcpyDeviceToHost, s);
     tp_status e = cuda_status(cudaStreamSynchronize(s));
     if (e != TP_OK) return e;
     if (t->n == 0) nn = ng = ne = 0;
@@ -533,6 +740,7 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
     out->mean_nj = ng ? (double)ne / (double)ng : 0.0;
     out->max_nj = mx;
     out->nbox = t->nbox;
+    out->n_windows = t->chunked ? (int64_t)t->win_count.size() : 1;
     return TP_OK;
 }
 
@@ -597,7 +805,7 @@ tp_status tp_export_groups(tp_tree *t, int64_t *ints, double *dbl)
 
 tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries)
 {
-    if (!t || !offsets) return TP_ERR_INVALID_ARG;
+    if (!t || !offsets || t->chunked) return TP_ERR_INVALID_ARG;
     tp_stats st;
     tp_status e = tp_tree_stats(t, &st);
     if (e != TP_OK) return e;

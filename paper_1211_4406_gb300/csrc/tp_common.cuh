@@ -79,6 +79,7 @@ struct TreeDev {
     double *gcx, *gcy, *gcz, *ghx, *ghy, *ghz;
     uint32_t *gux, *guy, *guz, *ghux, *ghuy, *ghuz;
     uint64_t *gX, *gY, *gZ;
+    int32_t *gpad;                    // [cap_groups] padded slots the group's walk needs (count pass)
     // walk items: subtree tasks and top-level monopoles, group-major, DFS order
     int64_t cap_items;
     int32_t *icnt;                    // [cap_groups] items per group

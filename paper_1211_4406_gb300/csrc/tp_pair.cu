@@ -874,51 +874,76 @@ void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s)
     TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, nullptr, nullptr);
 }
 
-template <class R>
-static void vjp_impl(TreeDev &T, const R *cot, double *grad, double *gs, double *ncot,
-                     int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                     cudaEvent_t ev1 = nullptr)
+// The adjoint in three stages so that a caller can run the pair stage once
+// per window of groups: zero the accumulators, the pair kernels, then the
+// push-down of node cotangents and the scatter to input order.
+void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s)
 {
     cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)T.n, s);
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
-    if (G > 0) {
-        // occupancies are queried once, outside any capture
-        static int nb = 0, nbf = 0;
-        if (nb == 0) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, k_vjp_fused, kThreads, 0);
-            nb = nb > 0 ? nb : 1; nbf = nbf > 0 ? nbf : 1;
-        }
-        auto grid_of = [&](int per_sm) {
-            int64_t gr = (int64_t)num_sms() * per_sm;
-            return (int)(gr > G ? G : gr);
-        };
-        if (sizeof(R) == 4) {
-            cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
-            if (ev0) cudaEventRecord(ev0, s);
-            TP_LAUNCH(k_vjp_fused, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1,
-                      order);
-            if (ev1) cudaEventRecord(ev1, s);
-        } else {
-            cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-        }
-        auto k = k_vjp<R>;
-        TP_LAUNCH(k, grid_of(nb), kThreads, 0, s, T, cot, gs, ncot, queue, order);
+}
+
+template <class R>
+static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
+                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    if (G <= 0) return;
+    // occupancies are queried once, outside any capture
+    static int nb = 0, nbf = 0;
+    if (nb == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, k_vjp_fused, kThreads, 0);
+        nb = nb > 0 ? nb : 1; nbf = nbf > 0 ? nbf : 1;
     }
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    if (sizeof(R) == 4) {
+        cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+        if (ev0) cudaEventRecord(ev0, s);
+        TP_LAUNCH(k_vjp_fused, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1,
+                  order);
+        if (ev1) cudaEventRecord(ev1, s);
+    } else {
+        cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    }
+    auto k = k_vjp<R>;
+    TP_LAUNCH(k, grid_of(nb), kThreads, 0, s, T, cot, gs, ncot, queue, order);
+}
+
+void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s)
+{
     TP_LAUNCH(k_pushdown, 152 * 4, 256, 0, s, T, gs, ncot);
     TP_LAUNCH(k_unsort3, grid_for(T.n, 256), 256, 0, s, T, gs, grad);
+}
+
+void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
+                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1);
+}
+
+void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
+                   const int32_t *order, int64_t G, cudaStream_t s)
+{
+    vjp_pairs<double>(T, cot, gs, ncot, queue, order, G, s, nullptr, nullptr);
 }
 
 void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
              const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
 {
-    vjp_impl<float>(T, cot, grad, gs, ncot, queue, order, G, s, ev0, ev1);
+    vjp_begin(T, gs, ncot, s);
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1);
+    vjp_end(T, grad, gs, ncot, s);
 }
 
 void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
              const int32_t *order, int64_t G, cudaStream_t s)
 {
-    vjp_impl<double>(T, cot, grad, gs, ncot, queue, order, G, s);
+    vjp_begin(T, gs, ncot, s);
+    vjp_pairs<double>(T, cot, gs, ncot, queue, order, G, s, nullptr, nullptr);
+    vjp_end(T, grad, gs, ncot, s);
 }
 
 }  // namespace tp

@@ -155,7 +155,7 @@ __device__ __forceinline__ bool keep_particle(const TreeDev &T, const WalkGroup 
 // pointers).  Returns the number of items; with out != nullptr writes them to
 // out[0 .. out_n).
 __device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start, int32_t split, int32_t *out,
-                            int64_t out_n, unsigned long long &ambig)
+                            int64_t out_n, unsigned long long &ambig, int64_t *slots = nullptr)
 {
     int32_t cnt = 0;
     int32_t nd = start;
@@ -174,10 +174,12 @@ __device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start,
         } else if (d == kAccept) {
             if (out && cnt < out_n) out[cnt] = -(nd + 1);
             cnt++;
+            if (slots) *slots += 1;
             nd = w.skip;
         } else if (w.child < 0 || w.count <= split) {
             if (out && cnt < out_n) out[cnt] = nd;       // a task: expand its subtree later
             cnt++;
+            if (slots) *slots += w.count;
             nd = w.skip;
         } else {
             nd = w.child;
@@ -197,7 +199,9 @@ __global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
          g += (int64_t)gridDim.x * blockDim.x) {
         const WalkGroup W = load_walk_group(T, g);
         if (!WRITE) {
-            T.icnt[g] = walk_top(T, W, T.gbox[g], split, nullptr, 0, ambig);
+            int64_t slots = 0;
+            T.icnt[g] = walk_top(T, W, T.gbox[g], split, nullptr, 0, ambig, &slots);
+            T.gpad[g] = slots < 0x7fffffff ? (int32_t)slots : 0x7fffffff;
         } else {
             const int64_t o = T.ioff[g];
             const int64_t n = T.icnt[g];
@@ -419,6 +423,13 @@ void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 {
     if (T.cap_groups <= 0) return;
     TP_LAUNCH(k_walk_top<false>, grid_for(T.cap_groups, kBlock), kBlock, 0, s, T, split);
+    scan_i32_to_i64(T.icnt, T.ioff, 0, T.n_groups, T.n_items, scan_tmp, s);
+}
+
+// Item offsets of the groups from their counts (already in T.icnt).
+void walk_top_scan(TreeDev &T, void *scan_tmp, cudaStream_t s)
+{
+    if (T.cap_groups <= 0) return;
     scan_i32_to_i64(T.icnt, T.ioff, 0, T.n_groups, T.n_items, scan_tmp, s);
 }
 
