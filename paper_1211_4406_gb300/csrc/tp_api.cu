@@ -576,6 +576,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     t->key2 = B.get<uint64_t>(nn); t->perm2 = B.get<uint32_t>(nn);
     D.x = B.get<double>(nn); D.y = B.get<double>(nn); D.z = B.get<double>(nn); D.m = B.get<double>(nn);
     D.X = B.get<uint64_t>(nn); D.Y = B.get<uint64_t>(nn); D.Z = B.get<uint64_t>(nn);
+    D.P32 = B.get<uint4>(nn);
     t->radix_tmp = B.get<char>(tp::radix_tmp_bytes(n));
     t->scan_tmp = B.get<char>(tp::scan_tmp_bytes());
     t->flag = B.get<uint32_t>(nn); t->gofs = B.get<uint32_t>(nn);

@@ -64,7 +64,9 @@ __global__ void k_gather(const double *pos, const double *mass, TreeDev T)
         const int64_t i = T.perm[s];
         const double x = wrap01(pos[3 * i]), y = wrap01(pos[3 * i + 1]), z = wrap01(pos[3 * i + 2]);
         T.x[s] = x; T.y[s] = y; T.z[s] = z;
-        T.X[s] = tp_fixed64(x); T.Y[s] = tp_fixed64(y); T.Z[s] = tp_fixed64(z);
+        const uint64_t X = tp_fixed64(x), Y = tp_fixed64(y), Z = tp_fixed64(z);
+        T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
+        T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
         T.m[s] = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
     }
 }

@@ -62,6 +62,7 @@ struct TreeDev {
     uint32_t *perm;
     double *x, *y, *z, *m;
     uint64_t *X, *Y, *Z;
+    uint4 *P32;                       // {X, Y, Z} >> 32 per particle: the walk's 2^-32 grid
     // nodes
     int32_t *first, *count, *child, *nchild, *parent, *skip, *nbx;
     uint8_t *level;

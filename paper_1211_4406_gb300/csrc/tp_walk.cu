@@ -138,9 +138,8 @@ __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W,
 // Whether particle p of an opened leaf enters the list: point-to-box gap < r_cut.
 __device__ __forceinline__ bool keep_particle(const TreeDev &T, const WalkGroup &W, int32_t p, int &namb)
 {
-    const uint32_t qx = absdiff32((uint32_t)(T.X[p] >> 32), W.gx);
-    const uint32_t qy = absdiff32((uint32_t)(T.Y[p] >> 32), W.gy);
-    const uint32_t qz = absdiff32((uint32_t)(T.Z[p] >> 32), W.gz);
+    const uint4 q = T.P32[p];
+    const uint32_t qx = absdiff32(q.x, W.gx), qy = absdiff32(q.y, W.gy), qz = absdiff32(q.z, W.gz);
     const uint64_t ex = qx > W.hx ? qx - W.hx : 0, ey = qy > W.hy ? qy - W.hy : 0, ez = qz > W.hz ? qz - W.hz : 0;
     const uint64_t p2 = ex * ex + ey * ey + ez * ez;
     if (p2 >= W.P->T_hi) return false;
@@ -230,9 +229,9 @@ __global__ void k_item_bounds(TreeDev T)
 // Each lane expands one item at a time by a stackless depth-first walk of the
 // task's subtree and takes its next item from a global counter as soon as it
 // is done, so lanes with short tasks do not wait for the warp's longest one.
-// Every loop iteration does one unit of work -- one node decision or one
-// particle test of an opened leaf -- so lanes at different stages of their
-// walks diverge by at most one branch per iteration.
+// Every loop iteration does one unit of work -- one node decision, or the
+// tests of the next two particles of an opened leaf -- so lanes at different
+// stages of their walks diverge by at most one branch per iteration.
 __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long long *counter)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
@@ -280,14 +279,21 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
         }
         if (__all_sync(full, exhausted)) break;
         if (it < 0) continue;
-        if (pcur < pend) {                             // one particle of an opened leaf
+        if (pcur < pend) {                             // one or two particles of an opened leaf
             int namb = 0;
-            if (keep_particle(T, W, pcur, namb)) {
+            const bool two = pcur + 1 < pend;
+            const bool k0 = keep_particle(T, W, pcur, namb);
+            const bool k1 = two && keep_particle(T, W, pcur + 1, namb);
+            if (k0) {
                 if (cnt < bound) out[cnt] = pcur;
                 cnt++;
             }
+            if (k1) {
+                if (cnt < bound) out[cnt] = pcur + 1;
+                cnt++;
+            }
             ambig += namb;
-            pcur++;
+            pcur += two ? 2 : 1;
         } else if (nd == end || nd < 0 || --budget < 0 || nd >= T.cap_nodes) {
             if (budget < 0 || (nd != end && nd >= T.cap_nodes)) tp_latch(T.status, TP_ERR_TIMEOUT);
             if (cnt > bound) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
