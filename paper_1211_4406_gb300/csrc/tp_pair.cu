@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kTile = 256;
+constexpr int kVjpEntries = 2;   // list entries per thread in the fused adjoint
 
 __device__ __forceinline__ float sqrt_approx(float x)
 {
@@ -639,8 +640,11 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // (four halving exchanges and one final one, 16 shuffles in all) so that each
 // lane pair ends with one total, written to the warp's row; the thread that
 // owns the particle adds the rows and keeps a compensated FP32 sum across
-// tiles.
-__global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
+// tiles.  Each thread holds E list entries (a tile is E x 128 entries) and
+// adds their particle-side values before the reduce-scatter, so its cost is
+// shared by E entries.
+template <int E>
+__global__ void __launch_bounds__(kThreads, 6) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order)
 {
     constexpr int kWarps = kThreads / 32;
@@ -685,18 +689,25 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
             // particle-side sums across tiles, compensated FP32 (hi + lo)
             float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
             __syncthreads();
-            for (int t0 = 0; t0 < ne; t0 += kThreads) {
-                const int q = t0 + threadIdx.x;
-                const bool valid = q < ne;
-                int32_t e = 0;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (valid) {
-                    e = T.ent[G.e0 + q];
-                    r = T.rec[G.e0 + q];
+            for (int t0 = 0; t0 < ne; t0 += E * kThreads) {
+                int32_t e[E];
+                f2 XJ[E], YJ[E], ZJ[E];
+                float MJ[E];
+                f2 vx[E], vy[E], vz[E];
+#pragma unroll
+                for (int u = 0; u < E; u++) {
+                    const int q = t0 + u * kThreads + threadIdx.x;
+                    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                    e[u] = 0;
+                    if (q < ne) {
+                        e[u] = T.ent[G.e0 + q];
+                        r = T.rec[G.e0 + q];
+                    }
+                    XJ[u] = f2pack(r.x, r.x); YJ[u] = f2pack(r.y, r.y); ZJ[u] = f2pack(r.z, r.z);
+                    MJ[u] = r.w;                               // 0 for an empty slot
+                    vx[u] = vy[u] = vz[u] = f2pack(0.f, 0.f);
                 }
-                const f2 XJ = f2pack(r.x, r.x), YJ = f2pack(r.y, r.y), ZJ = f2pack(r.z, r.z);
                 const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
-                f2 vx = f2pack(0.f, 0.f), vy = vx, vz = vx;
                 for (int pp = 0; pp < npe; pp += 2) {
                     float v[16];
 #pragma unroll
@@ -704,52 +715,64 @@ __global__ void __launch_bounds__(kThreads) k_vjp_fused(TreeDev T, const float *
                         const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&IA[pp + P]);
                         const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&IB[pp + P]);
                         const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(&IC[pp + P]);
-                        const f2 dx = f2sub(XJ, a.x), dy = f2sub(YJ, a.y), dz = f2sub(ZJ, b.x);
                         const f2 WX = b.y, WY = c.x, WZ = c.y;
-                        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-                        float r2a, r2b, s2a, s2b;
-                        f2unpack(r2, r2a, r2b);
-                        f2unpack(f2add(r2, E2), s2a, s2b);
-                        const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-                        const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
-                        f2 gv, gp;
-                        g_gpx_packed(x, gv, gp);
-                        const f2 ri2 = f2mul(ri, ri);
-                        // m_j / s'^3, zero for the particle itself (and coincident pairs)
-                        const f2 mr3 = f2mul(f2pack(r2a > 0.f ? r.w : 0.f, r2b > 0.f ? r.w : 0.f), f2mul(ri2, ri));
-                        const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
-                        const f2 alpha = f2mul(gv, mr3);                       // m phi
-                        const f2 beta = f2mul(f2mul(f2fma(gv, f2mul(M3, ri2), gp), mr3), dw);   // m psi (d.w)
-                        vx = f2fma(beta, dx, f2fma(alpha, WX, vx));
-                        vy = f2fma(beta, dy, f2fma(alpha, WY, vy));
-                        vz = f2fma(beta, dz, f2fma(alpha, WZ, vz));
-                        f2unpack(alpha, v[8 * P + 0], v[8 * P + 1]);
-                        f2unpack(f2mul(beta, dx), v[8 * P + 2], v[8 * P + 3]);
-                        f2unpack(f2mul(beta, dy), v[8 * P + 4], v[8 * P + 5]);
-                        f2unpack(f2mul(beta, dz), v[8 * P + 6], v[8 * P + 7]);
+                        f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa;
+#pragma unroll
+                        for (int u = 0; u < E; u++) {
+                            const f2 dx = f2sub(XJ[u], a.x), dy = f2sub(YJ[u], a.y), dz = f2sub(ZJ[u], b.x);
+                            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+                            float r2a, r2b, s2a, s2b;
+                            f2unpack(r2, r2a, r2b);
+                            f2unpack(f2add(r2, E2), s2a, s2b);
+                            const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+                            const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+                            f2 gv, gp;
+                            g_gpx_packed(x, gv, gp);
+                            const f2 ri2 = f2mul(ri, ri);
+                            // m_j / s'^3, zero for the particle itself (and coincident pairs)
+                            const f2 mr3 = f2mul(f2pack(r2a > 0.f ? MJ[u] : 0.f, r2b > 0.f ? MJ[u] : 0.f),
+                                                 f2mul(ri2, ri));
+                            const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
+                            const f2 alpha = f2mul(gv, mr3);                       // m phi
+                            const f2 beta = f2mul(f2mul(f2fma(gv, f2mul(M3, ri2), gp), mr3), dw);   // m psi (d.w)
+                            vx[u] = f2fma(beta, dx, f2fma(alpha, WX, vx[u]));
+                            vy[u] = f2fma(beta, dy, f2fma(alpha, WY, vy[u]));
+                            vz[u] = f2fma(beta, dz, f2fma(alpha, WZ, vz[u]));
+                            sa = f2add(sa, alpha);
+                            sbx = f2fma(beta, dx, sbx);
+                            sby = f2fma(beta, dy, sby);
+                            sbz = f2fma(beta, dz, sbz);
+                        }
+                        f2unpack(sa, v[8 * P + 0], v[8 * P + 1]);
+                        f2unpack(sbx, v[8 * P + 2], v[8 * P + 3]);
+                        f2unpack(sby, v[8 * P + 4], v[8 * P + 5]);
+                        f2unpack(sbz, v[8 * P + 6], v[8 * P + 7]);
                     }
-                    // reduce-scatter over the warp's 32 entries: each halving step
+                    // reduce-scatter over the warp's 32 lanes: each halving step
                     // keeps the half of the values selected by one lane bit
 #pragma unroll
                     for (int lvl = 0; lvl < 4; lvl++) {
                         const int off = 16 >> lvl, half = 8 >> lvl;
                         const bool upper = (lane & off) != 0;
 #pragma unroll
-                        for (int k = 0; k < half; k++) {
-                            const float send = upper ? v[k] : v[k + half];
-                            const float keep = upper ? v[k + half] : v[k];
-                            v[k] = keep + __shfl_xor_sync(kFull, send, off);
+                        for (int kk = 0; kk < half; kk++) {
+                            const float send = upper ? v[kk] : v[kk + half];
+                            const float keep = upper ? v[kk + half] : v[kk];
+                            v[kk] = keep + __shfl_xor_sync(kFull, send, off);
                         }
                     }
                     v[0] += __shfl_xor_sync(kFull, v[0], 1);
                     if ((lane & 1) == 0) part[warp][vq][2 * (pp + vP) + vh] = v[0];
                 }
-                if (valid) {
-                    float l, h;
-                    double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
-                    f2unpack(vx, l, h); atomicAdd(dst, gk3 * (double)(l + h));
-                    f2unpack(vy, l, h); atomicAdd(dst + 1, gk3 * (double)(l + h));
-                    f2unpack(vz, l, h); atomicAdd(dst + 2, gk3 * (double)(l + h));
+#pragma unroll
+                for (int u = 0; u < E; u++) {
+                    if (t0 + u * kThreads + (int)threadIdx.x < ne) {
+                        float l, h;
+                        double *dst = e[u] >= 0 ? gs + 3 * (int64_t)e[u] : ncot + 3 * (int64_t)(-e[u] - 1);
+                        f2unpack(vx[u], l, h); atomicAdd(dst, gk3 * (double)(l + h));
+                        f2unpack(vy[u], l, h); atomicAdd(dst + 1, gk3 * (double)(l + h));
+                        f2unpack(vz[u], l, h); atomicAdd(dst + 2, gk3 * (double)(l + h));
+                    }
                 }
                 __syncthreads();
                 if (threadIdx.x < nic) {
@@ -892,7 +915,8 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
     static int nb = 0, nbf = 0;
     if (nb == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, k_vjp_fused, kThreads, 0);
+        auto kfq = k_vjp_fused<kVjpEntries>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, kfq, kThreads, 0);
         nb = nb > 0 ? nb : 1; nbf = nbf > 0 ? nbf : 1;
     }
     auto grid_of = [&](int per_sm) {
@@ -902,8 +926,8 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
     if (sizeof(R) == 4) {
         cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
         if (ev0) cudaEventRecord(ev0, s);
-        TP_LAUNCH(k_vjp_fused, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1,
-                  order);
+        auto kf = k_vjp_fused<kVjpEntries>;
+        TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order);
         if (ev1) cudaEventRecord(ev1, s);
     } else {
         cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
