@@ -19,7 +19,8 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kTile = 256;
-constexpr int kVjpEntries = 2;   // list entries per thread in the fused adjoint
+constexpr int kVjpEntries = 4;     // list entries per thread in the fused adjoint
+constexpr int kPairParticles = 2;  // particles per thread in the forward pair kernel
 
 __device__ __forceinline__ float sqrt_approx(float x)
 {
@@ -206,48 +207,62 @@ __device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPar
 // factored form, on [0,1] the second adds Eq. 3's difference between its two
 // branches, (1 - xi)^6 c(xi).  Both terms are non-negative (no cancellation in
 // FP32) and u = 0 makes g vanish exactly at and beyond the cutoff.
+// Two pairs per step, packed, for NI particles per thread: each staged entry
+// pair (A = {x0, x1, y0, y1}, B = {z0, z1, m0, m1}) is loaded once and used
+// for all NI particles.  Eq. 3 as g = u^5 h + v^6 c (exact 0 beyond the cutoff).
+template <int NI>
 __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4 *SB, int st, int npairs, int ns,
-                                                  float xi, float yi, float zi, float eps2, float &axs,
-                                                  float &ays, float &azs)
+                                                  const float *xi, const float *yi, const float *zi, float eps2,
+                                                  float *axs, float *ays, float *azs)
 {
-    const f2 X = f2pack(xi, xi), Y = f2pack(yi, yi), Z = f2pack(zi, zi);
+    f2 X[NI], Y[NI], Z[NI], ax[NI], ay[NI], az[NI];
+#pragma unroll
+    for (int k = 0; k < NI; k++) {
+        X[k] = f2pack(xi[k], xi[k]); Y[k] = f2pack(yi[k], yi[k]); Z[k] = f2pack(zi[k], zi[k]);
+        ax[k] = ay[k] = az[k] = f2pack(0.f, 0.f);
+    }
     const f2 E2 = f2pack(eps2, eps2), TWO = f2pack(2.f, 2.f), ONE = f2pack(1.f, 1.f);
     const f2 H3 = f2pack(7.f / 140.f, 7.f / 140.f), H2 = f2pack(22.f / 140.f, 22.f / 140.f);
     const f2 H1 = f2pack(10.f / 140.f, 10.f / 140.f), H0 = f2pack(4.f / 140.f, 4.f / 140.f);
     const f2 C2 = f2pack(7.f / 35.f, 7.f / 35.f), C1 = f2pack(18.f / 35.f, 18.f / 35.f);
     const f2 C0 = f2pack(3.f / 35.f, 3.f / 35.f);
-    f2 ax = f2pack(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll 2
     for (int p = st; p < npairs; p += ns) {
         const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&SA[p]);
         const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&SB[p]);
-        const f2 dx = f2sub(a.x, X), dy = f2sub(a.y, Y), dz = f2sub(b.x, Z);
-        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-        float r2a, r2b, s2a, s2b;
-        f2unpack(r2, r2a, r2b);
-        f2unpack(f2add(r2, E2), s2a, s2b);
-        const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-        const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
-        const f2 u = f2relu(f2sub(TWO, x));
-        const f2 v = f2relu(f2sub(ONE, x));
-        f2 h = f2fma(H3, x, H2);
-        h = f2fma(h, x, H1);
-        h = f2fma(h, x, H0);
-        f2 c = f2fma(C2, x, C1);
-        c = f2fma(c, x, C0);
-        const f2 u2 = f2mul(u, u), v2 = f2mul(v, v);
-        const f2 u5 = f2mul(f2mul(u2, u2), u), v6 = f2mul(f2mul(v2, v2), v2);
-        const f2 g = f2fma(v6, c, f2mul(u5, h));
-        const f2 ri3 = f2mul(f2mul(ri, ri), ri);
-        const f2 f = f2mul(f2mul(b.y, g), ri3);
-        ax = f2fma(f, dx, ax);
-        ay = f2fma(f, dy, ay);
-        az = f2fma(f, dz, az);
+#pragma unroll
+        for (int k = 0; k < NI; k++) {
+            const f2 dx = f2sub(a.x, X[k]), dy = f2sub(a.y, Y[k]), dz = f2sub(b.x, Z[k]);
+            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+            float r2a, r2b, s2a, s2b;
+            f2unpack(r2, r2a, r2b);
+            f2unpack(f2add(r2, E2), s2a, s2b);
+            const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+            const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+            const f2 u = f2relu(f2sub(TWO, x));
+            const f2 v = f2relu(f2sub(ONE, x));
+            f2 h = f2fma(H3, x, H2);
+            h = f2fma(h, x, H1);
+            h = f2fma(h, x, H0);
+            f2 c = f2fma(C2, x, C1);
+            c = f2fma(c, x, C0);
+            const f2 u2 = f2mul(u, u), v2 = f2mul(v, v);
+            const f2 u5 = f2mul(f2mul(u2, u2), u), v6 = f2mul(f2mul(v2, v2), v2);
+            const f2 g = f2fma(v6, c, f2mul(u5, h));
+            const f2 ri3 = f2mul(f2mul(ri, ri), ri);
+            const f2 f = f2mul(f2mul(b.y, g), ri3);
+            ax[k] = f2fma(f, dx, ax[k]);
+            ay[k] = f2fma(f, dy, ay[k]);
+            az[k] = f2fma(f, dz, az[k]);
+        }
     }
-    float l, h;
-    f2unpack(ax, l, h); axs += l + h;
-    f2unpack(ay, l, h); ays += l + h;
-    f2unpack(az, l, h); azs += l + h;
+#pragma unroll
+    for (int k = 0; k < NI; k++) {
+        float l, h;
+        f2unpack(ax[k], l, h); axs[k] += l + h;
+        f2unpack(ay[k], l, h); ays[k] += l + h;
+        f2unpack(az[k], l, h); azs[k] += l + h;
+    }
 }
 
 // g and g'/xi for two pairs at once, in the cancellation-free forms
@@ -408,11 +423,12 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 // t+1 (loaded one tile earlier into registers) into the other buffer and loads
 // its pair of tile t+2, so one barrier per tile suffices.  Each tile's FP32
 // partial enters an FP64 sum per particle.
+template <int NI>
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
     __shared__ float4 SA[2][kTile / 2], SB[2][kTile / 2];
-    __shared__ double red[3][kThreads];
+    __shared__ double red[3 * NI][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
@@ -424,17 +440,30 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
         const int ne = bad ? 0 : G.ne;
-        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
-            const int nic = min(kThreads, G.ni - i0);
-            const int ns = kThreads / nic;
+        for (int i0 = 0; i0 < G.ni; i0 += NI * kThreads) {
+            // particle k*nip + il of this chunk goes to the threads il, il + nip, ... (slices)
+            const int nic = min(NI * kThreads, G.ni - i0);
+            const int nip = (nic + NI - 1) / NI;
+            const int ns = kThreads / nip;
             const int slot = threadIdx.x;
-            const bool active = slot < nic * ns;
-            const int il = active ? slot % nic : 0, st = active ? slot / nic : 0;
-            const int32_t p = G.first + i0 + il;
-            const float xi = Arith<float>::from_fixed(T.X[p], G.X, sc);
-            const float yi = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
-            const float zi = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
-            double sax = 0.0, say = 0.0, saz = 0.0;
+            const bool active = slot < nip * ns;
+            const int il = active ? slot % nip : 0, st = active ? slot / nip : 0;
+            float xi[NI], yi[NI], zi[NI];
+#pragma unroll
+            for (int k = 0; k < NI; k++) {
+                const int i = k * nip + il;
+                if (i < nic) {
+                    const int32_t p = G.first + i0 + i;
+                    xi[k] = Arith<float>::from_fixed(T.X[p], G.X, sc);
+                    yi[k] = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
+                    zi[k] = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
+                } else {                                   // a pad particle far from everything
+                    xi[k] = yi[k] = zi[k] = -1.0e4f;
+                }
+            }
+            double sax[NI], say[NI], saz[NI];
+#pragma unroll
+            for (int k = 0; k < NI; k++) sax[k] = say[k] = saz[k] = 0.0;
             float4 n0 = pad, n1 = pad;
             auto fetch = [&](int t1) {
                 const int nt1 = min(kTile, ne - t1), q = 2 * (int)threadIdx.x;
@@ -452,9 +481,12 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
             for (int t0 = 0, b = 0; t0 < ne; t0 += kTile, b ^= 1) {
                 const int nt = min(kTile, ne - t0);
                 if (active) {
-                    float ax = 0.f, ay = 0.f, az = 0.f;
-                    force_tile_packed(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
-                    sax += ax; say += ay; saz += az;
+                    float ax[NI], ay[NI], az[NI];
+#pragma unroll
+                    for (int k = 0; k < NI; k++) ax[k] = ay[k] = az[k] = 0.f;
+                    force_tile_packed<NI>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+#pragma unroll
+                    for (int k = 0; k < NI; k++) { sax[k] += ax[k]; say[k] += ay[k]; saz[k] += az[k]; }
                 }
                 if (t0 + kTile < ne) {
                     SA[b ^ 1][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
@@ -463,16 +495,20 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
                 }
                 __syncthreads();
             }
-            red[0][slot] = sax; red[1][slot] = say; red[2][slot] = saz;
+#pragma unroll
+            for (int k = 0; k < NI; k++) {
+                red[3 * k][slot] = sax[k]; red[3 * k + 1][slot] = say[k]; red[3 * k + 2][slot] = saz[k];
+            }
             __syncthreads();
-            if (slot < nic) {
+            for (int i = slot; i < nic; i += kThreads) {
+                const int k = i / nip, l = i % nip;
                 double sxx = 0, syy = 0, szz = 0;
                 for (int s2 = 0; s2 < ns; s2++) {
-                    sxx += red[0][s2 * nic + slot];
-                    syy += red[1][s2 * nic + slot];
-                    szz += red[2][s2 * nic + slot];
+                    sxx += red[3 * k][s2 * nip + l];
+                    syy += red[3 * k + 1][s2 * nip + l];
+                    szz += red[3 * k + 2][s2 * nip + l];
                 }
-                const int64_t o = T.perm[G.first + i0 + slot];
+                const int64_t o = T.perm[G.first + i0 + i];
                 acc[3 * o] = (float)(sxx * G.P->gk2);
                 acc[3 * o + 1] = (float)(syy * G.P->gk2);
                 acc[3 * o + 2] = (float)(szz * G.P->gk2);
@@ -644,7 +680,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // adds their particle-side values before the reduce-scatter, so its cost is
 // shared by E entries.
 template <int E>
-__global__ void __launch_bounds__(kThreads, 6) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
+__global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order)
 {
     constexpr int kWarps = kThreads / 32;
@@ -719,6 +755,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_vjp_fused(TreeDev T, const floa
                         f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa;
 #pragma unroll
                         for (int u = 0; u < E; u++) {
+                            if (u > 0 && t0 + u * kThreads + warp * 32 >= ne) break;   // warp-uniform: no entries left
                             const f2 dx = f2sub(XJ[u], a.x), dy = f2sub(YJ[u], a.y), dz = f2sub(ZJ[u], b.x);
                             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
                             float r2a, r2b, s2a, s2b;
@@ -875,7 +912,8 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
     static int bps = 0, bpp = 0;          // occupancies, queried once outside any capture
     if (bps == 0) {
         bps = pair_blocks_per_sm<float>();
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, k_pair_packed, kThreads, 0);
+        auto kq = k_pair_packed<kPairParticles>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, kq, kThreads, 0);
         bpp = bpp > 0 ? bpp : 1;
     }
     auto grid_of = [&](int per_sm) {
@@ -883,7 +921,8 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
         return (int)(gr > G ? G : gr);
     };
     if (ev0) cudaEventRecord(ev0, s);
-    TP_LAUNCH(k_pair_packed, grid_of(bpp), kThreads, 0, s, T, acc, queue + 1, order);
+    auto kp = k_pair_packed<kPairParticles>;
+    TP_LAUNCH(kp, grid_of(bpp), kThreads, 0, s, T, acc, queue + 1, order);
     if (ev1) cudaEventRecord(ev1, s);
     auto k = k_pair<float, true>;
     TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
