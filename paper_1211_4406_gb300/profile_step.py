@@ -52,7 +52,7 @@ def record_traffic(csv_path: str, n: int) -> dict:
     for r in rows[hi + 1:]:
         if len(r) <= mi:
             continue
-        name = r[ki].split("(")[0].replace("<unnamed>::", "")
+        name = r[ki].split("(")[0].replace("<unnamed>::", "").replace("void ", "").split("<")[0].strip()
         if name not in TRAFFIC_KERNELS:
             continue
         d = per.setdefault((name, r[0]), {})
