@@ -81,10 +81,12 @@ typedef struct {
  * (tp_export_lists returns TP_ERR_INVALID_ARG), every force/vjp call re-walks
  * each window, and a force/vjp call after tp_rebuild_tree synchronises the
  * stream once to plan the windows (so it cannot be captured in a CUDA graph).
- * The build switches to chunked mode by itself when the lists would need more
- * than 2^30 entries; setting TP_FLAG_CHUNKED in any box's flags forces it (with
- * windows of about a quarter of the lists, which also exercises the mode on
- * small boxes).  Results are the same as with whole lists.                  */
+ * The build switches to chunked mode by itself when whole lists (24 bytes per
+ * padded slot of the walk) would take more than half of the device memory
+ * that is free at build time; setting TP_FLAG_CHUNKED in any box's flags
+ * forces it (with windows of about a quarter of the lists, which also
+ * exercises the mode on small boxes).  Results are the same as with whole
+ * lists.  tp_tree_stats reports n_windows > 1 for a chunked tree.           */
 #define TP_FLAG_CHUNKED 1
 
 typedef struct tp_tree tp_tree; /* opaque, library-owned */

@@ -234,6 +234,9 @@ class CapturedStep:
 
     def __init__(self, tree: ShortRangeTree, pos: torch.Tensor, mass, cot: torch.Tensor,
                  acc: torch.Tensor, grad: torch.Tensor, with_vjp: bool = True):
+        if tree.stats()["n_windows"] > 1:
+            raise ValueError("a tree in chunked mode (bounded list memory) plans its windows with a host "
+                             "synchronisation and cannot be captured in a CUDA graph")
         self.tree, self.pos, self.mass, self.cot, self.acc, self.grad = tree, pos, mass, cot, acc, grad
         self.with_vjp = with_vjp
         side = torch.cuda.Stream()

@@ -302,8 +302,8 @@ __global__ void k_check_entries(TreeDev T)
 // the tree whose group arrays start at the window's first group and whose
 // group count is the window's size, so every walk and pair kernel runs on it
 // unchanged, with its items, padded slots and lists reusing the same buffers.
-constexpr int64_t kChunkSlots = 1ll << 30;   // whole lists above this many padded slots: chunked
 constexpr int64_t kWindowSlots = 1ll << 29;  // padded-slot budget of one window
+constexpr double kSlotBytes = 4.0 + 4.0 + 16.0;   // per padded slot: slot, entry id, entry record
 constexpr int kMaxWindows = 1 << 16;
 
 static TreeDev window_view(const TreeDev &D, int64_t g0, int64_t ng, int64_t *d_ng)
@@ -485,7 +485,13 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
             total += gp[g];
             largest = gp[g] > largest ? gp[g] : largest;
         }
-        t->chunked = t->force_chunked || total > kChunkSlots;
+        // whole lists when their buffers take at most half of the free device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 0;
+        }
+        t->chunked = t->force_chunked || kSlotBytes * (double)total > 0.5 * (double)free_b;
         if (t->chunked) {
             int64_t budget = t->force_chunked ? total / 4 + 1 : kWindowSlots;
             return build_chunked(t, s, budget > largest ? budget : largest);
