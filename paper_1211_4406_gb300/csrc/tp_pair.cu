@@ -837,29 +837,43 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
     }
 }
 
-// Node cotangents reach member particles through the centre of mass: for each
-// leaf, P = sum over the path root..leaf of c_a / M_a (summed from the root
-// down); grad_p += m_p P.  Then key order -> input order.
-__global__ void k_pushdown(TreeDev T, double *gs, const double *ncot)
+// Node cotangents reach member particles through the centre of mass:
+// P_a = P_parent(a) + c_a / M_a, taken level by level from the roots down (in
+// place of c_a), so each node's sum runs root..node in that order; then
+// grad_p += m_p P_leaf(p).  Then key order -> input order.
+__global__ void k_pushdown_level(TreeDev T, double *ncot, int L)
 {
-    const int64_t nn = *T.n_nodes;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)t;
-        if (T.nchild[i] != 0 || T.count[i] == 0) continue;
-        int32_t path[TP_NLEVELS + 1];
-        int d = 0;
-        for (int32_t a = i; a >= 0 && d <= TP_NLEVELS; a = T.parent[a]) path[d++] = a;
-        double Px = 0.0, Py = 0.0, Pz = 0.0;
-        for (int k = d - 1; k >= 0; k--) {
-            const int32_t a = path[k];
-            const double M = T.M[a];
-            if (M > 0.0) {
-                Px += ncot[3 * (int64_t)a] / M;
-                Py += ncot[3 * (int64_t)a + 1] / M;
-                Pz += ncot[3 * (int64_t)a + 2] / M;
-            }
+    const int64_t s0 = T.lstart[L], nl = T.lcount[L];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = s0 + k;
+        if (a >= T.cap_nodes) break;
+        double px = 0.0, py = 0.0, pz = 0.0;
+        const int32_t par = T.parent[a];
+        if (par >= 0) {
+            px = ncot[3 * (int64_t)par];
+            py = ncot[3 * (int64_t)par + 1];
+            pz = ncot[3 * (int64_t)par + 2];
         }
+        const double M = T.M[a];
+        if (M > 0.0) {
+            px += ncot[3 * a] / M;
+            py += ncot[3 * a + 1] / M;
+            pz += ncot[3 * a + 2] / M;
+        }
+        ncot[3 * a] = px;
+        ncot[3 * a + 1] = py;
+        ncot[3 * a + 2] = pz;
+    }
+}
+
+__global__ void k_pushdown_leaves(TreeDev T, double *gs, const double *P)
+{
+    const int64_t nn = *T.n_nodes < T.cap_nodes ? *T.n_nodes : T.cap_nodes;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (T.nchild[i] != 0 || T.count[i] == 0) continue;
+        const double Px = P[3 * i], Py = P[3 * i + 1], Pz = P[3 * i + 2];
         for (int32_t p = T.first[i]; p < T.first[i] + T.count[i]; p++) {
             const double mp = T.m[p];
             gs[3 * (int64_t)p] += mp * Px;
@@ -977,7 +991,8 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
 
 void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s)
 {
-    TP_LAUNCH(k_pushdown, 152 * 4, 256, 0, s, T, gs, ncot);
+    for (int L = 0; L < TP_NLEVELS; L++) TP_LAUNCH(k_pushdown_level, 152 * 2, 256, 0, s, T, ncot, L);
+    TP_LAUNCH(k_pushdown_leaves, 152 * 4, 256, 0, s, T, gs, ncot);
     TP_LAUNCH(k_unsort3, grid_for(T.n, 256), 256, 0, s, T, gs, grad);
 }
 
