@@ -36,7 +36,6 @@ void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *nco
              const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
              const int32_t *order, int64_t G, cudaStream_t s);
-int num_sms();
 }  // namespace tp
 
 static std::atomic<long long> g_launches{0};

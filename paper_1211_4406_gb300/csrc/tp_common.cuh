@@ -129,6 +129,18 @@ extern "C" void tp_count_launch(void);
 
 // Launch helpers implemented in the .cu files.
 namespace tp {
+int num_sms();   // SMs of the current device, queried once per process
+// Resident blocks per SM of `kernel` at `block` threads (at least 1).
+template <class K>
+int occupancy(K kernel, int block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
+}
 int grid_for(int64_t n, int block);
 // Exclusive scans (device-wide).  Exactly one of n_host / d_n gives the
 // length: d_n != nullptr reads it from the device (graph friendly).

@@ -897,24 +897,23 @@ __global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
 template <class R>
 int pair_blocks_per_sm()
 {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair<R, true>, kThreads, 0);
-    return nb > 0 ? nb : 1;
+    return tp::occupancy(k_pair<R, true>, kThreads);
 }
 
 }  // namespace
 
 namespace tp {
 
+// Queried once per process (thread-safe static initialisation), outside any
+// stream capture: the first call of each launcher is never captured.
 int num_sms()
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }();
     return sms;
 }
 
@@ -923,13 +922,8 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
 {
     if (G <= 0) return;
     cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
-    static int bps = 0, bpp = 0;          // occupancies, queried once outside any capture
-    if (bps == 0) {
-        bps = pair_blocks_per_sm<float>();
-        auto kq = k_pair_packed<kPairParticles>;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpp, kq, kThreads, 0);
-        bpp = bpp > 0 ? bpp : 1;
-    }
+    static const int bps = occupancy(k_pair<float, true>, kThreads);
+    static const int bpp = occupancy(k_pair_packed<kPairParticles>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
@@ -964,14 +958,8 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
                       int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     if (G <= 0) return;
-    // occupancies are queried once, outside any capture
-    static int nb = 0, nbf = 0;
-    if (nb == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vjp<R>, kThreads, 0);
-        auto kfq = k_vjp_fused<kVjpEntries>;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbf, kfq, kThreads, 0);
-        nb = nb > 0 ? nb : 1; nbf = nbf > 0 ? nbf : 1;
-    }
+    static const int nb = occupancy(k_vjp<R>, kThreads);
+    static const int nbf = occupancy(k_vjp_fused<kVjpEntries>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);

@@ -452,16 +452,9 @@ void walk_items(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s)
 void walk_expand(TreeDev &T, unsigned long long *counter, void *scan_tmp, cudaStream_t s)
 {
     if (T.cap_items <= 0) return;
-    static int bps = 0;                    // occupancy, queried once outside any capture
-    if (bps == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_walk_task, kBlock, 0);
-        bps = bps > 0 ? bps : 1;
-    }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static const int bps = occupancy(k_walk_task, kBlock);   // once per process, never inside a capture
     cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    TP_LAUNCH(k_walk_task, (sms > 0 ? sms : 1) * bps, kBlock, 0, s, T, counter);
+    TP_LAUNCH(k_walk_task, num_sms() * bps, kBlock, 0, s, T, counter);
     scan_i32_to_i64(T.icnt2, T.ipos, 0, T.n_items, T.n_entries, scan_tmp, s);
     TP_LAUNCH(k_list_offsets, grid_for(T.cap_groups, 256), 256, 0, s, T);
 }

@@ -63,3 +63,26 @@ def test_chunked_batched_boxes():
     assert torch.equal(whole.force(), chunk.force())
     whole.close()
     chunk.close()
+
+
+@pytest.mark.parametrize("precision,eps0", [("fp64", False), ("fp32", True)])
+def test_chunked_general_kernels(precision, eps0):
+    """Tiny boxes (groups spanning half the box: the integer-offset general
+    kernels) and eps = 0 (the scalar FP32 kernel) through the chunked path."""
+    boxes = [inputs.config_box(1, n_override=n) for n in (512, 729, 1000, 4096)]
+    pos = torch.tensor(np.concatenate([b.pos for b in boxes]), device="cuda")
+    mass = torch.tensor(np.concatenate([b.mass for b in boxes]), device="cuda")
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).tolist()
+
+    def prm(chunked):
+        return [Params(b.G, 0.0 if eps0 else b.eps, b.r_cut, b.theta, 32, 8, precision, chunked=chunked)
+                for b in boxes]
+    whole = ShortRangeTree(pos, mass, prm(False), box_offsets=offs)
+    chunk = ShortRangeTree(pos, mass, prm(True), box_offsets=offs)
+    assert chunk.stats()["n_windows"] > 1
+    assert torch.equal(whole.force(), chunk.force())
+    cot = torch.tensor(np.concatenate([inputs.cotangent(b.n, b.seed + 7) for b in boxes]), device="cuda")
+    gw, gc = whole.vjp(cot).cpu().numpy(), chunk.vjp(cot).cpu().numpy()
+    assert np.abs(gw - gc).max() <= 1e-12 * np.sqrt(np.mean(gw ** 2))
+    whole.close()
+    chunk.close()
