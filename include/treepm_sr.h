@@ -143,6 +143,19 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream);
  * differentiated.  Asynchronous.                                            */
 tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *stream);
 
+/* The force of tp_short_range_force and the vector-Jacobian product of
+ * tp_short_range_vjp in one pass over the lists (no counterpart in the paper).
+ * For callers that know the cotangent before they need the forces: a loss
+ * linear in the accelerations, or the backward pass of a leapfrog step, where
+ * a step's force is recomputed next to its VJP.  The FP32 path's adjoint
+ * kernel already evaluates m_j g / s^3 for every pair and adds the Eq. 2 sum
+ * per particle alongside; an FP64 tree runs the two calls in turn.  acc:
+ * device [n][3] (float for TP_FP32, double for TP_FP64), cot: device [n][3]
+ * of the same type, grad: device double [n][3]; all input order,
+ * overwritten.  Results agree with the separate calls within rounding (the
+ * particle-side sums are taken in a different order).  Asynchronous.        */
+tp_status tp_short_range_force_vjp(tp_tree *t, void *acc, const void *cot, double *grad, void *stream);
+
 /* Synchronise the tree's last stream and return its first latched error.   */
 tp_status tp_tree_status(tp_tree *t);
 
@@ -169,10 +182,10 @@ tp_status tp_tree_free(tp_tree *t);
 /* Kernel timing, a measurement aid with no counterpart in the paper.  With
  * enable != 0 the tree records CUDA events on the call's stream immediately
  * before and after its main FP32 pair-kernel launch in tp_short_range_force
- * and its main FP32 adjoint-kernel launch in tp_short_range_vjp (the kernels
- * that handle the groups not spanning half the box, with eps > 0).  Creates
- * the events on first use (TP_ERR_CUDA if that fails).  enable = 0 stops the
- * recording.                                                                */
+ * and its main FP32 adjoint-kernel launch in tp_short_range_vjp and
+ * tp_short_range_force_vjp (the kernels that handle the groups not spanning
+ * half the box, with eps > 0; not in chunked mode).  Creates the events on
+ * first use (TP_ERR_CUDA if that fails).  enable = 0 stops the recording.   */
 tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable);
 /* Durations in ms of those two launches in the last force and vjp calls made
  * with timing on; -1 for a call that recorded nothing (timing off, FP64 tree,

@@ -52,6 +52,7 @@ SIGNATURES = {
     "tp_rebuild_tree": ([_V, _V, _V, _V], C.c_int),
     "tp_short_range_force": ([_V, _V, _V], C.c_int),
     "tp_short_range_vjp": ([_V, _V, _V, _V], C.c_int),
+    "tp_short_range_force_vjp": ([_V, _V, _V, _V, _V], C.c_int),
     "tp_tree_status": ([_V], C.c_int),
     "tp_tree_stats": ([_V, C.POINTER(TPStats)], C.c_int),
     "tp_export_keys": ([_V, _V, _V], C.c_int),

@@ -133,6 +133,23 @@ class ShortRangeTree:
         _lib.check(code, "tp_short_range_vjp")
         return out
 
+    def force_vjp(self, cot: torch.Tensor, acc: torch.Tensor | None = None, grad: torch.Tensor | None = None,
+                  stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """(forces, dL/dx) in one pass over the lists, for a cotangent known in advance."""
+        cot = cot.to(self.acc_dtype).contiguous()
+        dev = self._pos.device
+        if acc is None:
+            acc = torch.empty((self.n, 3), dtype=self.acc_dtype, device=dev)
+        if grad is None:
+            grad = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
+        if acc.dtype != self.acc_dtype or not acc.is_contiguous() or tuple(acc.shape) != (self.n, 3):
+            raise ValueError("acc must be a contiguous [n,3] tensor of the tree's precision")
+        code = _lib.load().tp_short_range_force_vjp(self.handle, C.c_void_p(acc.data_ptr()),
+                                                    C.c_void_p(cot.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                                    _stream(stream))
+        _lib.check(code, "tp_short_range_force_vjp")
+        return acc, grad
+
     def status(self) -> int:
         return int(_lib.load().tp_tree_status(self.handle))
 

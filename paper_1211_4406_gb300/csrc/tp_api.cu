@@ -26,6 +26,8 @@ void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
                    const int32_t *order, int64_t G, cudaStream_t s);
 void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s);
+void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, double *ncot, int32_t *queue,
+                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
@@ -701,6 +703,38 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
     }
     else
         tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
+    return cuda_status(cudaGetLastError());
+}
+
+tp_status tp_short_range_force_vjp(tp_tree *t, void *acc, const void *cot, double *grad, void *stream)
+{
+    if (!t) return TP_ERR_INVALID_ARG;
+    if (t->n > 0 && (!is_device_ptr(acc) || !is_device_ptr(cot) || !is_device_ptr(grad)))
+        return TP_ERR_INVALID_ARG;
+    if (t->precision != TP_FP32) {           // the plain FP64 path: the two calls in turn
+        tp_status e = tp_short_range_force(t, acc, stream);
+        return e == TP_OK ? tp_short_range_vjp(t, cot, grad, stream) : e;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last = s;
+    if (t->n == 0) return TP_OK;
+    cudaMemsetAsync(acc, 0, sizeof(float) * 3 * (size_t)t->n, s);
+    tp::vjp_begin(t->D, t->gs, t->ncot, s);
+    t->kf_rec = false;
+    if (t->chunked) {
+        t->kv_rec = false;
+        tp_status e = for_each_window(t, s, [&](TreeDev &V) {
+            tp::force_vjp_pairs_f32(V, (float *)acc, (const float *)cot, t->gs, t->ncot, t->queue, t->order,
+                                    V.cap_groups, s, nullptr, nullptr);
+        });
+        if (e != TP_OK) return e;
+    } else {
+        tp::force_vjp_pairs_f32(t->D, (float *)acc, (const float *)cot, t->gs, t->ncot, t->queue, t->order,
+                                t->D.cap_groups, s, t->ktiming ? t->kev[2] : nullptr,
+                                t->ktiming ? t->kev[3] : nullptr);
+        t->kv_rec = t->ktiming && t->D.cap_groups > 0;
+    }
+    tp::vjp_end(t->D, grad, t->gs, t->ncot, s);
     return cuda_status(cudaGetLastError());
 }
 

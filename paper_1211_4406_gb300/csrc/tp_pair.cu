@@ -679,20 +679,26 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // tiles.  Each thread holds E list entries (a tile is E x 128 entries) and
 // adds their particle-side values before the reduce-scatter, so its cost is
 // shared by E entries.
-template <int E>
+template <int E, bool FWD>
 __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
-                                                        int32_t *queue, const int32_t *order)
+                                                        int32_t *queue, const int32_t *order, float *acc)
 {
     constexpr int kWarps = kThreads / 32;
     constexpr unsigned kFull = 0xffffffffu;
+    // particle-side quantities: A = sum alpha, B = sum beta d (3), with FWD also
+    // F = sum alpha d (3), the forward sum of Eq. 2 (alpha = m g / s^3)
+    constexpr int NQ = FWD ? 7 : 4;
+    constexpr int NV = FWD ? 32 : 16;      // values of two particle pairs (padded)
     __shared__ float4 IA[kThreads / 2], IB[kThreads / 2], IC[kThreads / 2];
-    __shared__ float part[kWarps][4][kThreads];
+    __shared__ float part[kWarps][NQ][kThreads];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // after the reduce-scatter below, lane holds the sum of value (lane >> 1) & 15
-    const int vidx = (lane >> 1) & 15, vP = vidx >> 3, vq = (vidx >> 1) & 3, vh = vidx & 1;
+    // after the reduce-scatter below, lane holds the sum of value vidx:
+    // value 8P + 2q + h (16 values) or 16P + 2q + h (32 values, FWD)
+    const int vidx = FWD ? lane : (lane >> 1) & 15;
+    const int vP = FWD ? vidx >> 4 : vidx >> 3, vq = FWD ? (vidx >> 1) & 7 : (vidx >> 1) & 3, vh = vidx & 1;
     for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
          item = next_item<true>(queue, item, &s_item)) {
         const int64_t g = order ? order[item] : item;
@@ -723,7 +729,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                 }
             }
             // particle-side sums across tiles, compensated FP32 (hi + lo)
-            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+            float sh[NQ], sl[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; q++) sh[q] = sl[q] = 0.f;
             __syncthreads();
             for (int t0 = 0; t0 < ne; t0 += E * kThreads) {
                 int32_t e[E];
@@ -745,14 +753,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                 }
                 const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
                 for (int pp = 0; pp < npe; pp += 2) {
-                    float v[16];
+                    float v[NV];
 #pragma unroll
                     for (int P = 0; P < 2; P++) {
                         const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(&IA[pp + P]);
                         const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(&IB[pp + P]);
                         const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(&IC[pp + P]);
                         const f2 WX = b.y, WY = c.x, WZ = c.y;
-                        f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa;
+                        f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa, sfx = sa, sfy = sa, sfz = sa;
 #pragma unroll
                         for (int u = 0; u < E; u++) {
                             if (u > 0 && t0 + u * kThreads + warp * 32 >= ne) break;   // warp-uniform: no entries left
@@ -779,17 +787,31 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                             sbx = f2fma(beta, dx, sbx);
                             sby = f2fma(beta, dy, sby);
                             sbz = f2fma(beta, dz, sbz);
+                            if (FWD) {
+                                sfx = f2fma(alpha, dx, sfx);
+                                sfy = f2fma(alpha, dy, sfy);
+                                sfz = f2fma(alpha, dz, sfz);
+                            }
                         }
-                        f2unpack(sa, v[8 * P + 0], v[8 * P + 1]);
-                        f2unpack(sbx, v[8 * P + 2], v[8 * P + 3]);
-                        f2unpack(sby, v[8 * P + 4], v[8 * P + 5]);
-                        f2unpack(sbz, v[8 * P + 6], v[8 * P + 7]);
+                        constexpr int B0 = FWD ? 16 : 8;
+                        f2unpack(sa, v[B0 * P + 0], v[B0 * P + 1]);
+                        f2unpack(sbx, v[B0 * P + 2], v[B0 * P + 3]);
+                        f2unpack(sby, v[B0 * P + 4], v[B0 * P + 5]);
+                        f2unpack(sbz, v[B0 * P + 6], v[B0 * P + 7]);
+                        if (FWD) {
+                            f2unpack(sfx, v[B0 * P + 8], v[B0 * P + 9]);
+                            f2unpack(sfy, v[B0 * P + 10], v[B0 * P + 11]);
+                            f2unpack(sfz, v[B0 * P + 12], v[B0 * P + 13]);
+                            v[B0 * P + 14] = 0.f;
+                            v[B0 * P + 15] = 0.f;
+                        }
                     }
                     // reduce-scatter over the warp's 32 lanes: each halving step
                     // keeps the half of the values selected by one lane bit
+                    constexpr int kLevels = FWD ? 5 : 4;
 #pragma unroll
-                    for (int lvl = 0; lvl < 4; lvl++) {
-                        const int off = 16 >> lvl, half = 8 >> lvl;
+                    for (int lvl = 0; lvl < kLevels; lvl++) {
+                        const int off = 16 >> lvl, half = (NV / 2) >> lvl;
                         const bool upper = (lane & off) != 0;
 #pragma unroll
                         for (int kk = 0; kk < half; kk++) {
@@ -798,8 +820,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                             v[kk] = keep + __shfl_xor_sync(kFull, send, off);
                         }
                     }
-                    v[0] += __shfl_xor_sync(kFull, v[0], 1);
-                    if ((lane & 1) == 0) part[warp][vq][2 * (pp + vP) + vh] = v[0];
+                    if (FWD) {
+                        if (vq < NQ) part[warp][vq][2 * (pp + vP) + vh] = v[0];
+                    } else {
+                        v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                        if ((lane & 1) == 0) part[warp][vq][2 * (pp + vP) + vh] = v[0];
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < E; u++) {
@@ -815,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                 if (threadIdx.x < nic) {
                     const int nw = (min(kThreads, ne - t0) + 31) >> 5;   // warps that held entries
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
+                    for (int k = 0; k < NQ; k++) {
                         float t = 0.f;
                         for (int w = 0; w < nw; w++) t += part[w][k][threadIdx.x];
                         two_sum_add(sh[k], sl[k], t);
@@ -832,6 +858,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const floa
                           -gk3 * (sA * (double)cot[3 * o + 1] + ((double)sh[2] + (double)sl[2])));
                 atomicAdd(gs + 3 * (int64_t)p + 2,
                           -gk3 * (sA * (double)cot[3 * o + 2] + ((double)sh[3] + (double)sl[3])));
+                if (FWD) {
+                    const double gk2 = G.P->gk2;
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        acc[3 * o + c] = (float)(gk2 * ((double)sh[4 + c] + (double)sl[4 + c]));
+                }
             }
         }
     }
@@ -955,11 +987,12 @@ void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s)
 
 template <class R>
 static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
-                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc = nullptr)
 {
     if (G <= 0) return;
     static const int nb = occupancy(k_vjp<R>, kThreads);
-    static const int nbf = occupancy(k_vjp_fused<kVjpEntries>, kThreads);
+    static const int nbf = occupancy(k_vjp_fused<kVjpEntries, false>, kThreads);
+    static const int nbw = occupancy(k_vjp_fused<kVjpEntries, true>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
@@ -967,8 +1000,14 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
     if (sizeof(R) == 4) {
         cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
         if (ev0) cudaEventRecord(ev0, s);
-        auto kf = k_vjp_fused<kVjpEntries>;
-        TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order);
+        if (acc) {
+            auto kw = k_vjp_fused<kVjpEntries, true>;
+            TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order, acc);
+        } else {
+            auto kf = k_vjp_fused<kVjpEntries, false>;
+            TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order,
+                      nullptr);
+        }
         if (ev1) cudaEventRecord(ev1, s);
     } else {
         cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
@@ -988,6 +1027,21 @@ void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32
                    int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1);
+}
+
+// Forward and adjoint of the FP32 path in one pass over the lists: the fused
+// adjoint kernel also sums Eq. 2 for the groups it takes; the general forward
+// kernel covers the rest.  acc must be zeroed by the caller.
+void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, double *ncot, int32_t *queue,
+                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    if (G <= 0) return;
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc);
+    static const int bps = occupancy(k_pair<float, true>, kThreads);
+    const int64_t gr = (int64_t)num_sms() * bps;
+    cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    auto k = k_pair<float, true>;
+    TP_LAUNCH(k, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
 }
 
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,

@@ -1,0 +1,74 @@
+"""tp_short_range_force_vjp: the force and its vector-Jacobian product in one
+pass over the lists.  The forces meet the same bounds against the FP64 oracle
+on identical lists as tp_short_range_force (rms <= 1e-6, max <= 1e-4); the
+gradient equals tp_short_range_vjp's up to the order of the particle-side
+sums, and the oracle's analytic VJP within 1e-4 per coordinate."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1211_4406_gb300 import inputs
+from paper_1211_4406_gb300.api import Params, ShortRangeTree
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, ref):
+    nr = np.linalg.norm(ref, axis=1)
+    e = np.linalg.norm(a - ref, axis=1) / np.maximum(nr, 1e-6 * np.median(nr))
+    return float(np.sqrt(np.mean(e ** 2))), float(e.max())
+
+
+@pytest.mark.parametrize("k,n", [(2, 2 ** 15), (2, 2 ** 19), (1, None)])
+def test_force_vjp_matches_oracle_and_separate_calls(k, n):
+    box = inputs.config_box(k, n_override=n)
+    pos = torch.tensor(box.pos, device="cuda")
+    mass = torch.tensor(box.mass, device="cuda")
+    w = inputs.cotangent(box.n, box.seed + 7)
+    cot = torch.tensor(w, device="cuda")
+    t = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, 64, 8, "fp32"))
+    acc, grad = t.force_vjp(cot)
+    ot = oracle.OracleTree(box.pos, box.mass, 8, 64)
+    ot.lists(box.r_cut, box.theta)
+    rms, mx = rel_err(acc.double().cpu().numpy(), ot.list_forces(box.G, box.eps, box.r_cut))
+    assert rms <= 1e-6 and mx <= 1e-4, (rms, mx)
+    g = grad.cpu().numpy()
+    g_sep = t.vjp(cot).cpu().numpy()
+    gref = ot.list_vjp(box.G, box.eps, box.r_cut, w.astype(np.float64))
+    scale = np.sqrt(np.mean(gref ** 2))
+    assert np.abs(g - g_sep).max() <= 1e-6 * scale
+    assert np.all(np.abs(g - gref) <= 1e-4 * np.maximum(np.abs(gref), scale))
+    t.close()
+
+
+def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
+    boxes = [inputs.config_box(1, n_override=nn) for nn in (729, 4096)] + [inputs.config_box(2, n_override=2 ** 14)]
+    pos = torch.tensor(np.concatenate([b.pos for b in boxes]), device="cuda")
+    mass = torch.tensor(np.concatenate([b.mass for b in boxes]), device="cuda")
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])]).tolist()
+    w = np.concatenate([inputs.cotangent(b.n, b.seed + 7) for b in boxes])
+    for precision in ("fp32", "fp64"):
+        prm = [Params(b.G, b.eps, b.r_cut, b.theta, 32, 8, precision) for b in boxes]
+        t = ShortRangeTree(pos, mass, prm, box_offsets=offs)
+        cot = torch.tensor(w, device="cuda")
+        acc, grad = t.force_vjp(cot)
+        a_sep, g_sep = t.force().clone(), t.vjp(cot).cpu().numpy()
+        scale = np.sqrt(np.mean(g_sep ** 2))
+        if precision == "fp64":
+            assert torch.equal(acc, a_sep)
+            # the adjoint adds with FP64 atomics: equal up to their order
+            assert np.abs(grad.cpu().numpy() - g_sep).max() <= 1e-12 * scale
+        else:
+            rms, mx = rel_err(acc.double().cpu().numpy(), a_sep.double().cpu().numpy())
+            assert rms <= 1e-6 and mx <= 1e-4, (rms, mx)
+            assert np.abs(grad.cpu().numpy() - g_sep).max() <= 1e-6 * scale
+            # chunked: the same pass window by window
+            prm_c = [Params(b.G, b.eps, b.r_cut, b.theta, 32, 8, precision, chunked=True) for b in boxes]
+            tc = ShortRangeTree(pos, mass, prm_c, box_offsets=offs)
+            assert tc.stats()["n_windows"] > 1
+            acc_c, grad_c = tc.force_vjp(cot)
+            assert torch.equal(acc, acc_c)
+            assert np.abs(grad_c.cpu().numpy() - grad.cpu().numpy()).max() <= 1e-12 * scale
+            tc.close()
+        t.close()
