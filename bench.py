@@ -2,9 +2,11 @@
 
 One step = the whole hot path on one synthetic box: tree build (keys, sort,
 octree, monopoles, groups, interaction lists), the FP32 force (Eq. 2 on the
-lists) and its adjoint (VJP with a fixed cotangent).  The workload is the
-FP32-precision clustered box: N = 128^3 = 2,097,152 particles, 70 % in 2000
-NFW halos, r_cut = 3/128, eps = 1/6400, theta = 0.5, n_crit = 64.
+lists) and its adjoint (VJP with a fixed cotangent), the last two in one pass
+over the lists (tp_short_range_force_vjp; the same step with separate force
+and adjoint calls is timed beside it).  The workload is the FP32-precision
+clustered box: N = 128^3 = 2,097,152 particles, 70 % in 2000 NFW halos,
+r_cut = 3/128, eps = 1/6400, theta = 0.5, n_crit = 64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,6 +41,7 @@ UNIT = "interactions/s"
 # d.w, the 3-vector for the list entry and the sums for the particle).
 FLOPS_PER_INTERACTION = 42
 VJP_FLOPS_PER_INTERACTION = 76
+FUSED_FLOPS_PER_INTERACTION = 82   # the adjoint's 76 + the forward's a += alpha d (3 FMA)
 PAPER_FLOPS_PER_INTERACTION = 51 # the paper's convention (Sec. II-A)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -188,7 +191,6 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
-    import torch.distributed as dist
 
     from paper_1211_4406_gb300 import build as libbuild
     from paper_1211_4406_gb300 import inputs
@@ -216,18 +218,28 @@ def run_ours(args, rank, world, local_rank):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
+    # One step: rebuild the tree from the positions, then the forces and their
+    # adjoint for the step's cotangent (known in advance: the loss is linear in
+    # the accelerations) in one pass over the lists.
     def step(p, m, c, evs=None):
         if evs:
             evs[0].record(stream)
         tree.rebuild(p, m)
         if evs:
             evs[1].record(stream)
-        tree.force(acc)
+        tree.force_vjp(c, acc, grad)
         if evs:
             evs[2].record(stream)
-        tree.vjp(c, grad)
-        if evs:
-            evs[3].record(stream)
+
+    # The same step with the force and the adjoint as separate calls.
+    def step_separate(evs):
+        evs[0].record(stream)
+        tree.rebuild(pos, mass)
+        evs[1].record(stream)
+        tree.force(acc)
+        evs[2].record(stream)
+        tree.vjp(cot, grad)
+        evs[3].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -241,32 +253,41 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     tree.set_kernel_timing(True)
     launches0 = launch_count()
-    per, k_pair_ms, k_vjp_ms = [], [], []
+    per, k_fused_ms = [], []
     for _ in range(args.steps):
         flush.zero_()
-        evs = [ev() for _ in range(4)]
+        evs = [ev() for _ in range(3)]
         step(pos, mass, cot, evs)
         per.append(evs)
-        kf, kv = tree.kernel_ms()          # events around the two pair kernels (waits for them)
-        k_pair_ms.append(kf)
-        k_vjp_ms.append(kv)
+        k_fused_ms.append(tree.kernel_ms()[1])   # events around the one-pass kernel (waits for it)
     torch.cuda.synchronize()
     launches = launch_count() - launches0
-    tree.set_kernel_timing(False)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     t_build = [e[0].elapsed_time(e[1]) for e in per]
-    t_force = [e[1].elapsed_time(e[2]) for e in per]
-    t_vjp = [e[2].elapsed_time(e[3]) for e in per]
-    t_step = [e[0].elapsed_time(e[3]) for e in per]
-    ms_step = sum(t_step) / len(t_step)
+    t_fused = [e[1].elapsed_time(e[2]) for e in per]
+    t_step = [e[0].elapsed_time(e[2]) for e in per]
     if tree.status() != 0:
         raise RuntimeError("tree status after the timed region")
+
+    # ---- the separate calls, each kernel timed by its own events ---------------
+    sep, k_pair_ms, k_vjp_ms = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        evs = [ev() for _ in range(4)]
+        step_separate(evs)
+        sep.append(evs)
+        kf, kv = tree.kernel_ms()
+        k_pair_ms.append(kf)
+        k_vjp_ms.append(kv)
+    tree.set_kernel_timing(False)
+    torch.cuda.synchronize()
 
     # ---- end to end from host buffers ---------------------------------------
     acc_h = torch.empty((box.n, 3), dtype=torch.float32).pin_memory()
@@ -286,15 +307,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = ev(), ev()
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
+    e2e_ms = _timed_replays(e2e_step, args.steps, flush, stream)
     h2d = pos_h.numel() * 8 + mass_h.numel() * 8 + cot_h.numel() * 4
     d2h = acc_h.numel() * 4 + grad_h.numel() * 8
 
@@ -304,71 +317,61 @@ def run_ours(args, rank, world, local_rank):
     acc64 = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
     tree64.force(acc64)
     torch.cuda.synchronize()
-    f64_ms = []
-    for _ in range(2):
-        flush.zero_()
-        a, b = ev(), ev()
-        a.record(stream)
-        tree64.force(acc64)
-        b.record(stream)
-        b.synchronize()
-        f64_ms.append(a.elapsed_time(b))
+    f64_ms = _timed_replays(lambda: tree64.force(acc64), 2, flush, stream)
     tree64.close()
 
     # ---- max over ranks --------------------------------------------------------
     inter = int(st["n_interactions"])
     per_step_inter = 2 * inter
-    tot_ms = sum(t_step)
-    tot_e2e = sum(e2e_ms)
-    tot_ms, tot_e2e = max_over_ranks([tot_ms, tot_e2e], device=dev)
+    tot_ms, tot_e2e = max_over_ranks([sum(t_step), sum(e2e_ms)], device=dev)
     value = whole_job_rate(world, per_step_inter, args.steps, tot_ms)
     e2e_value = whole_job_rate(world, per_step_inter, args.steps, tot_e2e)
 
     if rank != 0:
         tree.close()
         return
-    force_ms = sum(t_force) / len(t_force)
-    vjp_ms = sum(t_vjp) / len(t_vjp)
-    build_ms = sum(t_build) / len(t_build)
-    fp32_peak_nominal = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
-    kp_ms = sum(k_pair_ms) / len(k_pair_ms)
-    kv_ms = sum(k_vjp_ms) / len(k_vjp_ms)
+    mean = lambda xs: sum(xs) / len(xs)
+    sep_step = mean([e[0].elapsed_time(e[3]) for e in sep])
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    peak_basis = "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
     # every group of this workload takes the packed kernels (none spans half
     # the box and eps > 0), so each launch processes all interactions
-    ach_vjp = VJP_FLOPS_PER_INTERACTION * inter / (kv_ms * 1e-3)
-    ach_fwd = FLOPS_PER_INTERACTION * inter / (kp_ms * 1e-3)
+
+    def roofline(kernel, ms, flops, note):
+        ach = flops * inter / (ms * 1e-3)
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": traffic_for(kernel, box.n), "kernel": f"{kernel} ({note})",
+                "ms_per_launch": ms, "flops_per_interaction": flops, "peak_basis": peak_basis}
+
+    kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)
     meas_ffma = measure_peak("fp32")
     meas_ffma2 = measure_peak("fp32x2")
     meas_dfma = measure_peak("fp64")
-    peak_basis = "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(),
-        "roofline": {"bound": "alu", "achieved": ach_vjp / 1e12, "peak": fp32_peak_nominal / 1e12,
-                     "unit": "TFLOP/s", "frac": ach_vjp / fp32_peak_nominal,
-                     "traffic": traffic_for("k_vjp_fused", box.n),
-                     "kernel": "k_vjp_fused (FP32 adjoint pair kernel, the largest share of the step)",
-                     "ms_per_launch": kv_ms, "flops_per_interaction": VJP_FLOPS_PER_INTERACTION,
-                     "peak_basis": peak_basis},
-        "roofline_forward": {"bound": "alu", "achieved": ach_fwd / 1e12, "peak": fp32_peak_nominal / 1e12,
-                             "unit": "TFLOP/s", "frac": ach_fwd / fp32_peak_nominal,
-                             "traffic": traffic_for("k_pair_packed", box.n),
-                             "kernel": "k_pair_packed (FP32 forward pair kernel, Eq. 2 x Eq. 3)",
-                             "ms_per_launch": kp_ms, "flops_per_interaction": FLOPS_PER_INTERACTION,
-                             "peak_basis": peak_basis},
+        "roofline": roofline("k_vjp_fused<4, true>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
+                             "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
+        "roofline_forward": roofline("k_pair_packed<2>", kp_ms, FLOPS_PER_INTERACTION,
+                                     "FP32 forward pair kernel, separate call"),
+        "roofline_adjoint": roofline("k_vjp_fused<4, false>", kv_ms, VJP_FLOPS_PER_INTERACTION,
+                                     "FP32 adjoint pair kernel, separate call"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},
         "gpu_launches": launches,
         "clocks": clk,
-        "phases_ms": {"build": build_ms, "force_fp32": force_ms, "vjp_fp32": vjp_ms,
-                      "force_fp64": sum(f64_ms) / len(f64_ms)},
-        "forward_interactions_per_s": inter / (force_ms * 1e-3),
-        "adjoint_interactions_per_s": inter / (vjp_ms * 1e-3),
-        "fp64_forward_interactions_per_s": inter / (sum(f64_ms) / len(f64_ms) * 1e-3),
-        "fp32_over_fp64_forward_speedup": (sum(f64_ms) / len(f64_ms)) / force_ms,
-        "forward_paper_convention_frac": PAPER_FLOPS_PER_INTERACTION * inter / (kp_ms * 1e-3) / fp32_peak_nominal,
+        "phases_ms": {"build": mean(t_build), "force_and_vjp_one_pass": mean(t_fused),
+                      "force_fp32_separate": mean([e[1].elapsed_time(e[2]) for e in sep]),
+                      "vjp_fp32_separate": mean([e[2].elapsed_time(e[3]) for e in sep]),
+                      "force_fp64": mean(f64_ms)},
+        "separate_calls": {"ms_per_step": sep_step, "value": per_step_inter / (sep_step * 1e-3)},
+        "forward_interactions_per_s": inter / (kp_ms * 1e-3),
+        "adjoint_interactions_per_s": inter / (kv_ms * 1e-3),
+        "fp64_forward_interactions_per_s": inter / (mean(f64_ms) * 1e-3),
+        "fp32_over_fp64_forward_speedup": mean(f64_ms) / kp_ms,
+        "forward_paper_convention_frac": PAPER_FLOPS_PER_INTERACTION * inter / (kp_ms * 1e-3) / fp32_peak,
         "measured_peaks_tflops": {"ffma": meas_ffma / 1e12, "ffma2": meas_ffma2 / 1e12,
                                   "dfma": meas_dfma / 1e12},
         "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions",

@@ -1,12 +1,13 @@
 """Run the hot path once or a few times on a synthetic clustered box, for
 profilers (ncu launch lists and single-kernel captures).
 
-  python -m paper_1211_4406_gb300.profile_step [--n N] [--steps K] [--what step|force|vjp]
+  python -m paper_1211_4406_gb300.profile_step [--n N] [--steps K] [--what step|force|vjp|fused|all]
 
 --n 2097152 is the benchmark workload (128^3 particles, 2000 NFW halos,
 r_cut = 3/128); smaller n keeps the recipe (halo count, r_cut and eps scale
 with n).  The allocating build runs first; each step is rebuild + force +
-adjoint (or only the force / only the adjoint).
+adjoint (step), only the force or only the adjoint, rebuild + the one-pass
+force and adjoint (fused), or rebuild + all three (all).
 
   python -m paper_1211_4406_gb300.profile_step --record-traffic CSV --n N
 
@@ -31,6 +32,12 @@ TRAFFIC_JSON = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 TRAFFIC_KERNELS = ("k_pair_packed", "k_vjp_fused")
 
 
+def kernel_key(name: str) -> str:
+    """A kernel's name with template arguments in one spelling (ncu prints
+    bool arguments as 0/1)."""
+    return name.replace(" ", "").replace("true", "1").replace("false", "0")
+
+
 def kernel_source_digest() -> str:
     """SHA-256 of the pair kernels' device code: the shared header and the
     part of tp_pair.cu before its host launch functions."""
@@ -52,8 +59,8 @@ def record_traffic(csv_path: str, n: int) -> dict:
     for r in rows[hi + 1:]:
         if len(r) <= mi:
             continue
-        name = r[ki].split("(")[0].replace("<unnamed>::", "").replace("void ", "").split("<")[0].strip()
-        if name not in TRAFFIC_KERNELS:
+        name = kernel_key(r[ki].split("(")[0].replace("<unnamed>::", "").replace("void ", ""))
+        if name.split("<")[0] not in TRAFFIC_KERNELS:
             continue
         d = per.setdefault((name, r[0]), {})
         d[r[ni]] = float(r[mi].replace(",", ""))
@@ -68,8 +75,8 @@ def record_traffic(csv_path: str, n: int) -> dict:
                            "ncu_ms_per_launch": v["ns"] / v["launches"] / 1e6}
                        for k, v in out.items()},
            "command": ("ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                       "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused\" -c 2 --csv --log-file "
-                       f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1")}
+                       "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused\" -c 3 --csv --log-file "
+                       f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1 --what all")}
     os.makedirs(os.path.dirname(TRAFFIC_JSON), exist_ok=True)
     with open(TRAFFIC_JSON, "w") as f:
         json.dump(rec, f, indent=1)
@@ -78,15 +85,16 @@ def record_traffic(csv_path: str, n: int) -> dict:
 
 
 def traffic_for(kernel: str, n: int):
-    """DRAM bytes per launch of `kernel` at particle count n, or None when no
-    capture exists for n or the device code has changed since it was taken."""
+    """DRAM bytes per launch of `kernel` (its name with template arguments, as
+    ncu prints it) at particle count n, or None when no capture exists for n
+    or the device code has changed since it was taken."""
     try:
         rec = json.load(open(TRAFFIC_JSON))
     except (OSError, ValueError):
         return None
     if rec.get("n") != n or rec.get("digest") != kernel_source_digest():
         return None
-    k = rec.get("kernels", {}).get(kernel)
+    k = rec.get("kernels", {}).get(kernel_key(kernel))
     return None if k is None else k.get("bytes_per_launch")
 
 
@@ -94,7 +102,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=128 ** 3)
     ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--what", default="step", choices=["step", "force", "vjp"])
+    ap.add_argument("--what", default="step", choices=["step", "force", "vjp", "fused", "all"])
     ap.add_argument("--record-traffic", metavar="CSV")
     args = ap.parse_args()
     if args.record_traffic:
@@ -113,12 +121,14 @@ def main():
     acc = torch.empty((box.n, 3), dtype=torch.float32, device="cuda")
     grad = torch.empty((box.n, 3), dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
-        if args.what == "step":
+        if args.what in ("step", "fused", "all"):
             t.rebuild(pos, mass)
-        if args.what in ("step", "force"):
+        if args.what in ("step", "force", "all"):
             t.force(acc)
-        if args.what in ("step", "vjp"):
+        if args.what in ("step", "vjp", "all"):
             t.vjp(cot, grad)
+        if args.what in ("fused", "all"):
+            t.force_vjp(cot, acc, grad)
     torch.cuda.synchronize()
     st = t.stats()
     print(f"status={t.status()} n={st['n']} groups={st['n_groups']} entries={st['n_entries']} "
