@@ -243,8 +243,9 @@ def launch_count() -> int:
 
 
 class CapturedStep:
-    """One whole hot-path step -- rebuild, force, adjoint -- captured once in
-    a CUDA graph and replayed with a single launch.  `pos` (and `mass`,
+    """One whole hot-path step -- rebuild, then the forces and their adjoint
+    for the fixed cotangent `cot` in one pass -- captured once in a CUDA graph
+    and replayed with a single launch.  `pos` (and `mass`,
     `cot`) are read in place at every replay; `acc` and `grad` are written.
     The tree keeps the capacities of its allocating build: check
     tree.status() after replays whose particles moved far."""
@@ -268,9 +269,10 @@ class CapturedStep:
 
     def _body(self):
         self.tree.rebuild(self.pos, self.mass)
-        self.tree.force(self.acc)
-        if self.with_vjp:
-            self.tree.vjp(self.cot, self.grad)
+        if self.with_vjp:                    # the cotangent is fixed: forces and adjoint in one pass
+            self.tree.force_vjp(self.cot, self.acc, self.grad)
+        else:
+            self.tree.force(self.acc)
 
     def replay(self):
         self.graph.replay()
