@@ -12,7 +12,7 @@
 namespace tp {
 void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, uint64_t *key2,
                             uint32_t *perm2, void *radix_tmp, cudaStream_t s);
-void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, void *scan_tmp, cudaStream_t s);
+void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s);
 void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_tmp, cudaStream_t s);
 void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s);
 void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
@@ -144,6 +144,7 @@ struct tp_tree {
     void *radix_tmp = nullptr, *scan_tmp = nullptr;
     uint32_t *flag = nullptr, *gofs = nullptr;
     uint32_t *nch = nullptr, *nofs = nullptr;
+    int32_t *cbnd = nullptr;          // [7 cap_nodes] inner child bounds of one level's nodes
     int32_t *queue = nullptr;
     int32_t *order = nullptr;         // groups in LPT order for the work queue
     uint64_t *lpt_key = nullptr, *lpt_key2 = nullptr;
@@ -191,6 +192,7 @@ static bool alloc_nodes(tp_tree *t, int64_t cap)
     D.wn = P.get<WNode>(c);
     t->nch = P.get<uint32_t>(c);
     t->nofs = P.get<uint32_t>(c);
+    t->cbnd = P.get<int32_t>(7 * c);
     t->ncot = P.get<double>(3 * c);
     return P.ok;
 }
@@ -442,7 +444,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
     for (int attempt = 0;; attempt++) {
-        tp::build_topology(D, t->nch, t->nofs, t->scan_tmp, s);
+        tp::build_topology(D, t->nch, t->nofs, t->cbnd, t->scan_tmp, s);
         tp::build_group_starts(D, t->flag, t->gofs, t->scan_tmp, s);
         if (!sync) break;
         int32_t st = 0;

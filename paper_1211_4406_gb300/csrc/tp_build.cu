@@ -92,38 +92,57 @@ __global__ void k_init_roots(TreeDev T)
     }
 }
 
-// First index in [lo, hi) whose octant digit (at `shift`) is >= o.
-__device__ __forceinline__ int32_t octant_lower(const uint64_t *key, int32_t lo, int32_t hi, int shift,
-                                                uint32_t o)
-{
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (((uint32_t)(key[mid] >> shift) & 7u) < o) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
+// Child bounds of node i at level L: b[0] = first, b[8] = first + count and
+// b[o] = the first index of the range whose octant digit (at the level's
+// shift) is >= o.  The digits are non-decreasing over the node's range (the
+// keys are sorted and share the node's prefix), so the seven boundaries are
+// independent lower-bound searches; they advance in lockstep, seven key loads
+// in flight per step.  Returns the number of non-empty children (0 for a
+// leaf).
 __device__ __forceinline__ int child_bounds(const TreeDev &T, int32_t i, int L, int32_t *b)
 {
     const int32_t f = T.first[i], c = T.count[i];
     if (L >= TP_MAX_LEVEL || c <= T.box[T.nbx[i]].n_leaf) return 0;
     const int shift = 3 * (TP_MAX_LEVEL - 1 - L);
+    int32_t lo[8], hi[8];
+#pragma unroll
+    for (int o = 1; o < 8; o++) { lo[o] = f; hi[o] = f + c; }
+    for (int it = 0; it < 32; it++) {                 // ceil(log2(count + 1)) <= 31 steps
+        uint64_t kv[8];
+#pragma unroll
+        for (int o = 1; o < 8; o++) kv[o] = lo[o] < hi[o] ? T.key[(lo[o] + hi[o]) >> 1] : 0;
+        bool more = false;
+#pragma unroll
+        for (int o = 1; o < 8; o++) {
+            if (lo[o] < hi[o]) {
+                const int32_t mid = (lo[o] + hi[o]) >> 1;
+                if (((uint32_t)(kv[o] >> shift) & 7u) < (uint32_t)o) lo[o] = mid + 1; else hi[o] = mid;
+                more |= lo[o] < hi[o];
+            }
+        }
+        if (!more) break;
+    }
     b[0] = f;
     b[8] = f + c;
+#pragma unroll
+    for (int o = 1; o < 8; o++) b[o] = lo[o];
     int k = 0;
-    for (uint32_t o = 1; o < 8; o++) b[o] = octant_lower(T.key, b[o - 1], f + c, shift, o);
     for (int o = 0; o < 8; o++) k += b[o + 1] > b[o];
     return k;
 }
 
-// a4 (count): number of non-empty children of every node of level L.
-__global__ void k_split_count(TreeDev T, int L, uint32_t *nch)
+// a4 (count): number of non-empty children of every node of level L; their
+// inner bounds b[1..7] are kept for the write pass.
+__global__ void k_split_count(TreeDev T, int L, uint32_t *nch, int32_t *cb)
 {
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
          t += (int64_t)gridDim.x * blockDim.x) {
         int32_t b[9];
-        nch[t] = (uint32_t)child_bounds(T, (int32_t)(s0 + t), L, b);
+        const int k = child_bounds(T, (int32_t)(s0 + t), L, b);
+        nch[t] = (uint32_t)k;
+        if (k > 0)
+            for (int o = 1; o < 8; o++) cb[7 * t + o - 1] = b[o];
     }
 }
 
@@ -142,7 +161,7 @@ __global__ void k_level_finish(TreeDev T, int L)
 // a4 (write): children of level-L nodes at lstart[L+1] + scan offset, in
 // octant order; skip pointers make the breadth-first array walkable depth
 // first without a stack (next sibling, else the parent's skip).
-__global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint32_t *ofs)
+__global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint32_t *ofs, const int32_t *cb)
 {
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
     const int64_t nnext = T.lcount[L + 1], base0 = T.lstart[L + 1];
@@ -155,7 +174,10 @@ __global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint3
             continue;
         }
         int32_t b[9];
-        const int k = child_bounds(T, i, L, b);
+        b[0] = T.first[i];
+        b[8] = b[0] + T.count[i];
+        for (int o = 1; o < 8; o++) b[o] = cb[7 * t + o - 1];
+        const int k = (int)nch[t];
         const int64_t base = base0 + ofs[t];
         if (base + k > base0 + nnext) {   // truncated by an overflow
             T.child[i] = -1;
@@ -359,14 +381,14 @@ void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, u
 }
 
 // Topology and monopoles.  nch/ofs: scratch of cap_nodes u32 each.
-void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, void *scan_tmp, cudaStream_t s)
+void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s)
 {
     TP_LAUNCH(k_init_roots, (T.nbox + 127) / 128, 128, 0, s, T);
     for (int L = 0; L < TP_MAX_LEVEL; L++) {
-        TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch);
+        TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch, cb);
         scan_u32(nch, ofs, 0, T.lcount + L, T.lcount + L + 1, scan_tmp, s);
         TP_LAUNCH(k_level_finish, 1, 32, 0, s, T, L);
-        TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs);
+        TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs, cb);
     }
     for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_moments, kLevelGrid, kBlock, 0, s, T, L);
 }
