@@ -192,6 +192,7 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local_rank):
     import torch
 
+    from paper_1211_4406_gb300 import autotune
     from paper_1211_4406_gb300 import build as libbuild
     from paper_1211_4406_gb300 import inputs
     from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count, measure_peak
@@ -212,6 +213,7 @@ def run_ours(args, rank, world, local_rank):
     prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
     tree = ShortRangeTree(pos, mass, prm)                   # allocating build (setup)
     st = tree.stats()
+    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"clustered-2M|n{box.n}")   # setup, not timed
     acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
     grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -351,12 +353,13 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(),
-        "roofline": roofline("k_vjp_fused<4, true>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
+        "config": dict(workload_config(), tile_autotuned={"forward_particles_per_thread": tile[0],
+                                                          "adjoint_entries_per_thread": tile[1]}),
+        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
                              "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
-        "roofline_forward": roofline("k_pair_packed<2>", kp_ms, FLOPS_PER_INTERACTION,
+        "roofline_forward": roofline(f"k_pair_packed<{tile[0]}>", kp_ms, FLOPS_PER_INTERACTION,
                                      "FP32 forward pair kernel, separate call"),
-        "roofline_adjoint": roofline("k_vjp_fused<4, false>", kv_ms, VJP_FLOPS_PER_INTERACTION,
+        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false>", kv_ms, VJP_FLOPS_PER_INTERACTION,
                                      "FP32 adjoint pair kernel, separate call"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},
@@ -431,6 +434,7 @@ def run_batched(args, rank, world, local_rank):
     tree = ShortRangeTree(pos, mass, prm, box_offsets=offs.tolist())
     st = tree.stats()
     n = tree.n
+    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"batched-64|n{n}")
     acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
     grad = torch.empty((n, 3), dtype=torch.float64, device=dev)
     l0 = launch_count()
@@ -478,7 +482,9 @@ def run_batched(args, rank, world, local_rank):
         "config": {"workload": "batched-64", "nbox": 64, "n_total": int(n), "n_min": int(min(b.n for b in boxes)),
                    "n_max": int(max(b.n for b in boxes)), "kinds": "even uniform, odd clustered",
                    "r_cut": "3/N_b^(1/3)", "eps": "1/(50 N_b^(1/3))", "theta": 0.5,
-                   "n_crit_autotuned": hist, "graph": "rebuild + force + adjoint of all boxes in one replay",
+                   "n_crit_autotuned": hist,
+                   "tile_autotuned": {"forward_particles_per_thread": tile[0], "adjoint_entries_per_thread": tile[1]},
+                   "graph": "rebuild + one-pass forces and adjoint of all boxes in one replay",
                    "l2": "flushed (256 MiB write) before every timed replay"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": pos_h.numel() * 8 + mass_h.numel() * 8
                 + cot_h.numel() * 4, "d2h_bytes_per_step": acc_h.numel() * 4 + grad_h.numel() * 8,

@@ -179,6 +179,14 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
 
 tp_status tp_tree_free(tp_tree *t);
 
+/* Tile shape of the FP32 pair kernels, a tuning knob with no counterpart in
+ * the paper: group particles per thread of the forward kernel (1 or 2) and
+ * list entries per thread of the adjoint kernel (2 or 4); 2 and 4 by default.
+ * Applies to later force / vjp calls on t (not to calls already enqueued).
+ * Results agree to rounding (the per-particle sums are taken in a different
+ * order).  TP_ERR_INVALID_ARG for other values.                              */
+tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entries);
+
 /* Kernel timing, a measurement aid with no counterpart in the paper.  With
  * enable != 0 the tree records CUDA events on the call's stream immediately
  * before and after its main FP32 pair-kernel launch in tp_short_range_force

@@ -153,7 +153,14 @@ class ShortRangeTree:
     def status(self) -> int:
         return int(_lib.load().tp_tree_status(self.handle))
 
-    # -- kernel timing (events around the main pair and adjoint launches) ------
+    # -- tuning and kernel timing ----------------------------------------------
+    def set_tile(self, fwd_particles: int = 2, adj_entries: int = 4) -> None:
+        """Particles per thread of the forward pair kernel (1, 2) and list
+        entries per thread of the adjoint kernel (2, 4)."""
+        _lib.check(_lib.load().tp_tree_set_tile(self.handle, int(fwd_particles), int(adj_entries)),
+                   "tp_tree_set_tile")
+        self.tile = (int(fwd_particles), int(adj_entries))
+
     def set_kernel_timing(self, enable: bool = True) -> None:
         _lib.check(_lib.load().tp_tree_set_kernel_timing(self.handle, 1 if enable else 0),
                    "tp_tree_set_kernel_timing")

@@ -1,9 +1,13 @@
-"""Group-size autotuner for the batched persistent launch.
+"""Autotuner for the group size and the tile shape of the pair kernels.
 
 For every box the group size n_crit (Barnes' <N_i>, Sec. II) is chosen among
 candidates by timing the whole step (rebuild, force, adjoint) on the GPU; the
 choice is cached in JSON keyed by GPU name, SM count, particle-count bucket
-(log2) and the box kind, so boxes of the same shape reuse it.
+(log2) and the box kind, so boxes of the same shape reuse it.  For a built
+tree (one box or a whole batch) the tile shape -- group particles per thread
+of the forward kernel, list entries per thread of the adjoint kernel -- is
+chosen the same way, by timing rebuild + the one-pass forces and adjoint for
+each shape on the tree itself, and cached under a caller-given key.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ import torch
 from .api import Params, ShortRangeTree
 
 CANDIDATES = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+TILES = ((2, 4), (1, 4), (2, 2), (1, 2))   # (forward particles per thread, adjoint entries per thread)
 
 
 def default_cache_path() -> str:
@@ -96,3 +101,40 @@ def tune_boxes(boxes, kinds, base_params, cache_path: str | None = None, candida
         out.append(int(cache[key]["n_crit"]))
     save_cache(cache_path, cache)
     return out
+
+
+def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cache_path: str | None = None,
+              tiles=TILES, reps: int = 3) -> tuple[int, int]:
+    """Tile shape of `tree` (set on it and returned): the shape with the
+    shortest median of rebuild + one-pass forces and adjoint.  With a key the
+    choice is cached and reused for trees of the same workload."""
+    cache_path = cache_path or default_cache_path()
+    cache = load_cache(cache_path)
+    ck = f"{gpu_key()}|tile|{key}" if key else None
+    if ck and ck in cache:
+        best = tuple(cache[ck]["tile"])
+        tree.set_tile(*best)
+        return best
+    acc = torch.empty((tree.n, 3), dtype=tree.acc_dtype, device=pos.device)
+    grad = torch.empty((tree.n, 3), dtype=torch.float64, device=pos.device)
+    times = {}
+    for tile in tiles:
+        tree.set_tile(*tile)
+        ts = []
+        for r in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            tree.rebuild(pos, mass)
+            tree.force_vjp(cot, acc, grad)
+            b.record()
+            b.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        ts.sort()
+        times[tile] = ts[len(ts) // 2]
+    best = min(times, key=times.get)
+    tree.set_tile(*best)
+    if ck:
+        cache[ck] = {"tile": list(best), "ms": {f"{f}x{e}": v for (f, e), v in times.items()}}
+        save_cache(cache_path, cache)
+    return best

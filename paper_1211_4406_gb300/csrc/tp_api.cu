@@ -22,20 +22,21 @@ void walk_write(TreeDev &T, cudaStream_t s);
 void walk_top_scan(TreeDev &T, void *scan_tmp, cudaStream_t s);
 void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s);
 void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
-                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries);
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
                    const int32_t *order, int64_t G, cudaStream_t s);
 void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s);
 void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, double *ncot, int32_t *queue,
-                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                         int adj_entries);
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
-                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles);
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s);
 void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1);
+             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries);
 void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
              const int32_t *order, int64_t G, cudaStream_t s);
 }  // namespace tp
@@ -160,6 +161,8 @@ struct tp_tree {
     std::vector<int64_t> win_first, win_count;
     int64_t *d_wsz = nullptr;         // [kMaxWindows] device copies of the window sizes
     int64_t *d_etot = nullptr;        // entries summed over the windows
+    // tile shapes of the FP32 pair kernels (tp_tree_set_tile)
+    int32_t fwd_particles = 2, adj_entries = 4;
     // kernel timing: events around the main forward / adjoint kernel launches
     bool ktiming = false, kf_rec = false, kv_rec = false;
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -656,7 +659,8 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
         t->kf_rec = false;
         tp_status e = for_each_window(t, s, [&](TreeDev &V) {
             if (f32)
-                tp::pair_forward_f32(V, (float *)acc, t->queue, t->order, V.cap_groups, s, nullptr, nullptr);
+                tp::pair_forward_f32(V, (float *)acc, t->queue, t->order, V.cap_groups, s, nullptr, nullptr,
+                                     t->fwd_particles);
             else
                 tp::pair_forward_f64(V, (double *)acc, V.cap_groups, s);
         });
@@ -666,7 +670,7 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
     if (t->precision == TP_FP32) {
         cudaMemsetAsync(acc, 0, sizeof(float) * 3 * (size_t)t->n, s);
         tp::pair_forward_f32(t->D, (float *)acc, t->queue, t->order, t->D.cap_groups, s,
-                             t->ktiming ? t->kev[0] : nullptr, t->ktiming ? t->kev[1] : nullptr);
+                             t->ktiming ? t->kev[0] : nullptr, t->ktiming ? t->kev[1] : nullptr, t->fwd_particles);
         t->kf_rec = t->ktiming;
     } else {
         cudaMemsetAsync(acc, 0, sizeof(double) * 3 * (size_t)t->n, s);
@@ -689,7 +693,7 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
         tp_status e = for_each_window(t, s, [&](TreeDev &V) {
             if (f32)
                 tp::vjp_pairs_f32(V, (const float *)cot, t->gs, t->ncot, t->queue, t->order, V.cap_groups, s,
-                                  nullptr, nullptr);
+                                  nullptr, nullptr, t->adj_entries);
             else
                 tp::vjp_pairs_f64(V, (const double *)cot, t->gs, t->ncot, t->queue, t->order, V.cap_groups, s);
         });
@@ -700,7 +704,7 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
     if (t->precision == TP_FP32)
     {
         tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s,
-                    t->ktiming ? t->kev[2] : nullptr, t->ktiming ? t->kev[3] : nullptr);
+                    t->ktiming ? t->kev[2] : nullptr, t->ktiming ? t->kev[3] : nullptr, t->adj_entries);
         t->kv_rec = t->ktiming && t->D.cap_groups > 0;
     }
     else
@@ -727,13 +731,13 @@ tp_status tp_short_range_force_vjp(tp_tree *t, void *acc, const void *cot, doubl
         t->kv_rec = false;
         tp_status e = for_each_window(t, s, [&](TreeDev &V) {
             tp::force_vjp_pairs_f32(V, (float *)acc, (const float *)cot, t->gs, t->ncot, t->queue, t->order,
-                                    V.cap_groups, s, nullptr, nullptr);
+                                    V.cap_groups, s, nullptr, nullptr, t->adj_entries);
         });
         if (e != TP_OK) return e;
     } else {
         tp::force_vjp_pairs_f32(t->D, (float *)acc, (const float *)cot, t->gs, t->ncot, t->queue, t->order,
                                 t->D.cap_groups, s, t->ktiming ? t->kev[2] : nullptr,
-                                t->ktiming ? t->kev[3] : nullptr);
+                                t->ktiming ? t->kev[3] : nullptr, t->adj_entries);
         t->kv_rec = t->ktiming && t->D.cap_groups > 0;
     }
     tp::vjp_end(t->D, grad, t->gs, t->ncot, s);
@@ -860,6 +864,15 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries)
     if (e == TP_OK && st.n_entries > 0)
         e = cuda_status(cudaMemcpy(entries, t->D.ent, sizeof(int32_t) * st.n_entries, cudaMemcpyDeviceToHost));
     return e;
+}
+
+tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entries)
+{
+    if (!t || (fwd_particles != 1 && fwd_particles != 2) || (adj_entries != 2 && adj_entries != 4))
+        return TP_ERR_INVALID_ARG;
+    t->fwd_particles = fwd_particles;
+    t->adj_entries = adj_entries;
+    return TP_OK;
 }
 
 tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable)

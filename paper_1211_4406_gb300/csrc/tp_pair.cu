@@ -19,8 +19,9 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kTile = 256;
-constexpr int kVjpEntries = 4;     // list entries per thread in the fused adjoint
-constexpr int kPairParticles = 2;  // particles per thread in the forward pair kernel
+// Tile shapes (chosen per tree, see tp_tree_set_tile): particles per thread of
+// the forward pair kernel (1 or 2) and list entries per thread of the fused
+// adjoint (2 or 4).
 
 __device__ __forceinline__ float sqrt_approx(float x)
 {
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // adds their particle-side values before the reduce-scatter, so its cost is
 // shared by E entries.
 template <int E, bool FWD>
-__global__ void __launch_bounds__(kThreads, 4) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
+__global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order, float *acc)
 {
     constexpr int kWarps = kThreads / 32;
@@ -950,19 +951,25 @@ int num_sms()
 }
 
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
-                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                      cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles)
 {
     if (G <= 0) return;
     cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
     static const int bps = occupancy(k_pair<float, true>, kThreads);
-    static const int bpp = occupancy(k_pair_packed<kPairParticles>, kThreads);
+    static const int bp1 = occupancy(k_pair_packed<1>, kThreads);
+    static const int bp2 = occupancy(k_pair_packed<2>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
     };
     if (ev0) cudaEventRecord(ev0, s);
-    auto kp = k_pair_packed<kPairParticles>;
-    TP_LAUNCH(kp, grid_of(bpp), kThreads, 0, s, T, acc, queue + 1, order);
+    if (fwd_particles == 1) {
+        auto kp = k_pair_packed<1>;
+        TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
+    } else {
+        auto kp = k_pair_packed<2>;
+        TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
+    }
     if (ev1) cudaEventRecord(ev1, s);
     auto k = k_pair<float, true>;
     TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
@@ -985,14 +992,34 @@ void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s)
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
 }
 
+// The fused adjoint kernel with E entries per thread, with or without the
+// forward sum, on its own occupancy.
+template <int E>
+static void launch_vjp_fused(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
+                             const int32_t *order, int64_t G, float *acc, cudaStream_t s)
+{
+    static const int nbf = occupancy(k_vjp_fused<E, false>, kThreads);
+    static const int nbw = occupancy(k_vjp_fused<E, true>, kThreads);
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    if (acc) {
+        auto kw = k_vjp_fused<E, true>;
+        TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
+    } else {
+        auto kf = k_vjp_fused<E, false>;
+        TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, cot, gs, ncot, queue, order, nullptr);
+    }
+}
+
 template <class R>
 static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
-                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc = nullptr)
+                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc = nullptr,
+                      int adj_entries = 4)
 {
     if (G <= 0) return;
     static const int nb = occupancy(k_vjp<R>, kThreads);
-    static const int nbf = occupancy(k_vjp_fused<kVjpEntries, false>, kThreads);
-    static const int nbw = occupancy(k_vjp_fused<kVjpEntries, true>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
@@ -1000,14 +1027,10 @@ static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_
     if (sizeof(R) == 4) {
         cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
         if (ev0) cudaEventRecord(ev0, s);
-        if (acc) {
-            auto kw = k_vjp_fused<kVjpEntries, true>;
-            TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order, acc);
-        } else {
-            auto kf = k_vjp_fused<kVjpEntries, false>;
-            TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, (const float *)cot, gs, ncot, queue + 1, order,
-                      nullptr);
-        }
+        if (adj_entries == 2)
+            launch_vjp_fused<2>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
+        else
+            launch_vjp_fused<4>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
         if (ev1) cudaEventRecord(ev1, s);
     } else {
         cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
@@ -1024,19 +1047,20 @@ void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s)
 }
 
 void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
-                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                   int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries)
 {
-    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1);
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, nullptr, adj_entries);
 }
 
 // Forward and adjoint of the FP32 path in one pass over the lists: the fused
 // adjoint kernel also sums Eq. 2 for the groups it takes; the general forward
 // kernel covers the rest.  acc must be zeroed by the caller.
 void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, double *ncot, int32_t *queue,
-                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+                         const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                         int adj_entries)
 {
     if (G <= 0) return;
-    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc);
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc, adj_entries);
     static const int bps = occupancy(k_pair<float, true>, kThreads);
     const int64_t gr = (int64_t)num_sms() * bps;
     cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
@@ -1051,10 +1075,10 @@ void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int3
 }
 
 void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1)
+             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries)
 {
     vjp_begin(T, gs, ncot, s);
-    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1);
+    vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, nullptr, adj_entries);
     vjp_end(T, grad, gs, ncot, s);
 }
 

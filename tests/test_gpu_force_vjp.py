@@ -72,3 +72,32 @@ def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
             assert np.abs(grad_c.cpu().numpy() - grad.cpu().numpy()).max() <= 1e-12 * scale
             tc.close()
         t.close()
+
+
+@pytest.mark.parametrize("tile", [(1, 2), (1, 4), (2, 2), (2, 4)])
+def test_every_tile_shape(tile):
+    """Each tile shape (forward particles per thread, adjoint entries per
+    thread) meets the oracle bounds, for the separate and the one-pass calls."""
+    box = inputs.config_box(2, n_override=2 ** 15)
+    pos = torch.tensor(box.pos, device="cuda")
+    mass = torch.tensor(box.mass, device="cuda")
+    w = inputs.cotangent(box.n, box.seed + 7)
+    cot = torch.tensor(w, device="cuda")
+    t = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, 64, 8, "fp32"))
+    t.set_tile(*tile)
+    ot = oracle.OracleTree(box.pos, box.mass, 8, 64)
+    ot.lists(box.r_cut, box.theta)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    gref = ot.list_vjp(box.G, box.eps, box.r_cut, w.astype(np.float64))
+    scale = np.sqrt(np.mean(gref ** 2))
+    a1 = t.force().double().cpu().numpy()
+    g1 = t.vjp(cot).cpu().numpy()
+    a2, g2 = t.force_vjp(cot)
+    for a in (a1, a2.double().cpu().numpy()):
+        rms, mx = rel_err(a, ref)
+        assert rms <= 1e-6 and mx <= 1e-4, (tile, rms, mx)
+    for g in (g1, g2.cpu().numpy()):
+        assert np.all(np.abs(g - gref) <= 1e-4 * np.maximum(np.abs(gref), scale)), tile
+    with pytest.raises(Exception):
+        t.set_tile(3, 4)
+    t.close()
