@@ -6,8 +6,9 @@ choice is cached in JSON keyed by GPU name, SM count, particle-count bucket
 (log2) and the box kind, so boxes of the same shape reuse it.  For a built
 tree (one box or a whole batch) the tile shape -- group particles per thread
 of the forward kernel, list entries per thread of the adjoint kernel -- is
-chosen the same way, by timing rebuild + the one-pass forces and adjoint for
-each shape on the tree itself, and cached under a caller-given key.
+chosen the same way on the tree itself -- the forward shape by timing the
+force call, the adjoint shape by timing the one-pass forces and adjoint --
+and cached under a caller-given key.
 """
 from __future__ import annotations
 
@@ -20,7 +21,6 @@ import torch
 from .api import Params, ShortRangeTree
 
 CANDIDATES = (16, 24, 32, 48, 64, 96, 128, 192, 256)
-TILES = ((2, 4), (1, 4), (2, 2), (1, 2))   # (forward particles per thread, adjoint entries per thread)
 
 
 def default_cache_path() -> str:
@@ -104,10 +104,12 @@ def tune_boxes(boxes, kinds, base_params, cache_path: str | None = None, candida
 
 
 def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cache_path: str | None = None,
-              tiles=TILES, reps: int = 3) -> tuple[int, int]:
-    """Tile shape of `tree` (set on it and returned): the shape with the
-    shortest median of rebuild + one-pass forces and adjoint.  With a key the
-    choice is cached and reused for trees of the same workload."""
+              fwd_choices=(2, 1), adj_choices=(4, 2), reps: int = 3) -> tuple[int, int]:
+    """Tile shape of `tree` (set on it and returned): group particles per
+    thread of the forward kernel, timed on the force call, and list entries
+    per thread of the adjoint kernel, timed on the one-pass forces + adjoint
+    call; each the choice with the shortest median.  With a key the choice is
+    cached and reused for trees of the same workload."""
     cache_path = cache_path or default_cache_path()
     cache = load_cache(cache_path)
     ck = f"{gpu_key()}|tile|{key}" if key else None
@@ -117,24 +119,33 @@ def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cach
         return best
     acc = torch.empty((tree.n, 3), dtype=tree.acc_dtype, device=pos.device)
     grad = torch.empty((tree.n, 3), dtype=torch.float64, device=pos.device)
-    times = {}
-    for tile in tiles:
-        tree.set_tile(*tile)
+    tree.rebuild(pos, mass)
+
+    def median_ms(fn):
         ts = []
         for r in range(reps + 1):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            tree.rebuild(pos, mass)
-            tree.force_vjp(cot, acc, grad)
+            fn()
             b.record()
             b.synchronize()
             if r:
                 ts.append(a.elapsed_time(b))
         ts.sort()
-        times[tile] = ts[len(ts) // 2]
-    best = min(times, key=times.get)
+        return ts[len(ts) // 2]
+
+    fwd_ms, adj_ms = {}, {}
+    for f in fwd_choices:
+        tree.set_tile(f, adj_choices[0])
+        fwd_ms[f] = median_ms(lambda: tree.force(acc))
+    best_f = min(fwd_ms, key=fwd_ms.get)
+    for e in adj_choices:
+        tree.set_tile(best_f, e)
+        adj_ms[e] = median_ms(lambda: tree.force_vjp(cot, acc, grad))
+    best = (best_f, min(adj_ms, key=adj_ms.get))
     tree.set_tile(*best)
     if ck:
-        cache[ck] = {"tile": list(best), "ms": {f"{f}x{e}": v for (f, e), v in times.items()}}
+        cache[ck] = {"tile": list(best), "forward_ms": {str(k): v for k, v in fwd_ms.items()},
+                     "one_pass_ms": {str(k): v for k, v in adj_ms.items()}}
         save_cache(cache_path, cache)
     return best
