@@ -69,15 +69,24 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling every 100 ms and wait (up to 3 s) for the first sample."""
+        self.first = 0
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:
+                time.sleep(0.02)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark(self):
+        """The timed region starts: later summaries use samples from here on."""
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -86,6 +95,7 @@ class ClockSampler:
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)                      # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -93,7 +103,7 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for l in self.lines[self.first:]:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -243,6 +253,8 @@ def run_ours(args, rank, world, local_rank):
         tree.vjp(cot, grad)
         evs[3].record(stream)
 
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
     for _ in range(args.warmup):
         flush.zero_()
         step(pos, mass, cot)
@@ -252,8 +264,7 @@ def run_ours(args, rank, world, local_rank):
         raise RuntimeError(f"tree status {status} after warm-up")
 
     # ---- device-resident timed region -------------------------------------
-    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
-    clocks.start()
+    clocks.mark()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -448,6 +459,7 @@ def run_batched(args, rank, world, local_rank):
         raise RuntimeError("tree status after warm-up replays")
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
+    clocks.mark()
     ms = _timed_replays(step.replay, args.steps, flush, stream)
     clk = clocks.stop()
     if tree.status() != 0:
@@ -617,6 +629,7 @@ def run_large(args, rank, world, local_rank):
         raise RuntimeError(f"tree status {tree.status()} after warm-up")
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
+    clocks.mark()
     l0 = launch_count()
     phases = []
     for _ in range(args.steps):
@@ -682,7 +695,7 @@ WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k":
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
