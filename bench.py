@@ -49,10 +49,27 @@ SM_MAX_MHZ = 2070.0
 CONFIG_K = 2
 
 
-def workload_config():
+def workload_config(paper_regime: bool = False):
+    if paper_regime:
+        return {"workload": "paper-regime-2M", "n": 128 ** 3, "halos": 2000, "r_cut": "7.5/128",
+                "eps": "1/6400", "theta": 0.5, "n_crit": 128, "n_leaf": 8, "seed": 14408,
+                "l2": "flushed (256 MiB write) before every timed step",
+                "why": "the paper's list shapes (Table I: <N_i> ~ 115, <N_j> ~ 2300; r_cut = 7.5 mean "
+                       "spacings as in its 4096^3 PM mesh for 10240^3 particles)"}
     return {"workload": "clustered-2M", "n": 128 ** 3, "halos": 2000, "r_cut": "3/128",
             "eps": "1/6400", "theta": 0.5, "n_crit": 64, "n_leaf": 8, "seed": 14408,
             "l2": "flushed (256 MiB write) before every timed step"}
+
+
+def bench_box(paper_regime: bool = False):
+    """The clustered 2M box; in the paper's regime with r_cut = 7.5/128 and
+    n_crit = 128 instead of 3/128 and 64."""
+    from paper_1211_4406_gb300 import inputs
+    box = inputs.config_box(CONFIG_K)
+    if paper_regime:
+        box.r_cut = 7.5 / 128
+        box.n_crit = 128
+    return box
 
 
 # ---------------------------------------------------------------------------
@@ -199,7 +216,11 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def run_ours(args, rank, world, local_rank):
+def run_paper_regime(args, rank, world, local_rank):
+    run_ours(args, rank, world, local_rank, paper_regime=True)
+
+
+def run_ours(args, rank, world, local_rank, paper_regime=False):
     import torch
 
     from paper_1211_4406_gb300 import autotune
@@ -212,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    box = inputs.config_box(CONFIG_K)
+    box = bench_box(paper_regime)
     w = inputs.cotangent(box.n, box.seed + 7)
     pos_h = torch.tensor(box.pos).pin_memory()
     mass_h = torch.tensor(box.mass).pin_memory()
@@ -223,7 +244,8 @@ def run_ours(args, rank, world, local_rank):
     prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
     tree = ShortRangeTree(pos, mass, prm)                   # allocating build (setup)
     st = tree.stats()
-    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"clustered-2M|n{box.n}")   # setup, not timed
+    wl = workload_config(paper_regime)["workload"]
+    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"{wl}|n{box.n}")   # setup, not timed
     acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
     grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -361,10 +383,11 @@ def run_ours(args, rank, world, local_rank):
     meas_ffma2 = measure_peak("fp32x2")
     meas_dfma = measure_peak("fp64")
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC.replace("clustered 2M box", "clustered 2M box, paper's list regime") if paper_regime
+        else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(), tile_autotuned={"forward_particles_per_thread": tile[0],
+        "config": dict(workload_config(paper_regime), tile_autotuned={"forward_particles_per_thread": tile[0],
                                                           "adjoint_entries_per_thread": tile[1]}),
         "roofline": roofline(f"k_vjp_fused<{tile[1]}, true>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
                              "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
@@ -391,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
         "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions",
                                     "n_ambiguous", "mean_ni", "mean_nj", "max_nj")},
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not paper_regime:
         r = oracle_sample_rate(box, w, steps=1)
         line["cpu_baseline"] = {"value": r["per_step_interactions"] / r["times"][0], "unit": UNIT,
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
@@ -689,7 +712,7 @@ def run_large(args, rank, world, local_rank):
 
 
 WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64,
-             "clustered-134M": run_large}
+             "clustered-134M": run_large, "paper-regime-2M": run_paper_regime}
 
 
 def main():
@@ -703,7 +726,8 @@ def main():
                     help="clustered-2M (the default line); batched-64: 64 independent boxes, "
                          "autotuned n_crit, the whole step as one CUDA-graph replay; uniform-32k: "
                          "the plain FP64 path on the uniform 32^3 box; clustered-134M: "
-                         "the 512^3 throughput box (chunked lists)")
+                         "the 512^3 throughput box (chunked lists); paper-regime-2M: the 2M box with the "
+                         "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
