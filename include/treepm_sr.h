@@ -180,7 +180,7 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
 tp_status tp_tree_free(tp_tree *t);
 
 /* Tile shape of the FP32 pair kernels, a tuning knob with no counterpart in
- * the paper: group particles per thread of the forward kernel (1 or 2) and
+ * the paper: group particles per thread of the forward kernel (1, 2 or 4) and
  * list entries per thread of the adjoint kernel (2 or 4); 2 and 4 by default.
  * Applies to later force / vjp calls on t (not to calls already enqueued).
  * Results agree to rounding (the per-particle sums are taken in a different

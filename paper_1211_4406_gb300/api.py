@@ -155,7 +155,7 @@ class ShortRangeTree:
 
     # -- tuning and kernel timing ----------------------------------------------
     def set_tile(self, fwd_particles: int = 2, adj_entries: int = 4) -> None:
-        """Particles per thread of the forward pair kernel (1, 2) and list
+        """Particles per thread of the forward pair kernel (1, 2, 4) and list
         entries per thread of the adjoint kernel (2, 4)."""
         _lib.check(_lib.load().tp_tree_set_tile(self.handle, int(fwd_particles), int(adj_entries)),
                    "tp_tree_set_tile")

@@ -20,7 +20,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kTile = 256;
 // Tile shapes (chosen per tree, see tp_tree_set_tile): particles per thread of
-// the forward pair kernel (1 or 2) and list entries per thread of the fused
+// the forward pair kernel (1, 2 or 4) and list entries per thread of the fused
 // adjoint (2 or 4).
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -958,6 +958,7 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
     static const int bps = occupancy(k_pair<float, true>, kThreads);
     static const int bp1 = occupancy(k_pair_packed<1>, kThreads);
     static const int bp2 = occupancy(k_pair_packed<2>, kThreads);
+    static const int bp4 = occupancy(k_pair_packed<4>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
@@ -966,6 +967,9 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
     if (fwd_particles == 1) {
         auto kp = k_pair_packed<1>;
         TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
+    } else if (fwd_particles == 4) {
+        auto kp = k_pair_packed<4>;
+        TP_LAUNCH(kp, grid_of(bp4), kThreads, 0, s, T, acc, queue + 1, order);
     } else {
         auto kp = k_pair_packed<2>;
         TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
