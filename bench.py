@@ -711,8 +711,82 @@ def run_large(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_leapfrog(args, rank, world, local_rank):
+    """The adjoint workload: the gradient of L = sum w . a_T with respect to
+    x0 through 10 FP32 kick-drift-kick steps (dt = 1e-3) on the clustered
+    262k box (250 halos, r_cut = 3/64, eps = 1/3200), with one checkpoint per
+    step: 11 force evaluations forward, 10 rebuilds + adjoints and the first
+    force's adjoint backward.  Trees are rebuilt in place across the steps."""
+    import torch
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count
+    from paper_1211_4406_gb300.autograd import leapfrog
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    box = inputs.config_box(4)
+    steps, dt = 10, 1e-3
+    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
+    pos_h = torch.tensor(box.pos).pin_memory()
+    w_h = torch.tensor(inputs.cotangent(box.n, box.seed + 7)).pin_memory()
+    mass = torch.tensor(box.mass, device=dev)
+    wt = w_h.to(dev).double()
+    x0 = pos_h.to(dev).requires_grad_(True)
+    v0 = torch.zeros_like(x0)
+    t0 = ShortRangeTree(x0.detach(), mass, prm)
+    inter = int(t0.stats()["n_interactions"])
+    t0.close()
+
+    def grad_once(reuse=True):
+        x0.grad = None
+        _, _, aT = leapfrog(x0, v0, mass, prm, dt, steps, reuse_trees=reuse)
+        (aT.double() * wt).sum().backward()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        grad_once()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    clocks.mark()
+    l0 = launch_count()
+    ms = _timed_replays(grad_once, args.steps, flush, stream)
+    launches = launch_count() - l0
+    clk = clocks.stop()
+    ms_fresh = _timed_replays(lambda: grad_once(False), max(2, args.steps // 4), flush, stream)
+    g = x0.grad.detach()
+    e2e_ms = _timed_replays(lambda: (x0.data.copy_(pos_h, non_blocking=True), grad_once(),
+                                     g.cpu()), max(2, args.steps // 4), flush, stream)
+    per = 2 * (steps + 1) * inter              # forces and adjoints of one gradient
+    tot_ms, = max_over_ranks([sum(ms)], device=dev)
+    value = whole_job_rate(world, per, args.steps, tot_ms)
+    if rank != 0:
+        return
+    line = {
+        "metric": "short-range interactions/s (FP32 10-step leapfrog gradient, clustered 262k box)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "leapfrog-262k", "n": box.n, "halos": 250, "r_cut": "3/64", "eps": "1/3200",
+                   "theta": 0.5, "n_crit": box.n_crit, "kdk_steps": steps, "dt": dt,
+                   "step": "one gradient: 11 forces forward, 11 adjoints backward, checkpoint per KDK step",
+                   "l2": "flushed (256 MiB write) before every timed gradient"},
+        "e2e": {"value": whole_job_rate(world, per, len(e2e_ms), sum(e2e_ms)), "unit": UNIT,
+                "h2d_bytes_per_step": box.n * 24, "d2h_bytes_per_step": box.n * 24,
+                "ms_per_step": sum(e2e_ms) / len(e2e_ms)},
+        "gpu_launches": launches, "clocks": clk,
+        "interactions_per_force": inter,
+        "ms_per_gradient_fresh_trees": sum(ms_fresh) / len(ms_fresh),
+    }
+    print(json.dumps(line), flush=True)
+
+
 WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64,
-             "clustered-134M": run_large, "paper-regime-2M": run_paper_regime}
+             "clustered-134M": run_large, "paper-regime-2M": run_paper_regime, "leapfrog-262k": run_leapfrog}
 
 
 def main():
@@ -727,7 +801,8 @@ def main():
                          "autotuned n_crit, the whole step as one CUDA-graph replay; uniform-32k: "
                          "the plain FP64 path on the uniform 32^3 box; clustered-134M: "
                          "the 512^3 throughput box (chunked lists); paper-regime-2M: the 2M box with the "
-                         "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128)")
+                         "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128); leapfrog-262k: the gradient "
+                         "of a 10-step KDK chain (checkpointed adjoint)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

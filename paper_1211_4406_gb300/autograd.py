@@ -4,7 +4,8 @@ ShortRangeForce: forward = tree build + Eq. 2 on the lists (tp_build_tree +
 tp_short_range_force); backward = tp_short_range_vjp on the same tree (walk
 decisions are piecewise constant and not differentiated).
 
-KDKStep: one leapfrog step with the short-range force only,
+KDKStep: one leapfrog step with the short-range force only (the steps of one
+chain reuse a forward tree and a backward tree, rebuilt in place),
     v_h = v + a dt/2,  x1 = x + v_h dt,  a1 = F(x1),  v1 = v_h + a1 dt/2,
 saving only its inputs (x, v, a): backward rebuilds the tree at x1 (the
 recomputation that makes every step a checkpoint) and chains the adjoint
@@ -60,28 +61,64 @@ def short_range_force(pos, mass, params: Params) -> torch.Tensor:
     return ShortRangeForce.apply(pos, mass, params)
 
 
-def _force(x, mass, params):
-    t = ShortRangeTree(x, mass, params)
+class _TreeSlot:
+    """One tree reused across the steps of a leapfrog chain: rebuilt in place
+    (no allocation) from each step's positions, replaced by a fresh allocating
+    build when a rebuild exceeded the capacities of the tree's first build
+    (the step synchronises anyway, so the latched status is read there)."""
+
+    def __init__(self):
+        self.tree = None
+
+    def tree_at(self, x, mass, params):
+        if self.tree is None:
+            self.tree = ShortRangeTree(x, mass, params)
+        else:
+            self.tree.rebuild(x, mass)
+        return self.tree
+
+    def check(self, x, mass, params) -> bool:
+        """True if the last rebuild was good; else rebuilds with allocation."""
+        if self.tree.status() == 0:
+            return True
+        self.tree.close()
+        self.tree = ShortRangeTree(x, mass, params)
+        return False
+
+    def close(self):
+        if self.tree is not None:
+            self.tree.close()
+            self.tree = None
+
+
+def _force(x, mass, params, slot: _TreeSlot | None = None):
+    if slot is None:
+        t = ShortRangeTree(x, mass, params)
+        return t, t.force()
+    t = slot.tree_at(x, mass, params)
     a = t.force()
-    return t, a
+    if not slot.check(x, mass, params):
+        a = slot.tree.force()
+    return slot.tree, a
 
 
 class KDKStep(torch.autograd.Function):
     """(x, v, a) -> (x1, v1, a1), one checkpointed kick-drift-kick step."""
 
     @staticmethod
-    def forward(ctx, x, v, a, mass, params: Params, dt: float):
+    def forward(ctx, x, v, a, mass, params: Params, dt: float, slots=None):
         vh = _copy64(v)
         axpy(vh, a.contiguous(), 0.5 * dt)
         x1 = _copy64(x)
         axpy(x1, vh, dt)
-        t, a1 = _force(x1, mass, params)
+        t, a1 = _force(x1, mass, params, None if slots is None else slots[0])
         v1 = _copy64(vh)
         axpy(v1, a1, 0.5 * dt)
         torch.cuda.current_stream().synchronize()
-        t.close()
+        if slots is None:
+            t.close()
         ctx.save_for_backward(x, v, a)
-        ctx.mass, ctx.params, ctx.dt = mass, params, dt
+        ctx.mass, ctx.params, ctx.dt, ctx.slots = mass, params, dt, slots
         ctx.a_dtype = a.dtype
         return x1, v1, a1
 
@@ -97,7 +134,13 @@ class KDKStep(torch.autograd.Function):
         axpy(vh, a.contiguous(), 0.5 * dt)
         x1 = _copy64(x)
         axpy(x1, vh, dt)
-        tree = ShortRangeTree(x1, ctx.mass, ctx.params)
+        slot = None if ctx.slots is None else ctx.slots[1]
+        if slot is None:
+            tree = ShortRangeTree(x1, ctx.mass, ctx.params)
+        else:
+            slot.tree_at(x1, ctx.mass, ctx.params)
+            slot.check(x1, ctx.mass, ctx.params)
+            tree = slot.tree
         # g_a1' = g_a1 + (dt/2) g_v1, in the force's precision
         ga = torch.empty(x.shape, dtype=torch.float64, device=dev)
         scale(ga, g_v1.contiguous(), 0.5 * dt)
@@ -112,15 +155,20 @@ class KDKStep(torch.autograd.Function):
         g_a = torch.empty(x.shape, dtype=ctx.a_dtype, device=dev)
         scale(g_a, gvh, 0.5 * dt)                        # g_a = (dt/2) g_vh
         torch.cuda.current_stream().synchronize()
-        tree.close()
-        return gx, gvh, g_a, None, None, None
+        if slot is None:
+            tree.close()
+        return gx, gvh, g_a, None, None, None, None
 
 
-def leapfrog(x0: torch.Tensor, v0: torch.Tensor, mass, params: Params, dt: float, steps: int):
+def leapfrog(x0: torch.Tensor, v0: torch.Tensor, mass, params: Params, dt: float, steps: int,
+             reuse_trees: bool = True):
     """Integrate `steps` KDK steps from (x0, v0); returns (x_T, v_T, a_T).
-    Differentiable in x0 and v0 with one checkpoint (x, v, a) per step."""
+    Differentiable in x0 and v0 with one checkpoint (x, v, a) per step.  With
+    reuse_trees the steps share one tree for the forward pass and one for the
+    backward pass, rebuilt in place (the trees are freed with the graph)."""
     a = short_range_force(x0, mass, params)
+    slots = (_TreeSlot(), _TreeSlot()) if reuse_trees else None
     x, v = x0, v0
     for _ in range(steps):
-        x, v, a = KDKStep.apply(x, v, a, mass, params, dt)
+        x, v, a = KDKStep.apply(x, v, a, mass, params, dt, slots)
     return x, v, a
