@@ -204,3 +204,39 @@ def test_eps_zero_and_coincident_pairs_are_finite():
     ref = oracle_tree(box).list_forces(box.G, box.eps, box.r_cut)
     rms, mx = rel_err(a, ref)
     assert rms <= FP32_RMS and mx <= FP32_MAX
+
+
+def test_lognormal_masses_far_images_and_default_mass():
+    """Masses spanning ~8 decades, G != 1, coordinates many boxes away from
+    [0,1) (wrapped by both sides) and some exactly at 1.0: structure bit-exact,
+    forces and the adjoint within the bounds; mass = None equals explicit 1/n."""
+    rng = np.random.default_rng(4406)
+    base = inputs.config_box(2, n_override=2 ** 15)
+    mass = np.exp(rng.normal(0.0, 3.0, base.n)) / base.n
+    shift = rng.integers(-5, 6, size=base.pos.shape).astype(np.float64)
+    pos = base.pos + shift
+    pos[:7, 0] = 1.0                              # the wrap of 1.0 is 0.0
+    pos[7:11, 1] = -3.0
+    box = inputs.Box("lognormal", pos, mass, 6.674e-3, base.eps, base.r_cut, base.theta)
+    ot = oracle_tree(box)
+    g32 = gpu_tree(box, "fp32")
+    keys, perm = g32.export_keys()
+    okeys = ot.export().keys
+    assert np.array_equal(keys, okeys)
+    ref = ot.list_forces(box.G, box.eps, box.r_cut)
+    rms, mx = rel_err(g32.force().double().cpu().numpy(), ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+    w = inputs.cotangent(box.n, 4407)
+    gref = ot.list_vjp(box.G, box.eps, box.r_cut, w.astype(np.float64))
+    scale = np.sqrt(np.mean(gref ** 2))
+    g = g32.vjp(torch.tensor(w, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(g - gref) <= 1e-4 * np.maximum(np.abs(gref), scale))
+    a2, g2 = g32.force_vjp(torch.tensor(w, device="cuda"))
+    rms, mx = rel_err(a2.double().cpu().numpy(), ref)
+    assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+    # the default mass (1/n) is the same as passing it
+    p = torch.tensor(base.pos, device="cuda")
+    prm = Params(base.G, base.eps, base.r_cut, base.theta, 64, 8, "fp32")
+    t_none = ShortRangeTree(p, None, prm)
+    t_expl = ShortRangeTree(p, torch.full((base.n,), 1.0 / base.n, dtype=torch.float64, device="cuda"), prm)
+    assert torch.equal(t_none.force(), t_expl.force())
