@@ -129,6 +129,21 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass,
  * force/vjp calls write zeros; rebuild outside the graph with tp_build_tree. */
 tp_status tp_rebuild_tree(tp_tree *t, const double *pos, const double *mass, void *stream);
 
+/* Keep the tree's structure, groups and interaction lists from its last
+ * (re)build and refresh everything that depends on positions: the particle
+ * images, the node monopoles (mass, centre of mass, box) and the list entries'
+ * FP32 records.  For integrators that reuse the lists over several short
+ * steps -- the paper's multiple-stepsize scheme evaluates the PP part more
+ * often than the PM part -- and for derivatives with a frozen tree.
+ * pos: device [n][3], the same particles in the same order as the build;
+ * each is taken at the periodic image nearest to its position at the last
+ * build, so displacements must stay below half the box (and, for the lists to
+ * stay complete, well below r_cut: entries are neither added nor removed,
+ * pairs beyond r_cut still contribute exactly zero).  mass: device [n] or NULL
+ * to keep the masses.  No allocation, no synchronisation (graph-capturable).
+ * TP_ERR_INVALID_ARG for a tree in chunked mode (its lists are not kept).   */
+tp_status tp_refit_tree(tp_tree *t, const double *pos, const double *mass, void *stream);
+
 /* Short-range accelerations, Eq. 2, for the lists of t.  acc: device [n][3]
  * in input order; float when the tree's precision is TP_FP32, double when it
  * is TP_FP64.  Overwritten.  Asynchronous.                                  */

@@ -50,6 +50,7 @@ SIGNATURES = {
     "tp_build_tree_batched": ([_V, _V, C.POINTER(_I64), _I32, C.POINTER(TPParams), _V, C.POINTER(_V)],
                               C.c_int),
     "tp_rebuild_tree": ([_V, _V, _V, _V], C.c_int),
+    "tp_refit_tree": ([_V, _V, _V, _V], C.c_int),
     "tp_short_range_force": ([_V, _V, _V], C.c_int),
     "tp_short_range_vjp": ([_V, _V, _V, _V], C.c_int),
     "tp_short_range_force_vjp": ([_V, _V, _V, _V, _V], C.c_int),

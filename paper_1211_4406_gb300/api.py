@@ -113,6 +113,20 @@ class ShortRangeTree:
                                            _stream(stream))
         _lib.check(code, "tp_rebuild_tree")
 
+    def refit(self, pos: torch.Tensor, mass: torch.Tensor | None = None, stream=None) -> None:
+        """Keep structure, groups and lists; refresh images, monopoles and
+        entry records from new positions (same particles, small moves)."""
+        pos = _dev_f64(pos, 3)
+        if pos.shape[0] != self.n:
+            raise ValueError("refit needs the same particle count")
+        if mass is not None:
+            mass = _dev_f64(mass)
+        self._pos, self._mass = pos, mass
+        code = _lib.load().tp_refit_tree(self.handle, C.c_void_p(pos.data_ptr()),
+                                         C.c_void_p(mass.data_ptr()) if mass is not None else None,
+                                         _stream(stream))
+        _lib.check(code, "tp_refit_tree")
+
     def force(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """Short-range accelerations (Eq. 2), [n, 3] in input order."""
         if out is None:

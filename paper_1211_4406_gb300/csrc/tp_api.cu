@@ -446,6 +446,11 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     cudaMemsetAsync(D.status, 0, sizeof(int32_t), s);
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
+    if (D.n > 0) {                            // the refit reference: this build's sorted positions
+        cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(D.ry, D.y, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(D.rz, D.z, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
+    }
     for (int attempt = 0;; attempt++) {
         tp::build_topology(D, t->nch, t->nofs, t->cbnd, t->scan_tmp, s);
         tp::build_group_starts(D, t->flag, t->gofs, t->scan_tmp, s);
@@ -589,6 +594,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.x = B.get<double>(nn); D.y = B.get<double>(nn); D.z = B.get<double>(nn); D.m = B.get<double>(nn);
     D.X = B.get<uint64_t>(nn); D.Y = B.get<uint64_t>(nn); D.Z = B.get<uint64_t>(nn);
     D.P32 = B.get<uint4>(nn);
+    D.rx = B.get<double>(nn); D.ry = B.get<double>(nn); D.rz = B.get<double>(nn);
     t->radix_tmp = B.get<char>(tp::radix_tmp_bytes(n));
     t->scan_tmp = B.get<char>(tp::scan_tmp_bytes());
     t->flag = B.get<uint32_t>(nn); t->gofs = B.get<uint32_t>(nn);
@@ -645,6 +651,21 @@ tp_status tp_rebuild_tree(tp_tree *t, const double *pos, const double *mass, voi
     tp_status e = run_build(t, pos, mass, s, false);
     if (e == TP_OK) e = cuda_status(cudaGetLastError());
     return e;
+}
+
+tp_status tp_refit_tree(tp_tree *t, const double *pos, const double *mass, void *stream)
+{
+    if (!t || t->chunked) return TP_ERR_INVALID_ARG;
+    if (t->n > 0 && !is_device_ptr(pos)) return TP_ERR_INVALID_ARG;
+    if (mass && !is_device_ptr(mass)) return TP_ERR_INVALID_ARG;
+    if (!t->D.gfirst || !t->D.ent) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    t->last = s;
+    if (t->n == 0) return TP_OK;
+    tp::refit_gather(t->D, pos, mass, s);
+    tp::build_moments(t->D, s);
+    tp::refit_records(t->D, s);
+    return cuda_status(cudaGetLastError());
 }
 
 tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)

@@ -71,6 +71,30 @@ __global__ void k_gather(const double *pos, const double *mass, TreeDev T)
     }
 }
 
+// Refit: each particle keeps its sorted slot and takes the periodic image of
+// its new position nearest to the position of the last build (so a node's
+// members stay together when one crosses the box boundary); masses are
+// replaced only when given.
+__global__ void k_refit_gather(const double *pos, const double *mass, TreeDev T)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < T.n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = T.perm[s];
+        const double r[3] = {T.rx[s], T.ry[s], T.rz[s]};
+        double x[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const double d = __dsub_rn(pos[3 * i + c], r[c]);
+            x[c] = __dadd_rn(r[c], __dsub_rn(d, rint(d)));
+        }
+        T.x[s] = x[0]; T.y[s] = x[1]; T.z[s] = x[2];
+        const uint64_t X = tp_fixed64(wrap01(x[0])), Y = tp_fixed64(wrap01(x[1])), Z = tp_fixed64(wrap01(x[2]));
+        T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
+        T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
+        if (mass) T.m[s] = mass[i];
+    }
+}
+
 __global__ void k_init_roots(TreeDev T)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,11 +276,13 @@ __global__ void k_moments(TreeDev T, int L)
         const double my = M > 0.0 ? __ddiv_rn(Sy, M) : cy;
         const double mz = M > 0.0 ? __ddiv_rn(Sz, M) : cz;
         T.comx[i] = mx; T.comy[i] = my; T.comz[i] = mz;
-        T.cX[i] = tp_fixed64(mx); T.cY[i] = tp_fixed64(my); T.cZ[i] = tp_fixed64(mz);
+        // images of the centres (in [0,1) after a build; after a refit they
+        // may lie just outside, hence the wrap)
+        T.cX[i] = tp_fixed64(wrap01(mx)); T.cY[i] = tp_fixed64(wrap01(my)); T.cZ[i] = tp_fixed64(wrap01(mz));
         WNode w;
-        w.cx = (uint32_t)(tp_fixed64(cx) >> 32);
-        w.cy = (uint32_t)(tp_fixed64(cy) >> 32);
-        w.cz = (uint32_t)(tp_fixed64(cz) >> 32);
+        w.cx = (uint32_t)(tp_fixed64(wrap01(cx)) >> 32);
+        w.cy = (uint32_t)(tp_fixed64(wrap01(cy)) >> 32);
+        w.cz = (uint32_t)(tp_fixed64(wrap01(cz)) >> 32);
         w.hx = (uint32_t)(tp_fixed64(fx) >> 32);
         w.hy = (uint32_t)(tp_fixed64(fy) >> 32);
         w.hz = (uint32_t)(tp_fixed64(fz) >> 32);
@@ -390,7 +416,20 @@ void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void 
         TP_LAUNCH(k_level_finish, 1, 32, 0, s, T, L);
         TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs, cb);
     }
+    build_moments(T, s);
+}
+
+// Monopoles of every node, bottom-up by level.
+void build_moments(TreeDev &T, cudaStream_t s)
+{
     for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_moments, kLevelGrid, kBlock, 0, s, T, L);
+}
+
+// New positions for a refit (same particles, same sorted order).
+void refit_gather(TreeDev &T, const double *pos, const double *mass, cudaStream_t s)
+{
+    if (T.n == 0) return;
+    TP_LAUNCH(k_refit_gather, grid_for(T.n, kBlock), kBlock, 0, s, pos, mass, T);
 }
 
 // Group starts and their count (into *T.n_groups).  flag/gofs: [n] u32.

@@ -63,6 +63,7 @@ struct TreeDev {
     double *x, *y, *z, *m;
     uint64_t *X, *Y, *Z;
     uint4 *P32;                       // {X, Y, Z} >> 32 per particle: the walk's 2^-32 grid
+    double *rx, *ry, *rz;             // sorted positions of the last build (refit reference)
     // nodes
     int32_t *first, *count, *child, *nchild, *parent, *skip, *nbx;
     uint8_t *level;
@@ -130,6 +131,9 @@ extern "C" void tp_count_launch(void);
 // Launch helpers implemented in the .cu files.
 namespace tp {
 int num_sms();   // SMs of the current device, queried once per process
+void build_moments(TreeDev &T, cudaStream_t s);
+void refit_gather(TreeDev &T, const double *pos, const double *mass, cudaStream_t s);
+void refit_records(TreeDev &T, cudaStream_t s);
 // Resident blocks per SM of `kernel` at `block` threads (at least 1).
 template <class K>
 int occupancy(K kernel, int block)

@@ -366,6 +366,24 @@ __global__ void k_compact(TreeDev T)
     }
 }
 
+// Refit: the records of the kept lists from the new particle images and
+// node centres of mass, against the same group centres (a warp per group).
+__global__ void k_refit_records(TreeDev T)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    if (*T.n_entries > T.cap_entries) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = w0; g < G; g += nw) {
+        const int64_t e0 = T.loff[g];
+        const int32_t ne = T.lcnt[g];
+        const uint64_t GX = T.gX[g], GY = T.gY[g], GZ = T.gZ[g];
+        const float sc = T.box[T.gbox[g]].scale;
+        for (int32_t k = lane; k < ne; k += 32) T.rec[e0 + k] = entry_record(T, GX, GY, GZ, sc, T.ent[e0 + k]);
+    }
+}
+
 // LPT keys for the persistent work queue: groups in descending order of their
 // pair count n_i * n_j (ties by group index, the sort is stable).
 __global__ void k_lpt_keys(TreeDev T, uint64_t *key, uint32_t *val)
@@ -457,6 +475,12 @@ void walk_expand(TreeDev &T, unsigned long long *counter, void *scan_tmp, cudaSt
     TP_LAUNCH(k_walk_task, num_sms() * bps, kBlock, 0, s, T, counter);
     scan_i32_to_i64(T.icnt2, T.ipos, 0, T.n_items, T.n_entries, scan_tmp, s);
     TP_LAUNCH(k_list_offsets, grid_for(T.cap_groups, 256), 256, 0, s, T);
+}
+
+void refit_records(TreeDev &T, cudaStream_t s)
+{
+    if (T.cap_groups <= 0) return;
+    TP_LAUNCH(k_refit_records, grid_for(32 * T.cap_groups, 256), 256, 0, s, T);
 }
 
 void walk_write(TreeDev &T, cudaStream_t s)
