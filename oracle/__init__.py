@@ -50,12 +50,13 @@ def _load():
     lib.or_g.argtypes = [C.c_double]
     lib.or_gpx.restype = C.c_double
     lib.or_gpx.argtypes = [C.c_double]
-    lib.or_pair.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D]
-    lib.or_pair_jw.argtypes = [_D, C.c_double, _D, C.c_double, C.c_double, C.c_double, _D]
-    lib.or_brute_force.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D]
+    lib.or_pair.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D, C.c_int]
+    lib.or_pair_jw.argtypes = [_D, C.c_double, _D, C.c_double, C.c_double, C.c_double, _D, C.c_int]
+    lib.or_brute_force.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, C.c_int]
     lib.or_brute_force_sample.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double,
-                                          C.c_int64, _I64, _D]
-    lib.or_brute_vjp.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, _D]
+                                          C.c_int64, _I64, _D, C.c_int]
+    lib.or_brute_vjp.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, _D,
+                                 C.c_int]
     lib.or_morton.restype = C.c_uint64
     lib.or_morton.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
     lib.or_key_of.restype = C.c_uint64
@@ -64,12 +65,12 @@ def _load():
     lib.or_build.argtypes = [C.c_int64, _D, _D, C.c_int32, C.c_int32]
     lib.or_lists.restype = C.c_int64
     lib.or_lists.argtypes = [C.c_void_p, C.c_double, C.c_double]
-    lib.or_list_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
-    lib.or_list_vjp.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, _D]
+    lib.or_list_forces.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, C.c_int]
+    lib.or_list_vjp.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D, _D, C.c_int]
     lib.or_list_forces_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
-                                         C.c_double, _D]
+                                         C.c_double, _D, C.c_int]
     lib.or_list_vjp_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
-                                      C.c_double, _D, _D]
+                                      C.c_double, _D, _D, C.c_int]
     lib.or_refresh_moments.argtypes = [C.c_void_p, _D]
     lib.or_sizes.argtypes = [C.c_void_p, _I64]
     lib.or_export_keys.argtypes = [C.c_void_p, _U64, _I64]
@@ -110,45 +111,50 @@ def gpx(xi) -> np.ndarray | float:
     return np.array([lib.or_gpx(float(v)) for v in np.ravel(xi)]).reshape(np.shape(xi))
 
 
-def pair(d, mj, G, eps, rcut) -> np.ndarray:
-    """One term of Eq. 2: acceleration from mass mj at offset d = x_j - x_i."""
+def pair(d, mj, G, eps, rcut, xi_softened=False) -> np.ndarray:
+    """One term of Eq. 2: acceleration from mass mj at offset d = x_j - x_i.
+    xi_softened: take the cutoff argument of Eq. 3 from the softened distance
+    sqrt(r^2 + eps^2) (the paper's kernel form) instead of r; every force and
+    adjoint function below takes the same switch."""
     d = _f64(d)
     out = np.zeros(3)
-    _load().or_pair(_dp(d), float(mj), float(G), float(eps), float(rcut), _dp(out))
+    _load().or_pair(_dp(d), float(mj), float(G), float(eps), float(rcut), _dp(out), int(xi_softened))
     return out
 
 
-def pair_jw(d, mj, w, G, eps, rcut) -> np.ndarray:
+def pair_jw(d, mj, w, G, eps, rcut, xi_softened=False) -> np.ndarray:
     """G mj J(d) w for the Jacobian J of one Eq. 2 term."""
     d, w = _f64(d), _f64(w)
     out = np.zeros(3)
-    _load().or_pair_jw(_dp(d), float(mj), _dp(w), float(G), float(eps), float(rcut), _dp(out))
+    _load().or_pair_jw(_dp(d), float(mj), _dp(w), float(G), float(eps), float(rcut), _dp(out),
+                       int(xi_softened))
     return out
 
 
-def brute_force(pos, mass, G, eps, rcut) -> np.ndarray:
+def brute_force(pos, mass, G, eps, rcut, xi_softened=False) -> np.ndarray:
     """Eq. 2 summed over all pairs (O(N^2), periodic minimum image)."""
     pos, mass = _f64(pos), _f64(mass)
     n = pos.shape[0]
     acc = np.zeros((n, 3))
-    _load().or_brute_force(n, _dp(pos), _dp(mass), G, eps, rcut, _dp(acc))
+    _load().or_brute_force(n, _dp(pos), _dp(mass), G, eps, rcut, _dp(acc), int(xi_softened))
     return acc
 
 
-def brute_force_sample(pos, mass, G, eps, rcut, idx) -> np.ndarray:
+def brute_force_sample(pos, mass, G, eps, rcut, idx, xi_softened=False) -> np.ndarray:
     pos, mass = _f64(pos), _f64(mass)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     acc = np.zeros((idx.size, 3))
     _load().or_brute_force_sample(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, idx.size,
-                                  idx.ctypes.data_as(_I64), _dp(acc))
+                                  idx.ctypes.data_as(_I64), _dp(acc), int(xi_softened))
     return acc
 
 
-def brute_vjp(pos, mass, G, eps, rcut, w) -> np.ndarray:
+def brute_vjp(pos, mass, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
     """dL/dx of L = sum_i w_i . a_i for the direct sum."""
     pos, mass, w = _f64(pos), _f64(mass), _f64(w)
     grad = np.zeros_like(pos)
-    _load().or_brute_vjp(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), _dp(grad))
+    _load().or_brute_vjp(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), _dp(grad),
+                         int(xi_softened))
     return grad
 
 
@@ -217,32 +223,34 @@ class OracleTree:
         self.has_lists = True
         return n_ent
 
-    def list_forces(self, G, eps, rcut) -> np.ndarray:
+    def list_forces(self, G, eps, rcut, xi_softened=False) -> np.ndarray:
         assert self.has_lists
         acc = np.zeros((self.n, 3))
-        _load().or_list_forces(self._h, G, eps, rcut, _dp(acc))
+        _load().or_list_forces(self._h, G, eps, rcut, _dp(acc), int(xi_softened))
         return acc
 
-    def list_vjp(self, G, eps, rcut, w) -> np.ndarray:
+    def list_vjp(self, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
         assert self.has_lists
         w = _f64(w)
         grad = np.zeros((self.n, 3))
-        _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad))
+        _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad), int(xi_softened))
         return grad
 
-    def list_forces_range(self, g0, g1, G, eps, rcut) -> np.ndarray:
+    def list_forces_range(self, g0, g1, G, eps, rcut, xi_softened=False) -> np.ndarray:
         """Forces of groups [g0, g1) only (other rows stay zero)."""
         assert self.has_lists
         acc = np.zeros((self.n, 3))
-        _load().or_list_forces_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(acc))
+        _load().or_list_forces_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(acc),
+                                     int(xi_softened))
         return acc
 
-    def list_vjp_range(self, g0, g1, G, eps, rcut, w) -> np.ndarray:
+    def list_vjp_range(self, g0, g1, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
         """Gradient of sum over groups [g0, g1) of w_i . a_i."""
         assert self.has_lists
         w = _f64(w)
         grad = np.zeros((self.n, 3))
-        _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad))
+        _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad),
+                                  int(xi_softened))
         return grad
 
     def refresh(self, pos) -> None:
@@ -275,11 +283,11 @@ class OracleTree:
                     gcen=gd[:, 0:3], ghalf=gd[:, 3:6], loff=loff, ent=ent)
 
 
-def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64):
+def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64, xi_softened=False):
     """Build, list and sum: the oracle's whole short-range force path."""
     t = OracleTree(pos, mass, n_leaf, n_crit)
     t.lists(rcut, theta)
-    return t.list_forces(G, eps, rcut), t
+    return t.list_forces(G, eps, rcut, xi_softened), t
 
 
 def leapfrog(pos0, vel0, mass, G, eps, rcut, theta, dt, steps, n_leaf=8, n_crit=64,

@@ -27,6 +27,9 @@
  * Readings where the paper is silent (every one is listed in the design notes):
  *   - softening: 1/|r|^3 -> 1/(r^2+eps^2)^{3/2}; the cutoff argument uses the
  *     unsoftened r; pairs with r >= r_cut or r == 0 contribute exactly 0.
+ *     Every force and adjoint function also takes xi_soft: when set, the
+ *     cutoff argument is the softened distance s = sqrt(r^2 + eps^2) instead
+ *     (the paper's kernel form), and pairs with s >= r_cut contribute 0.
  *   - keys: x wrapped to [0,1), quantised to 21 bits, x bit highest in each
  *     interleaved triplet; ties in the sort broken by input index.
  *   - octree: a node splits while count > n_leaf and level < 21; children in
@@ -97,6 +100,7 @@ static inline double minimg(double t) { return t - rint(t); }
 typedef struct {
     double G, eps, rcut, theta;
     double rc2, eps2, th2;
+    int soft;                  /* cutoff argument from the softened distance */
 } or_prm;
 
 static or_prm make_prm(double G, double eps, double rcut, double theta)
@@ -104,19 +108,31 @@ static or_prm make_prm(double G, double eps, double rcut, double theta)
     or_prm p;
     p.G = G; p.eps = eps; p.rcut = rcut; p.theta = theta;
     p.rc2 = rcut * rcut; p.eps2 = eps * eps; p.th2 = theta * theta;
+    p.soft = 0;
+    return p;
+}
+
+static or_prm make_prm_xi(double G, double eps, double rcut, int xi_soft)
+{
+    or_prm p = make_prm(G, eps, rcut, 0.0);
+    p.soft = xi_soft != 0;
     return p;
 }
 
 /* One term of Eq. 2: acceleration of i due to mass mj at minimum-image offset
- * d = x_j - x_i, softened on the 1/r^3 factor, cut by g(2r/r_cut). */
+ * d = x_j - x_i, softened on the 1/r^3 factor, cut by g(2c/r_cut).  The cutoff
+ * argument c is the plain distance r by default; in the softened-xi variant it
+ * is s = sqrt(r^2 + eps^2), the distance the paper's kernel takes from its one
+ * inverse square root per pair (Sec. II-A), so the term vanishes for s >= r_cut. */
 static inline void pair_acc(double dx, double dy, double dz, double mj,
                             const or_prm *P, double *ax, double *ay, double *az)
 {
     double r2 = (dx * dx + dy * dy) + dz * dz;
-    if (!(r2 < P->rc2) || r2 == 0.0) return;
+    if (r2 == 0.0) return;
     double s2 = r2 + P->eps2;
-    double r = sqrt(r2);
-    double g = or_g(2.0 * r / P->rcut);
+    double c2 = P->soft ? s2 : r2;
+    if (!(c2 < P->rc2)) return;
+    double g = or_g(2.0 * sqrt(c2) / P->rcut);
     double fac = P->G * mj * g / (s2 * sqrt(s2));
     *ax += fac * dx;
     *ay += fac * dy;
@@ -124,16 +140,20 @@ static inline void pair_acc(double dx, double dy, double dz, double mj,
 }
 
 /* v = G mj J(d) w with J = phi I + (phi'/r) d d^T the Jacobian of
- * d * phi(|d|), phi = g(xi)/s^3:  phi'/r = (2/r_cut)^2 (g'/xi)/s^3 - 3 g/s^5. */
+ * d * phi(|d|), phi = g(xi)/s^3:  phi'/r = (2/r_cut)^2 (g'/xi)/s^3 - 3 g/s^5.
+ * The same expression holds in the softened-xi variant (xi = 2s/r_cut): there
+ * dphi/dd = (g'(xi) (2/r_cut)/s^4 - 3 g/s^5) d, and (2/r_cut)/s^4 equals
+ * (2/r_cut)^2/(xi s^3). */
 static inline void pair_jw(double dx, double dy, double dz, double mj,
                            const double *w, const or_prm *P, double *v)
 {
     v[0] = v[1] = v[2] = 0.0;
     double r2 = (dx * dx + dy * dy) + dz * dz;
-    if (!(r2 < P->rc2) || r2 == 0.0) return;
+    if (r2 == 0.0) return;
     double s2 = r2 + P->eps2;
-    double r = sqrt(r2);
-    double xi = 2.0 * r / P->rcut;
+    double c2 = P->soft ? s2 : r2;
+    if (!(c2 < P->rc2)) return;
+    double xi = 2.0 * sqrt(c2) / P->rcut;
     double g = or_g(xi);
     double gp = or_gpx(xi);
     double s3 = s2 * sqrt(s2);
@@ -148,17 +168,18 @@ static inline void pair_jw(double dx, double dy, double dz, double mj,
 }
 
 /* Public single-pair helpers (tests pin these against closed forms). */
-void or_pair(const double *d, double mj, double G, double eps, double rcut, double *acc)
+void or_pair(const double *d, double mj, double G, double eps, double rcut, double *acc,
+             int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
     acc[0] = acc[1] = acc[2] = 0.0;
     pair_acc(minimg(d[0]), minimg(d[1]), minimg(d[2]), mj, &P, &acc[0], &acc[1], &acc[2]);
 }
 
 void or_pair_jw(const double *d, double mj, const double *w, double G, double eps,
-                double rcut, double *v)
+                double rcut, double *v, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
     pair_jw(minimg(d[0]), minimg(d[1]), minimg(d[2]), mj, w, &P, v);
 }
 
@@ -174,9 +195,9 @@ static inline double wrap01(double x)
 /* Eq. 2 summed directly over every other particle (the plain definition).  */
 /* ------------------------------------------------------------------------ */
 void or_brute_force(int64_t n, const double *pos, const double *mass, double G,
-                    double eps, double rcut, double *acc)
+                    double eps, double rcut, double *acc, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
     double *w = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     for (int64_t i = 0; i < 3 * n; i++) w[i] = wrap01(pos[i]);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -195,9 +216,9 @@ void or_brute_force(int64_t n, const double *pos, const double *mass, double G,
 /* The same sum for a sample of targets idx[0..ns) only (large boxes). */
 void or_brute_force_sample(int64_t n, const double *pos, const double *mass, double G,
                            double eps, double rcut, int64_t ns, const int64_t *idx,
-                           double *acc)
+                           double *acc, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t s = 0; s < ns; s++) {
         int64_t i = idx[s];
@@ -215,9 +236,9 @@ void or_brute_force_sample(int64_t n, const double *pos, const double *mass, dou
 /* Gradient of L = sum_i w_i . a_i for the direct sum:
  * dL/dx_k = G sum_{j != k} J(x_j - x_k) (m_k w_j - m_j w_k). */
 void or_brute_vjp(int64_t n, const double *pos, const double *mass, double G, double eps,
-                  double rcut, const double *wv, double *grad)
+                  double rcut, const double *wv, double *grad, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
     double *x = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     for (int64_t i = 0; i < 3 * n; i++) x[i] = wrap01(pos[i]);
 #pragma omp parallel for schedule(dynamic, 64)
@@ -608,9 +629,9 @@ static inline void entry_src(const or_tree *t, int64_t e, double *xj, double *mj
 /* Eq. 2 over the lists of groups [g0, g1) (nodes enter as monopoles, the self
  * entry is skipped); acc is written in input order for those groups' particles. */
 void or_list_forces_range(const or_tree *t, int64_t g0, int64_t g1, double G, double eps,
-                          double rcut, double *acc)
+                          double rcut, double *acc, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t g = g0; g < g1; g++) {
         for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
@@ -629,9 +650,10 @@ void or_list_forces_range(const or_tree *t, int64_t g0, int64_t g1, double G, do
     }
 }
 
-void or_list_forces(const or_tree *t, double G, double eps, double rcut, double *acc)
+void or_list_forces(const or_tree *t, double G, double eps, double rcut, double *acc,
+                    int xi_soft)
 {
-    or_list_forces_range(t, 0, t->n_groups, G, eps, rcut, acc);
+    or_list_forces_range(t, 0, t->n_groups, G, eps, rcut, acc, xi_soft);
 }
 
 /* Vector-Jacobian product of or_list_forces for fixed lists: w = dL/da (input
@@ -640,9 +662,9 @@ void or_list_forces(const or_tree *t, double G, double eps, double rcut, double 
  * member p as m_p * sum over the ancestors a of p of c_a / M_a (the derivative
  * of the centre of mass). */
 void or_list_vjp_range(const or_tree *t, int64_t g0, int64_t g1, double G, double eps,
-                       double rcut, const double *wv, double *grad)
+                       double rcut, const double *wv, double *grad, int xi_soft)
 {
-    or_prm P = make_prm(G, eps, rcut, 0.0);
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
     int64_t n = t->n, nn = t->n_nodes;
     double *gs = (double *)calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
     double *cot = (double *)calloc((size_t)(3 * (nn > 0 ? nn : 1)), sizeof(double));
@@ -693,9 +715,9 @@ void or_list_vjp_range(const or_tree *t, int64_t g0, int64_t g1, double G, doubl
 
 /* The gradient of sum_i w_i . a_i for all groups' lists. */
 void or_list_vjp(const or_tree *t, double G, double eps, double rcut, const double *wv,
-                 double *grad)
+                 double *grad, int xi_soft)
 {
-    or_list_vjp_range(t, 0, t->n_groups, G, eps, rcut, wv, grad);
+    or_list_vjp_range(t, 0, t->n_groups, G, eps, rcut, wv, grad, xi_soft);
 }
 
 /* Re-take the monopoles from new positions (input order) with the tree, the
