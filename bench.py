@@ -241,11 +241,12 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     pos = pos_h.to(dev)
     mass = mass_h.to(dev)
     cot = cot_h.to(dev)
-    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
+    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32", xi=args.xi)
     tree = ShortRangeTree(pos, mass, prm)                   # allocating build (setup)
     st = tree.stats()
     wl = workload_config(paper_regime)["workload"]
-    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"{wl}|n{box.n}")   # setup, not timed
+    xkey = "" if args.xi == "plain" else "|xi-softened"
+    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"{wl}|n{box.n}{xkey}")   # setup, not timed
     acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
     grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -348,7 +349,7 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
 
     # ---- plain FP64 GPU path (same lists), for the speedup --------------------
     tree64 = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit,
-                                              box.n_leaf, "fp64"))
+                                              box.n_leaf, "fp64", xi=args.xi))
     acc64 = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
     tree64.force(acc64)
     torch.cuda.synchronize()
@@ -379,6 +380,7 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
                 "ms_per_launch": ms, "flops_per_interaction": flops, "peak_basis": peak_basis}
 
     kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)
+    soft = "true" if args.xi == "softened" else "false"
     meas_ffma = measure_peak("fp32")
     meas_ffma2 = measure_peak("fp32x2")
     meas_dfma = measure_peak("fp64")
@@ -388,12 +390,13 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(paper_regime), tile_autotuned={"forward_particles_per_thread": tile[0],
-                                                          "adjoint_entries_per_thread": tile[1]}),
-        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
+                                                          "adjoint_entries_per_thread": tile[1]},
+                       **({} if args.xi == "plain" else {"xi": "softened: cutoff argument 2 sqrt(r^2+eps^2)/r_cut"})),
+        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true, {soft}>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
                              "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
-        "roofline_forward": roofline(f"k_pair_packed<{tile[0]}>", kp_ms, FLOPS_PER_INTERACTION,
+        "roofline_forward": roofline(f"k_pair_packed<{tile[0]}, {soft}>", kp_ms, FLOPS_PER_INTERACTION,
                                      "FP32 forward pair kernel, separate call"),
-        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false>", kv_ms, VJP_FLOPS_PER_INTERACTION,
+        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false, {soft}>", kv_ms, VJP_FLOPS_PER_INTERACTION,
                                      "FP32 adjoint pair kernel, separate call"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},
@@ -803,6 +806,9 @@ def main():
                          "the 512^3 throughput box (chunked lists); paper-regime-2M: the 2M box with the "
                          "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128); leapfrog-262k: the gradient "
                          "of a 10-step KDK chain (checkpointed adjoint)")
+    ap.add_argument("--xi", default="plain", choices=["plain", "softened"],
+                    help="cutoff argument of Eq. 3 for clustered-2M and paper-regime-2M: plain r (default) "
+                         "or the softened sqrt(r^2+eps^2) of the paper's kernel")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -66,7 +66,7 @@ typedef enum { TP_FP64 = 0, TP_FP32 = 1 } tp_precision;
  *   n_leaf  a tree node holding more than n_leaf particles is split, 1..64
  *   precision  TP_FP32 (pair arithmetic in FP32 on group-relative
  *           coordinates) or TP_FP64 (plain FP64 reference path)
- *   flags   0 or TP_FLAG_CHUNKED                                             */
+ *   flags   0, or TP_FLAG_CHUNKED and/or TP_FLAG_XI_SOFTENED                 */
 typedef struct {
     double G, eps, r_cut, theta;
     int32_t n_crit, n_leaf, precision, flags;
@@ -88,6 +88,19 @@ typedef struct {
  * exercises the mode on small boxes).  Results are the same as with whole
  * lists.  tp_tree_stats reports n_windows > 1 for a chunked tree.           */
 #define TP_FLAG_CHUNKED 1
+
+/* Cutoff argument from the softened distance (the paper's kernel form, Sec.
+ * II-A, which takes one inverse square root per pair for both the softened
+ * 1/s^3 factor and the cutoff argument).  By default a pair at distance r
+ * contributes G m_j d g(2r/r_cut) / (r^2 + eps^2)^{3/2} and vanishes for
+ * r >= r_cut.  With this flag the cutoff argument is 2s/r_cut with
+ * s = sqrt(r^2 + eps^2): a pair contributes G m_j d g(2s/r_cut) / s^3 and
+ * vanishes for s >= r_cut.  The two differ by O(eps^2 / r_cut^2) relative.
+ * The lists (cut at r_cut) are the same.  All boxes of a batched tree must
+ * agree on this flag (else TP_ERR_INVALID_ARG).  tp_short_range_vjp and
+ * tp_short_range_force_vjp differentiate the variant the tree was built
+ * with.  tp_short_range_force_noalloc does not take it.                    */
+#define TP_FLAG_XI_SOFTENED 2
 
 typedef struct tp_tree tp_tree; /* opaque, library-owned */
 
@@ -228,8 +241,9 @@ tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms);
  * every GPU that loads the library holds until the process exits.
  *   pos   device FP64 [n][3], finite; mass device FP64 [n] or NULL (1/n)
  *   n     0 <= n <= TP_NOALLOC_MAX_N, else TP_ERR_INVALID_ARG
- *   p     host; precision must be TP_FP32; theta, n_crit and n_leaf are not
- *         used: the sum runs over all pairs (Eq. 2 with Eq. 3, exact cutoff)
+ *   p     host; precision must be TP_FP32 and flags 0; theta, n_crit and
+ *         n_leaf are not used: the sum runs over all pairs (Eq. 2 with Eq. 3,
+ *         exact cutoff)
  *   acc   device FP32 [n][3], input order, overwritten
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream

@@ -80,6 +80,8 @@ template <class R> struct Arith;
 template <> struct Arith<float> {
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float sqrt(float x) { return sqrt_approx(x); }
+    // sqrt(s2) from the inverse square root already taken: one MUFU per pair
+    static __device__ __forceinline__ float soft_xi(float s2, float ri) { return s2 * ri; }
     static __device__ __forceinline__ float from_fixed(uint64_t a, uint64_t b, float sc)
     {
         return __ll2float_rn((long long)(a - b)) * sc;
@@ -89,6 +91,7 @@ template <> struct Arith<float> {
 template <> struct Arith<double> {
     static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double soft_xi(double s2, double) { return ::sqrt(s2); }
     static __device__ __forceinline__ double from_fixed(uint64_t a, uint64_t b, double sc)
     {
         return __ll2double_rn((long long)(a - b)) * sc;
@@ -211,7 +214,7 @@ __device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPar
 // Two pairs per step, packed, for NI particles per thread: each staged entry
 // pair (A = {x0, x1, y0, y1}, B = {z0, z1, m0, m1}) is loaded once and used
 // for all NI particles.  Eq. 3 as g = u^5 h + v^6 c (exact 0 beyond the cutoff).
-template <int NI>
+template <int NI, bool SOFT>
 __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4 *SB, int st, int npairs, int ns,
                                                   const float *xi, const float *yi, const float *zi, float eps2,
                                                   float *axs, float *ays, float *azs)
@@ -235,11 +238,18 @@ __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4
         for (int k = 0; k < NI; k++) {
             const f2 dx = f2sub(a.x, X[k]), dy = f2sub(a.y, Y[k]), dz = f2sub(b.x, Z[k]);
             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-            float r2a, r2b, s2a, s2b;
-            f2unpack(r2, r2a, r2b);
-            f2unpack(f2add(r2, E2), s2a, s2b);
+            const f2 s2 = f2add(r2, E2);
+            float s2a, s2b;
+            f2unpack(s2, s2a, s2b);
             const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-            const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+            f2 x;                                   // the cutoff argument xi
+            if (SOFT) {
+                x = f2mul(s2, ri);
+            } else {
+                float r2a, r2b;
+                f2unpack(r2, r2a, r2b);
+                x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+            }
             const f2 u = f2relu(f2sub(TWO, x));
             const f2 v = f2relu(f2sub(ONE, x));
             f2 h = f2fma(H3, x, H2);
@@ -328,7 +338,7 @@ __device__ __forceinline__ int64_t next_item(int32_t *queue, int64_t cur, int *s
     return it;
 }
 
-template <class R, bool WRAP>
+template <class R, bool WRAP, bool SOFT>
 __device__ __forceinline__ void force_tile(const JTile<R> &J, int st, int nt, int ns, const IPart<R> &I,
                                            R eps2, R sc, R &ax, R &ay, R &az)
 {
@@ -336,11 +346,13 @@ __device__ __forceinline__ void force_tile(const JTile<R> &J, int st, int nt, in
         R dx, dy, dz;
         pair_offset<R, WRAP>(J, j, I, sc, dx, dy, dz);
         const R r2 = dx * dx + dy * dy + dz * dz;
-        const R ri = Arith<R>::rsqrt(r2 + eps2);
-        const R x = Arith<R>::sqrt(r2);
-        const R g = g_p3m<R>(x, r2);
+        const R s2 = r2 + eps2;
+        const R ri = Arith<R>::rsqrt(s2);
+        const R c2 = SOFT ? s2 : r2;            // xi^2: the plain or the softened |d'|^2
+        const R x = SOFT ? Arith<R>::soft_xi(s2, ri) : Arith<R>::sqrt(r2);
+        const R g = g_p3m<R>(x, c2);
         R f = J.m[j] * g * (ri * ri * ri);
-        f = (r2 < R(4) && r2 > R(0)) ? f : R(0);
+        f = (c2 < R(4) && r2 > R(0)) ? f : R(0);
         ax += f * dx;
         ay += f * dy;
         az += f * dz;
@@ -350,7 +362,7 @@ __device__ __forceinline__ void force_tile(const JTile<R> &J, int st, int nt, in
 // ---------------------------------------------------------------------------
 // Forward: a_i = G k^2 sum_j m_j d' g(|d'|) / (|d'|^2 + (k eps)^2)^{3/2}.
 // ---------------------------------------------------------------------------
-template <class R, bool QUEUE>
+template <class R, bool QUEUE, bool SOFT>
 __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *queue,
                                                    const int32_t *order)
 {
@@ -392,9 +404,9 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
                 if (active) {
                     R ax = 0, ay = 0, az = 0;
                     if (G.wrap) {
-                        force_tile<R, true>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                        force_tile<R, true, SOFT>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
                     } else {
-                        force_tile<R, false>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
+                        force_tile<R, false, SOFT>(J, st, nt, ns, I, eps2, sc, ax, ay, az);
                     }
                     sax += (double)ax; say += (double)ay; saz += (double)az;
                 }
@@ -424,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 // t+1 (loaded one tile earlier into registers) into the other buffer and loads
 // its pair of tile t+2, so one barrier per tile suffices.  Each tile's FP32
 // partial enters an FP64 sum per particle.
-template <int NI>
+template <int NI, bool SOFT>
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
                     float ax[NI], ay[NI], az[NI];
 #pragma unroll
                     for (int k = 0; k < NI; k++) ax[k] = ay[k] = az[k] = 0.f;
-                    force_tile_packed<NI>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+                    force_tile_packed<NI, SOFT>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
 #pragma unroll
                     for (int k = 0; k < NI; k++) { sax[k] += ax[k]; say[k] += ay[k]; saz[k] += az[k]; }
                 }
@@ -551,7 +563,7 @@ __device__ __forceinline__ void g_gpx(R x, R &g, R &gp)
     gp = -(u4 * q) - R(8.0 / 5.0) * (v4 * v) * (x + R(2));
 }
 
-template <class R>
+template <class R, bool SOFT>
 __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, double *gs, double *ncot,
                                                   int32_t *queue, const int32_t *order)
 {
@@ -614,8 +626,9 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
                     }
                     const R wx = iwx[k], wy = iwy[k], wz = iwz[k];
                     const R r2 = dx * dx + dy * dy + dz * dz;
-                    const R ri = Arith<R>::rsqrt(r2 + eps2);
-                    const R x = Arith<R>::sqrt(r2);
+                    const R s2 = r2 + eps2;
+                    const R ri = Arith<R>::rsqrt(s2);
+                    const R x = SOFT ? Arith<R>::soft_xi(s2, ri) : Arith<R>::sqrt(r2);
                     R gv, gp;
                     g_gpx<R>(x, gv, gp);
                     const R ri2 = ri * ri, ri3 = ri2 * ri;
@@ -680,7 +693,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // tiles.  Each thread holds E list entries (a tile is E x 128 entries) and
 // adds their particle-side values before the reduce-scatter, so its cost is
 // shared by E entries.
-template <int E, bool FWD>
+template <int E, bool FWD, bool SOFT>
 __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order, float *acc)
 {
@@ -767,11 +780,13 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                             if (u > 0 && t0 + u * kThreads + warp * 32 >= ne) break;   // warp-uniform: no entries left
                             const f2 dx = f2sub(XJ[u], a.x), dy = f2sub(YJ[u], a.y), dz = f2sub(ZJ[u], b.x);
                             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+                            const f2 s2 = f2add(r2, E2);
                             float r2a, r2b, s2a, s2b;
                             f2unpack(r2, r2a, r2b);
-                            f2unpack(f2add(r2, E2), s2a, s2b);
+                            f2unpack(s2, s2a, s2b);
                             const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-                            const f2 x = f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+                            const f2 x = SOFT ? f2mul(s2, ri)          // the cutoff argument xi
+                                              : f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
                             f2 gv, gp;
                             g_gpx_packed(x, gv, gp);
                             const f2 ri2 = f2mul(ri, ri);
@@ -927,10 +942,106 @@ __global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
     }
 }
 
-template <class R>
-int pair_blocks_per_sm()
+// Launchers, instantiated for the plain (SOFT = false) and the softened
+// (SOFT = true) cutoff argument; the tp:: entry points pick one per tree.
+using tp::num_sms;
+using tp::occupancy;
+
+template <bool SOFT>
+void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
+                        cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles)
 {
-    return tp::occupancy(k_pair<R, true>, kThreads);
+    cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+    static const int bps = occupancy(k_pair<float, true, SOFT>, kThreads);
+    static const int bp1 = occupancy(k_pair_packed<1, SOFT>, kThreads);
+    static const int bp2 = occupancy(k_pair_packed<2, SOFT>, kThreads);
+    static const int bp4 = occupancy(k_pair_packed<4, SOFT>, kThreads);
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    if (ev0) cudaEventRecord(ev0, s);
+    if (fwd_particles == 1) {
+        auto kp = k_pair_packed<1, SOFT>;
+        TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
+    } else if (fwd_particles == 4) {
+        auto kp = k_pair_packed<4, SOFT>;
+        TP_LAUNCH(kp, grid_of(bp4), kThreads, 0, s, T, acc, queue + 1, order);
+    } else {
+        auto kp = k_pair_packed<2, SOFT>;
+        TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
+    }
+    if (ev1) cudaEventRecord(ev1, s);
+    auto k = k_pair<float, true, SOFT>;
+    TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
+}
+
+// The fused adjoint kernel with E entries per thread, with or without the
+// forward sum, on its own occupancy.
+template <int E, bool SOFT>
+void launch_vjp_fused(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
+                      const int32_t *order, int64_t G, float *acc, cudaStream_t s)
+{
+    static const int nbf = occupancy(k_vjp_fused<E, false, SOFT>, kThreads);
+    static const int nbw = occupancy(k_vjp_fused<E, true, SOFT>, kThreads);
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    if (acc) {
+        auto kw = k_vjp_fused<E, true, SOFT>;
+        TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
+    } else {
+        auto kf = k_vjp_fused<E, false, SOFT>;
+        TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, cot, gs, ncot, queue, order, nullptr);
+    }
+}
+
+template <class R, bool SOFT>
+void vjp_pairs_t(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
+                 int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc, int adj_entries)
+{
+    static const int nb = occupancy(k_vjp<R, SOFT>, kThreads);
+    auto grid_of = [&](int per_sm) {
+        int64_t gr = (int64_t)num_sms() * per_sm;
+        return (int)(gr > G ? G : gr);
+    };
+    if (sizeof(R) == 4) {
+        cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
+        if (ev0) cudaEventRecord(ev0, s);
+        if (adj_entries == 2)
+            launch_vjp_fused<2, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
+        else
+            launch_vjp_fused<4, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
+        if (ev1) cudaEventRecord(ev1, s);
+    } else {
+        cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    }
+    auto k = k_vjp<R, SOFT>;
+    TP_LAUNCH(k, grid_of(nb), kThreads, 0, s, T, cot, gs, ncot, queue, order);
+}
+
+template <class R>
+void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
+               int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc = nullptr,
+               int adj_entries = 4)
+{
+    if (G <= 0) return;
+    if (T.xi_soft)
+        vjp_pairs_t<R, true>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc, adj_entries);
+    else
+        vjp_pairs_t<R, false>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc, adj_entries);
+}
+
+// The general FP32 forward kernel for the groups the fused adjoint leaves.
+template <bool SOFT>
+void pair_rest_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
+{
+    static const int bps = occupancy(k_pair<float, true, SOFT>, kThreads);
+    const int64_t gr = (int64_t)num_sms() * bps;
+    cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
+    auto k = k_pair<float, true, SOFT>;
+    TP_LAUNCH(k, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
 }
 
 }  // namespace
@@ -954,37 +1065,23 @@ void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *ord
                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles)
 {
     if (G <= 0) return;
-    cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
-    static const int bps = occupancy(k_pair<float, true>, kThreads);
-    static const int bp1 = occupancy(k_pair_packed<1>, kThreads);
-    static const int bp2 = occupancy(k_pair_packed<2>, kThreads);
-    static const int bp4 = occupancy(k_pair_packed<4>, kThreads);
-    auto grid_of = [&](int per_sm) {
-        int64_t gr = (int64_t)num_sms() * per_sm;
-        return (int)(gr > G ? G : gr);
-    };
-    if (ev0) cudaEventRecord(ev0, s);
-    if (fwd_particles == 1) {
-        auto kp = k_pair_packed<1>;
-        TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
-    } else if (fwd_particles == 4) {
-        auto kp = k_pair_packed<4>;
-        TP_LAUNCH(kp, grid_of(bp4), kThreads, 0, s, T, acc, queue + 1, order);
-    } else {
-        auto kp = k_pair_packed<2>;
-        TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
-    }
-    if (ev1) cudaEventRecord(ev1, s);
-    auto k = k_pair<float, true>;
-    TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
+    if (T.xi_soft)
+        pair_forward_f32_t<true>(T, acc, queue, order, G, s, ev0, ev1, fwd_particles);
+    else
+        pair_forward_f32_t<false>(T, acc, queue, order, G, s, ev0, ev1, fwd_particles);
 }
 
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s)
 {
     if (G <= 0) return;
     int64_t grid = G < (1ll << 30) ? G : (1ll << 30);
-    auto k = k_pair<double, false>;
-    TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, nullptr, nullptr);
+    if (T.xi_soft) {
+        auto k = k_pair<double, false, true>;
+        TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, nullptr, nullptr);
+    } else {
+        auto k = k_pair<double, false, false>;
+        TP_LAUNCH(k, (int)grid, kThreads, 0, s, T, acc, nullptr, nullptr);
+    }
 }
 
 // The adjoint in three stages so that a caller can run the pair stage once
@@ -994,53 +1091,6 @@ void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s)
 {
     cudaMemsetAsync(gs, 0, sizeof(double) * 3 * (size_t)T.n, s);
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
-}
-
-// The fused adjoint kernel with E entries per thread, with or without the
-// forward sum, on its own occupancy.
-template <int E>
-static void launch_vjp_fused(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
-                             const int32_t *order, int64_t G, float *acc, cudaStream_t s)
-{
-    static const int nbf = occupancy(k_vjp_fused<E, false>, kThreads);
-    static const int nbw = occupancy(k_vjp_fused<E, true>, kThreads);
-    auto grid_of = [&](int per_sm) {
-        int64_t gr = (int64_t)num_sms() * per_sm;
-        return (int)(gr > G ? G : gr);
-    };
-    if (acc) {
-        auto kw = k_vjp_fused<E, true>;
-        TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
-    } else {
-        auto kf = k_vjp_fused<E, false>;
-        TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, cot, gs, ncot, queue, order, nullptr);
-    }
-}
-
-template <class R>
-static void vjp_pairs(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
-                      int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, float *acc = nullptr,
-                      int adj_entries = 4)
-{
-    if (G <= 0) return;
-    static const int nb = occupancy(k_vjp<R>, kThreads);
-    auto grid_of = [&](int per_sm) {
-        int64_t gr = (int64_t)num_sms() * per_sm;
-        return (int)(gr > G ? G : gr);
-    };
-    if (sizeof(R) == 4) {
-        cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
-        if (ev0) cudaEventRecord(ev0, s);
-        if (adj_entries == 2)
-            launch_vjp_fused<2>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
-        else
-            launch_vjp_fused<4>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
-        if (ev1) cudaEventRecord(ev1, s);
-    } else {
-        cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-    }
-    auto k = k_vjp<R>;
-    TP_LAUNCH(k, grid_of(nb), kThreads, 0, s, T, cot, gs, ncot, queue, order);
 }
 
 void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s)
@@ -1065,11 +1115,10 @@ void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, d
 {
     if (G <= 0) return;
     vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, acc, adj_entries);
-    static const int bps = occupancy(k_pair<float, true>, kThreads);
-    const int64_t gr = (int64_t)num_sms() * bps;
-    cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
-    auto k = k_pair<float, true>;
-    TP_LAUNCH(k, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
+    if (T.xi_soft)
+        pair_rest_f32_t<true>(T, acc, queue, order, G, s);
+    else
+        pair_rest_f32_t<false>(T, acc, queue, order, G, s);
 }
 
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
