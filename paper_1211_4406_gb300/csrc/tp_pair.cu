@@ -80,8 +80,10 @@ template <class R> struct Arith;
 template <> struct Arith<float> {
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float sqrt(float x) { return sqrt_approx(x); }
-    // sqrt(s2) from the inverse square root already taken: one MUFU per pair
-    static __device__ __forceinline__ float soft_xi(float s2, float ri) { return s2 * ri; }
+    // sqrt(s2) on the MUFU pipe, which has room to spare in these kernels;
+    // s2 * rsqrt(s2) would save the MUFU op but add an FMUL on the FMA pipe,
+    // the one that bounds them (measured 1-3 % slower)
+    static __device__ __forceinline__ float soft_xi(float s2, float) { return sqrt_approx(s2); }
     static __device__ __forceinline__ float from_fixed(uint64_t a, uint64_t b, float sc)
     {
         return __ll2float_rn((long long)(a - b)) * sc;
@@ -237,14 +239,16 @@ __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4
 #pragma unroll
         for (int k = 0; k < NI; k++) {
             const f2 dx = f2sub(a.x, X[k]), dy = f2sub(a.y, Y[k]), dz = f2sub(b.x, Z[k]);
-            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-            const f2 s2 = f2add(r2, E2);
+            // the softened form needs only s^2 (eps^2 folded into the chain);
+            // the self term vanishes through d = 0 in either form
+            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, SOFT ? f2fma(dx, dx, E2) : f2mul(dx, dx)));
+            const f2 s2 = SOFT ? r2 : f2add(r2, E2);
             float s2a, s2b;
             f2unpack(s2, s2a, s2b);
             const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
             f2 x;                                   // the cutoff argument xi
             if (SOFT) {
-                x = f2mul(s2, ri);
+                x = f2pack(sqrt_approx(s2a), sqrt_approx(s2b));
             } else {
                 float r2a, r2b;
                 f2unpack(r2, r2a, r2b);
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                             f2unpack(r2, r2a, r2b);
                             f2unpack(s2, s2a, s2b);
                             const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
-                            const f2 x = SOFT ? f2mul(s2, ri)          // the cutoff argument xi
+                            const f2 x = SOFT ? f2pack(sqrt_approx(s2a), sqrt_approx(s2b))   // xi
                                               : f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
                             f2 gv, gp;
                             g_gpx_packed(x, gv, gp);
