@@ -1,0 +1,132 @@
+"""CPU FP64 oracle of the long-range (PM) half of TreePM -- TEST INFRASTRUCTURE
+ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this module; the CUDA library shares no code with
+it.
+
+It follows the PM cycle of Sec. II (Ishiyama, Nitadori & Makino, SC12) step by
+step, in plain numpy over an N^3 periodic mesh of the unit box (spacing
+h = 1/N, mesh point (i, j, k) at (i h, j h, k h)):
+
+  1. assign      mass density by the triangular-shaped cloud (TSC): each
+                 particle reaches the 3 x 3 x 3 mesh points around its nearest
+                 one (27 points)
+  2. potential   FFT of the density, product with the Green's function of the
+                 long-range force, inverse FFT
+  3. gradient    four-point finite difference of the potential on the mesh
+  4. interpolate the mesh force back to each particle with the same TSC weights
+
+The long-range force is what the PP cutoff g_P3M of Eq. 3 leaves out: the
+force between two S2 clouds of radius r_cut/2 (the density of Eq. 1), whose
+Fourier transform is S(k)^2 times Newton's.  Readings where the paper is
+silent (each is listed in the design notes):
+  - Green's function: -4 pi G S(k)^2 / k^2, divided by the square of the TSC
+    window W(k) = prod_axes sinc(k_a h / 2)^3 (once for the assignment, once
+    for the interpolation); zero for k = 0 (the mean density is removed, as in
+    a periodic Ewald sum).
+  - the four-point difference is (8 (P[i+1] - P[i-1]) - (P[i+2] - P[i-2])) / 12h.
+  - the softening eps does not enter the PM part (eps << r_cut).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def s2_transform(x):
+    """Fourier transform of the unit-mass S2 density of Eq. 1 at x = k r_cut/2:
+    12 (2 - 2 cos x - x sin x) / x^4.  Below x = 0.3 the bracket (about
+    x^4 / 12) cancels in the closed form, so the Taylor series to x^8 is used
+    there (its first omitted term is below 1e-14)."""
+    x = np.asarray(x, dtype=np.float64)
+    with np.errstate(all="ignore"):
+        closed = 12.0 * (2.0 - 2.0 * np.cos(x) - x * np.sin(x)) / x ** 4
+    x2 = x * x
+    series = 1.0 + x2 * (-1.0 / 15.0 + x2 * (1.0 / 560.0 + x2 * (-1.0 / 37800.0 + x2 / 3991680.0)))
+    return np.where(np.abs(x) < 0.3, series, closed)
+
+
+def tsc_weights(d):
+    """TSC weights of the mesh points at offsets -1, 0, +1 from the nearest
+    one, for a particle d (in mesh units, |d| <= 1/2) away from it."""
+    d = np.asarray(d, dtype=np.float64)
+    return np.stack([0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2])
+
+
+def _stencil(pos, n_mesh):
+    """Nearest mesh point (integer, per axis) and the TSC weights [3 axes][3 offsets][n]."""
+    u = (np.asarray(pos, dtype=np.float64) % 1.0) * n_mesh
+    i0 = np.rint(u).astype(np.int64)
+    d = u - i0
+    return i0, [tsc_weights(d[:, a]) for a in range(3)]
+
+
+def assign(pos, mass, n_mesh):
+    """Step 1: mass density on the mesh (mass per cell / h^3)."""
+    i0, w = _stencil(pos, n_mesh)
+    mass = np.asarray(mass, dtype=np.float64)
+    rho = np.zeros((n_mesh,) * 3)
+    h3 = (1.0 / n_mesh) ** 3
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                idx = ((i0[:, 0] + a - 1) % n_mesh, (i0[:, 1] + b - 1) % n_mesh,
+                       (i0[:, 2] + c - 1) % n_mesh)
+                np.add.at(rho, idx, mass * w[0][a] * w[1][b] * w[2][c] / h3)
+    return rho
+
+
+def green(n_mesh, r_cut, G):
+    """Step 2's Green's function on the FFT grid (numpy fftn frequency order)."""
+    h = 1.0 / n_mesh
+    k1 = 2.0 * np.pi * np.fft.fftfreq(n_mesh, d=h)
+    kx, ky, kz = np.meshgrid(k1, k1, k1, indexing="ij")
+    k2 = kx * kx + ky * ky + kz * kz
+    s = s2_transform(np.sqrt(k2) * (0.5 * r_cut))
+
+    def sinc(t):
+        with np.errstate(all="ignore"):
+            return np.where(t == 0.0, 1.0, np.sin(t) / np.where(t == 0.0, 1.0, t))
+
+    window = (sinc(0.5 * h * kx) * sinc(0.5 * h * ky) * sinc(0.5 * h * kz)) ** 3
+    with np.errstate(all="ignore"):
+        gk = np.where(k2 > 0.0, -4.0 * np.pi * G * s * s / (k2 * window * window), 0.0)
+    return gk
+
+
+def potential(rho, gk):
+    """Step 2: the long-range potential on the mesh."""
+    return np.real(np.fft.ifftn(gk * np.fft.fftn(rho)))
+
+
+def gradient(phi):
+    """Step 3: the mesh acceleration -grad(phi) by the four-point difference."""
+    n_mesh = phi.shape[0]
+    h = 1.0 / n_mesh
+    out = []
+    for a in range(3):
+        d = (8.0 * (np.roll(phi, -1, a) - np.roll(phi, 1, a))
+             - (np.roll(phi, -2, a) - np.roll(phi, 2, a))) / (12.0 * h)
+        out.append(-d)
+    return out
+
+
+def interpolate(pos, amesh):
+    """Step 4: the mesh acceleration at each particle, TSC weights."""
+    n_mesh = amesh[0].shape[0]
+    i0, w = _stencil(pos, n_mesh)
+    acc = np.zeros((i0.shape[0], 3))
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                idx = ((i0[:, 0] + a - 1) % n_mesh, (i0[:, 1] + b - 1) % n_mesh,
+                       (i0[:, 2] + c - 1) % n_mesh)
+                wt = w[0][a] * w[1][b] * w[2][c]
+                for q in range(3):
+                    acc[:, q] += wt * amesh[q][idx]
+    return acc
+
+
+def pm_forces(pos, mass, n_mesh, r_cut, G):
+    """The whole PM cycle: long-range accelerations of every particle."""
+    rho = assign(pos, mass, n_mesh)
+    phi = potential(rho, green(n_mesh, r_cut, G))
+    return interpolate(pos, gradient(phi))
