@@ -253,6 +253,55 @@ tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms);
 tp_status tp_short_range_force_noalloc(const double *pos, const double *mass, int64_t n,
                                        const tp_params *p, float *acc, void *stream);
 
+/* ------------------------------------------------------------------------
+ * The long-range (PM) half of TreePM (Sec. II).  Each tp_pm_force call runs
+ * the PM cycle on one GPU over an n_mesh^3 periodic mesh of the unit box
+ * (mesh point (i,j,k) at (i,j,k)/n_mesh):
+ *   1. TSC assignment of the masses to the 27 mesh points around each
+ *      particle's nearest one;
+ *   2. FFT, product with the Green's function of the long-range force, and
+ *      the inverse FFT, which give the potential on the mesh;
+ *   3. -grad(phi) on the mesh by the four-point finite difference;
+ *   4. TSC interpolation of that mesh force to each particle.
+ * The long-range pair force is the force between two S2 clouds of radius
+ * r_cut/2 (Eq. 1), the complement of the cutoff g_P3M of Eq. 3, so that
+ * tp_short_range_force + tp_pm_force with the same r_cut and G is the whole
+ * TreePM acceleration.  Green's function: -4 pi G S(k)^2 / k^2, with
+ * S(x) = 12 (2 - 2 cos x - x sin x) / x^4 at x = |k| r_cut / 2.  It is
+ * divided by the square of the TSC window prod_a sinc(k_a h/2)^3 (for the
+ * assignment and the interpolation) and is 0 at k = 0, which removes the
+ * mean density as a periodic Ewald sum does.  The mesh, the FFTs (cuFFT) and
+ * the interpolation are FP32.  The paper takes r_cut = 3 / n_mesh (three
+ * mesh spacings).  eps does not enter the PM part.                          */
+typedef struct tp_pm tp_pm; /* opaque, library-owned */
+
+/* Allocates the mesh (36 bytes per cell: the FP32 mass/potential mesh, the
+ * FP32 force mesh as float4, the half spectrum and the Green's table), the
+ * two cuFFT plans and the Green's table (computed on `stream`, which is
+ * synchronised once).
+ *   n_mesh  even, 8 <= n_mesh <= 1024
+ *   r_cut   0 < r_cut < 0.5, the same as the short-range half's
+ *   G       finite
+ * Errors: TP_ERR_INVALID_ARG, TP_ERR_NO_DEVICE, TP_ERR_OOM, TP_ERR_CUDA.     */
+tp_status tp_pm_create(int32_t n_mesh, double r_cut, double G, void *stream, tp_pm **out);
+
+/* Long-range accelerations of n particles.
+ *   pos   device FP64 [n][3], any finite values (wrapped into the box)
+ *   mass  device FP64 [n] or NULL (every mass 1/n)
+ *   acc   device FP32 [n][3], input order; overwritten, or added to when
+ *         accumulate != 0 (e.g. onto tp_short_range_force's output)
+ * Asynchronous on `stream`.  One tp_pm serves one stream at a time.         */
+tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
+                      int32_t accumulate, void *stream);
+
+/* Copies a mesh of the last tp_pm_force call to host memory (synchronous):
+ * which = 0 the potential [n_mesh^3], which = 1 the mesh acceleration
+ * -grad(phi) [n_mesh^3][3]; layout (i n_mesh + j) n_mesh + k.               */
+tp_status tp_pm_export_mesh(tp_pm *pm, int32_t which, float *host);
+
+/* Releases the mesh and plans (synchronises the device).  NULL is a no-op.  */
+tp_status tp_pm_free(tp_pm *pm);
+
 /* Leapfrog helpers for the kick-drift-kick integrator (y += a * x):
  * y: device double [n]; x: device [n], float when x_is_f32 else double.     */
 tp_status tp_axpy(double *y, const void *x, int32_t x_is_f32, double a, int64_t n,

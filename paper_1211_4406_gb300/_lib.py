@@ -70,6 +70,10 @@ SIGNATURES = {
     "tp_measure_peak": ([_I32, C.POINTER(_D), _V], C.c_int),
     "tp_short_range_force_noalloc": ([_V, _V, _I64, C.POINTER(TPParams), _V, _V], C.c_int),
     "tp_launch_count": ([], _I64),
+    "tp_pm_create": ([_I32, _D, _D, _V, C.POINTER(_V)], C.c_int),
+    "tp_pm_force": ([_V, _V, _V, _I64, _V, _I32, _V], C.c_int),
+    "tp_pm_export_mesh": ([_V, _I32, _V], C.c_int),
+    "tp_pm_free": ([_V], C.c_int),
     "tp_status_string": ([C.c_int], C.c_char_p),
 }
 

@@ -228,6 +228,65 @@ class ShortRangeTree:
         return off, ent[:st["n_entries"]]
 
 
+class PMSolver:
+    """The long-range (PM) half (Sec. II): an n_mesh^3 periodic mesh with its
+    Green's function and FFT plans, owned by the library.  force() runs the PM
+    cycle (TSC assignment, FFT, Green's function, four-point difference, TSC
+    interpolation); with the same r_cut and G it completes ShortRangeTree's
+    short-range force to the whole TreePM acceleration."""
+
+    def __init__(self, n_mesh: int, r_cut: float, G: float = 1.0, stream=None):
+        h = C.c_void_p()
+        _lib.check(_lib.load().tp_pm_create(int(n_mesh), float(r_cut), float(G), _stream(stream), C.byref(h)),
+                   "tp_pm_create")
+        self._h = h
+        self.n_mesh, self.r_cut, self.G = int(n_mesh), float(r_cut), float(G)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.load().tp_pm_free(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def force(self, pos: torch.Tensor, mass: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              accumulate: bool = False, stream=None) -> torch.Tensor:
+        """Long-range accelerations [n, 3] (FP32, input order); added to `out`
+        when accumulate is set (e.g. onto the short-range force)."""
+        if self._h is None:
+            raise RuntimeError("PM solver has been freed")
+        pos = _dev_f64(pos, 3)
+        if mass is not None:
+            mass = _dev_f64(mass)
+        n = int(pos.shape[0])
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate needs out")
+            out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (n, 3):
+            raise ValueError("out must be a contiguous float32 [n,3] tensor")
+        code = _lib.load().tp_pm_force(self._h, C.c_void_p(pos.data_ptr()),
+                                       C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
+                                       C.c_void_p(out.data_ptr()), int(bool(accumulate)), _stream(stream))
+        _lib.check(code, "tp_pm_force")
+        return out
+
+    def export_mesh(self, which: str = "potential") -> np.ndarray:
+        """The potential [N,N,N] or the mesh acceleration [N,N,N,3] of the last
+        force() call (synchronous copy)."""
+        N = self.n_mesh
+        idx = {"potential": 0, "acceleration": 1}[which]
+        out = np.zeros((N, N, N) if idx == 0 else (N, N, N, 3), dtype=np.float32)
+        _lib.check(_lib.load().tp_pm_export_mesh(self._h, idx, out.ctypes.data_as(C.c_void_p)),
+                   "tp_pm_export_mesh")
+        return out
+
+
 def short_range_force(pos: torch.Tensor, mass: torch.Tensor | None, params: Params,
                       stream=None) -> torch.Tensor:
     """Build and evaluate in one call (the tree is freed afterwards)."""

@@ -69,8 +69,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for l in logs:
             sys.stderr.write(l)
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], capture_output=True,
-                       text=True)
+    # cuFFT (the PM half's transforms) from the toolkit that compiles the
+    # library, found at run time through the rpath
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, f"-L{cuda_lib}",
+                        "-lcufft", "-Xlinker", f"-rpath={cuda_lib}"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

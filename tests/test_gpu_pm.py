@@ -1,0 +1,114 @@
+"""GPU parity of the long-range (PM) half against the PM oracle (Sec. II's PM
+cycle), through the C-ABI.
+
+The GPU mesh, FFTs and interpolation are FP32, the oracle FP64.  Bounds,
+relative to the rms of the reference: potential and mesh acceleration rms
+<= 1e-5; particle accelerations rms <= 1e-5 and max <= 1e-3 (with the same
+1e-6 x median guard as the short-range tests).  Full-size case: the
+clustered 2M box on its 128^3 mesh (r_cut = 3/128, three mesh spacings).
+The PM + PP total through the library meets the oracle's Ewald bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from ewald_ref import ewald
+from oracle import pm as opm
+from paper_1211_4406_gb300 import inputs
+from paper_1211_4406_gb300._lib import TreeSRError
+from paper_1211_4406_gb300.api import Params, PMSolver, ShortRangeTree
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, ref):
+    nr = np.linalg.norm(ref, axis=1)
+    e = np.linalg.norm(a - ref, axis=1) / np.maximum(nr, 1e-6 * np.median(nr))
+    return float(np.sqrt(np.mean(e ** 2))), float(e.max())
+
+
+def mesh_rel(a, ref):
+    return float(np.sqrt(np.mean((a - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
+
+
+def cases():
+    rng = np.random.default_rng(11)
+    out = []
+    pos = rng.random((500, 3))
+    pos[:5] += np.array([3.0, -2.0, 7.0])          # far images
+    pos[5] = [1.0, 0.0, 0.999999999]               # exactly on the boundary
+    out.append(("random500-mesh16", pos, rng.random(500) + 0.5, 16, 1.3))
+    box = inputs.config_box(1)                     # uniform 32^3
+    out.append(("uniform32k-mesh32", box.pos, None, 32, 1.0))
+    box = inputs.config_box(2, n_override=2 ** 15)
+    out.append(("clustered32k-mesh32", box.pos, box.mass * np.linspace(0.5, 1.5, box.n), 32, 1.0))
+    box = inputs.config_box(2, n_override=2 ** 15)
+    out.append(("clustered32k-mesh24", box.pos, None, 24, 0.7))
+    return out
+
+
+@pytest.mark.parametrize("name,pos,mass,n_mesh,G", cases(), ids=[c[0] for c in cases()])
+def test_pm_matches_oracle(name, pos, mass, n_mesh, G):
+    rc = 3.0 / n_mesh
+    n = pos.shape[0]
+    m_ref = np.full(n, 1.0 / n) if mass is None else mass
+    rho = opm.assign(pos, m_ref, n_mesh)
+    phi = opm.potential(rho, opm.green(n_mesh, rc, G))
+    amesh = opm.gradient(phi)
+    ref = opm.interpolate(pos, amesh)
+    solver = PMSolver(n_mesh, rc, G)
+    p = torch.tensor(pos, device="cuda")
+    m = None if mass is None else torch.tensor(mass, device="cuda")
+    acc = solver.force(p, m).double().cpu().numpy()
+    assert mesh_rel(solver.export_mesh("potential"), phi) <= 1e-5
+    assert mesh_rel(solver.export_mesh("acceleration"), np.stack(amesh, axis=-1)) <= 1e-5
+    rms, mx = rel_err(acc, ref)
+    assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+    # accumulate adds onto what is there
+    base = torch.full((n, 3), 0.25, dtype=torch.float32, device="cuda")
+    solver.force(p, m, out=base, accumulate=True)
+    assert np.abs(base.double().cpu().numpy() - 0.25 - acc).max() <= 1e-6 * max(np.abs(acc).max(), 1.0)
+    solver.close()
+
+
+def test_clustered_2M_full_size():
+    box = inputs.config_box(2)
+    n_mesh, rc = 128, box.r_cut
+    assert abs(rc - 3.0 / n_mesh) < 1e-15
+    ref = opm.pm_forces(box.pos, box.mass, n_mesh, rc, box.G)
+    solver = PMSolver(n_mesh, rc, box.G)
+    acc = solver.force(torch.tensor(box.pos, device="cuda"), torch.tensor(box.mass, device="cuda"))
+    rms, mx = rel_err(acc.double().cpu().numpy(), ref)
+    assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+    solver.close()
+
+
+def test_treepm_total_through_the_library_matches_ewald():
+    rng = np.random.default_rng(1)
+    n, n_mesh, G = 64, 32, 1.0
+    pos = rng.random((n, 3))
+    mass = np.full(n, 1.0 / n)
+    rc = 3.0 / n_mesh
+    p, m = torch.tensor(pos, device="cuda"), torch.tensor(mass, device="cuda")
+    tree = ShortRangeTree(p, m, Params(G, 0.0, rc, 0.0, 8, 8, "fp32"))
+    acc = tree.force()
+    PMSolver(n_mesh, rc, G).force(p, m, out=acc, accumulate=True)
+    ref = ewald(pos, mass, G)
+    e = np.linalg.norm(acc.double().cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert np.sqrt(np.mean(e ** 2)) <= 3e-2 and e.max() <= 0.1
+    total_oracle = oracle.brute_force(pos, mass, G, 0.0, rc) + opm.pm_forces(pos, mass, n_mesh, rc, G)
+    rms, _ = rel_err(acc.double().cpu().numpy(), total_oracle)
+    assert rms <= 1e-5, rms
+    tree.close()
+
+
+def test_pm_errors_and_empty():
+    with pytest.raises(TreeSRError):
+        PMSolver(15, 0.2)                      # odd mesh
+    with pytest.raises(TreeSRError):
+        PMSolver(16, 0.5)                      # r_cut must be < 1/2
+    s = PMSolver(16, 3 / 16)
+    empty = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    assert s.force(empty).shape == (0, 3)
+    s.close()
