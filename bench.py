@@ -788,8 +788,100 @@ def run_leapfrog(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_treepm(args, rank, world, local_rank):
+    """The whole TreePM acceleration of the clustered 2M box: rebuild the
+    tree, the FP32 short-range force (Eq. 2 with Eq. 3, r_cut = 3/128), and
+    the long-range PM force on the 128^3 mesh (three mesh spacings per r_cut,
+    as the paper sets it) added onto it."""
+    import torch
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, PMSolver, ShortRangeTree, launch_count
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    box = inputs.config_box(CONFIG_K)
+    n_mesh = 128
+    pos_h = torch.tensor(box.pos).pin_memory()
+    pos = pos_h.to(dev)
+    mass = torch.tensor(box.mass, device=dev)
+    tree = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32"))
+    pm = PMSolver(n_mesh, box.r_cut, box.G)
+    acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
+    acc_h = torch.empty((box.n, 3), dtype=torch.float32).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    phases = []
+
+    def step(record=False):
+        e = [ev() for _ in range(4)] if record else None
+        if record:
+            e[0].record(stream)
+        tree.rebuild(pos, mass)
+        if record:
+            e[1].record(stream)
+        tree.force(acc)
+        if record:
+            e[2].record(stream)
+        pm.force(pos, mass, out=acc, accumulate=True)
+        if record:
+            e[3].record(stream)
+            phases.append(e)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    clocks.mark()
+    l0 = launch_count()
+    ms = _timed_replays(lambda: step(True), args.steps, flush, stream)
+    launches = launch_count() - l0
+    clk = clocks.stop()
+    pm_only = _timed_replays(lambda: pm.force(pos, mass, out=acc), args.steps, flush, stream)
+    e2e_ms = _timed_replays(lambda: (pos.copy_(pos_h, non_blocking=True), step(), acc_h.copy_(acc, non_blocking=True)),
+                            max(2, args.steps // 2), flush, stream)
+    tot_ms, tot_e2e = max_over_ranks([sum(ms), sum(e2e_ms)], device=dev)
+    value = whole_job_rate(world, box.n, args.steps, tot_ms)
+    st = tree.stats()
+    if rank != 0:
+        return
+    mean = lambda xs: sum(xs) / len(xs)
+    ph = {"build": mean([e[0].elapsed_time(e[1]) for e in phases]),
+          "short_range_force": mean([e[1].elapsed_time(e[2]) for e in phases]),
+          "pm_force": mean([e[2].elapsed_time(e[3]) for e in phases]),
+          "pm_force_alone_l2_flushed": mean(pm_only)}
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    ach = FLOPS_PER_INTERACTION * st["n_interactions"] / (ph["short_range_force"] * 1e-3)
+    line = {
+        "metric": "particles/s (whole TreePM acceleration: rebuild + FP32 short-range + PM on 128^3, clustered 2M box)",
+        "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "treepm-2M", "n": box.n, "halos": 2000, "r_cut": "3/128", "eps": "1/6400",
+                   "theta": 0.5, "n_crit": box.n_crit, "n_mesh": n_mesh,
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / fp32_peak, "traffic": None,
+                     "kernel": "short-range force call (k_pair_packed + general kernel), the largest share",
+                     "flops_per_interaction": FLOPS_PER_INTERACTION},
+        "phases_ms": ph,
+        "e2e": {"value": whole_job_rate(world, box.n, len(e2e_ms), tot_e2e), "unit": "particles/s",
+                "h2d_bytes_per_step": box.n * 24, "d2h_bytes_per_step": box.n * 12,
+                "ms_per_step": tot_e2e / len(e2e_ms)},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    pm.close()
+    tree.close()
+
+
 WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64,
-             "clustered-134M": run_large, "paper-regime-2M": run_paper_regime, "leapfrog-262k": run_leapfrog}
+             "clustered-134M": run_large, "paper-regime-2M": run_paper_regime, "leapfrog-262k": run_leapfrog,
+             "treepm-2M": run_treepm}
 
 
 def main():
@@ -805,7 +897,8 @@ def main():
                          "the plain FP64 path on the uniform 32^3 box; clustered-134M: "
                          "the 512^3 throughput box (chunked lists); paper-regime-2M: the 2M box with the "
                          "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128); leapfrog-262k: the gradient "
-                         "of a 10-step KDK chain (checkpointed adjoint)")
+                         "of a 10-step KDK chain (checkpointed adjoint); treepm-2M: the whole TreePM "
+                         "acceleration (rebuild + short-range + PM on 128^3)")
     ap.add_argument("--xi", default="plain", choices=["plain", "softened"],
                     help="cutoff argument of Eq. 3 for clustered-2M and paper-regime-2M: plain r (default) "
                          "or the softened sqrt(r^2+eps^2) of the paper's kernel")

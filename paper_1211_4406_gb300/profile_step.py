@@ -102,7 +102,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=128 ** 3)
     ap.add_argument("--steps", type=int, default=1)
-    ap.add_argument("--what", default="step", choices=["step", "force", "vjp", "fused", "all"])
+    ap.add_argument("--what", default="step", choices=["step", "force", "vjp", "fused", "all", "treepm"],
+                    help="treepm: rebuild + short-range force + PM force on the mesh of r_cut = 3 spacings")
     ap.add_argument("--record-traffic", metavar="CSV")
     args = ap.parse_args()
     if args.record_traffic:
@@ -110,7 +111,7 @@ def main():
         return
     import torch
 
-    from .api import Params, ShortRangeTree
+    from .api import Params, PMSolver, ShortRangeTree
     _build.build()
     box = inputs.config_box(2, n_override=args.n)
     pos = torch.tensor(box.pos, device="cuda")
@@ -120,7 +121,13 @@ def main():
                                          box.n_leaf, "fp32"))
     acc = torch.empty((box.n, 3), dtype=torch.float32, device="cuda")
     grad = torch.empty((box.n, 3), dtype=torch.float64, device="cuda")
+    pm = PMSolver(int(round(3.0 / box.r_cut)), box.r_cut, box.G) if args.what == "treepm" else None
     for _ in range(args.steps):
+        if pm is not None:
+            t.rebuild(pos, mass)
+            t.force(acc)
+            pm.force(pos, mass, out=acc, accumulate=True)
+            continue
         if args.what in ("step", "fused", "all"):
             t.rebuild(pos, mass)
         if args.what in ("step", "force", "all"):
