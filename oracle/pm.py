@@ -130,3 +130,58 @@ def pm_forces(pos, mass, n_mesh, r_cut, G):
     rho = assign(pos, mass, n_mesh)
     phi = potential(rho, green(n_mesh, r_cut, G))
     return interpolate(pos, gradient(phi))
+
+
+def tsc_weight_derivatives(d):
+    """d/dd of tsc_weights (offsets -1, 0, +1); they sum to zero."""
+    d = np.asarray(d, dtype=np.float64)
+    return np.stack([-(0.5 - d), -2.0 * d, 0.5 + d])
+
+
+def divergence(field):
+    """Sum over axes of the four-point difference of field[a] along axis a
+    (the transpose of gradient() up to sign)."""
+    n_mesh = field[0].shape[0]
+    h = 1.0 / n_mesh
+    out = np.zeros_like(field[0])
+    for a in range(3):
+        f = field[a]
+        out += (8.0 * (np.roll(f, -1, a) - np.roll(f, 1, a))
+                - (np.roll(f, -2, a) - np.roll(f, 2, a))) / (12.0 * h)
+    return out
+
+
+def pm_vjp(pos, mass, n_mesh, r_cut, G, w):
+    """dL/dx of L = sum_i w_i . a_i over the PM cycle (the adjoint of
+    pm_forces).  With U_a = the TSC assignment of the cotangent component
+    w_a, A = -grad(phi) the mesh force and B = K div(U), K the potential
+    solve of step 2 (symmetric) and div the four-point divergence
+    (the four-point difference is antisymmetric):
+        dL/dx_k = sum_c grad W_k(c) [w_k . A(c) + (m_k / h^3) B(c)],
+    grad W_k the derivative of particle k's TSC weight at mesh point c."""
+    pos = np.asarray(pos, dtype=np.float64)
+    mass = np.asarray(mass, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    h3 = (1.0 / n_mesh) ** 3
+    gk = green(n_mesh, r_cut, G)
+    amesh = gradient(potential(assign(pos, mass, n_mesh), gk))
+    # U: each cotangent component assigned like a mass (assign() divides by h^3)
+    umesh = [assign(pos, w[:, a], n_mesh) * h3 for a in range(3)]
+    bmesh = potential(divergence(umesh), gk)
+    u = (pos % 1.0) * n_mesh
+    i0 = np.rint(u).astype(np.int64)
+    d = u - i0
+    W = [tsc_weights(d[:, a]) for a in range(3)]
+    dW = [tsc_weight_derivatives(d[:, a]) * n_mesh for a in range(3)]
+    grad = np.zeros_like(pos)
+    for a in range(3):
+        for b in range(3):
+            for c in range(3):
+                idx = ((i0[:, 0] + a - 1) % n_mesh, (i0[:, 1] + b - 1) % n_mesh,
+                       (i0[:, 2] + c - 1) % n_mesh)
+                s = (w[:, 0] * amesh[0][idx] + w[:, 1] * amesh[1][idx] + w[:, 2] * amesh[2][idx]
+                     + mass / h3 * bmesh[idx])
+                grad[:, 0] += dW[0][a] * W[1][b] * W[2][c] * s
+                grad[:, 1] += W[0][a] * dW[1][b] * W[2][c] * s
+                grad[:, 2] += W[0][a] * W[1][b] * dW[2][c] * s
+    return grad

@@ -122,3 +122,29 @@ def test_treepm_total_matches_ewald():
     ref = ewald(pos, mass, G)
     e = np.linalg.norm(total - ref, axis=1) / np.linalg.norm(ref, axis=1)
     assert np.sqrt(np.mean(e ** 2)) <= 3e-2 and e.max() <= 0.1, (np.sqrt(np.mean(e ** 2)), e.max())
+
+
+def test_pm_vjp_matches_central_differences():
+    """The PM adjoint against central differences of the PM forward (the TSC
+    weights are C^1, so the differences converge everywhere, also across a
+    change of nearest mesh point)."""
+    rng = np.random.default_rng(4)
+    n, n_mesh, G = 60, 16, 1.7
+    pos = rng.random((n, 3))
+    pos[0] = [0.5 / n_mesh + 1e-9, 0.3, 0.999]        # on a stencil switch and the boundary
+    mass = rng.random(n) + 0.5
+    w = rng.normal(size=(n, 3))
+    g = pm.pm_vjp(pos, mass, n_mesh, 3 / n_mesh, G, w)
+    loss = lambda p: (w * pm.pm_forces(p, mass, n_mesh, 3 / n_mesh, G)).sum()
+    rms = np.sqrt(np.mean(g ** 2))
+    picks = [(0, 0), (0, 2)] + [(int(rng.integers(n)), int(rng.integers(3))) for _ in range(14)]
+    for i, c in picks:
+        h = 1e-6
+        p, m = pos.copy(), pos.copy()
+        p[i, c] += h
+        m[i, c] -= h
+        fd = (loss(p) - loss(m)) / (2 * h)
+        # across particle 0's stencil switch the weights' second derivative
+        # jumps, so the central difference there is only first order in h
+        tol = 1e-5 if i == 0 else 1e-7
+        assert abs(fd - g[i, c]) <= tol * max(abs(fd), rms), (i, c, fd, g[i, c])
