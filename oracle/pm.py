@@ -185,3 +185,122 @@ def pm_vjp(pos, mass, n_mesh, r_cut, G, w):
                 grad[:, 1] += W[0][a] * dW[1][b] * W[2][c] * s
                 grad[:, 2] += W[0][a] * W[1][b] * dW[2][c] * s
     return grad
+
+
+# ---------------------------------------------------------------------------
+# TreePM time integration with multiple step sizes (the paper's Sec. IV-A
+# schedule: one PM cycle and two PP cycles per step).  The slow PM force
+# kicks at the step's ends; the short-range force is integrated with two
+# kick-drift-kick sub-steps of dt/2 in between:
+#     v += a_PM(x) dt/2
+#     twice:  v += a_PP dt/4;  x += v dt/2;  a_PP = PP(x);  v += a_PP dt/4
+#     a_PM = PM(x);  v += a_PM dt/2
+# ---------------------------------------------------------------------------
+def treepm_leapfrog(pos0, vel0, mass, G, eps, r_cut, theta, n_mesh, dt, steps, n_leaf=8, n_crit=64,
+                    refit=False):
+    """Integrate `steps` TreePM steps; returns (x_T, v_T, a_PP(x_T),
+    a_PM(x_T), evals) with evals = [(tree, x)] for every PP evaluation in
+    order (the initial one and two per step).  With refit the second PP
+    sub-step of each step keeps the first sub-step's tree structure and only
+    re-takes its monopoles from the new positions (OracleTree.refresh)."""
+    from . import OracleTree
+    mass = np.asarray(mass, dtype=np.float64)
+    x = np.asarray(pos0, dtype=np.float64).copy()
+    v = np.asarray(vel0, dtype=np.float64).copy()
+
+    def build(xx):
+        t = OracleTree(xx, mass, n_leaf, n_crit)
+        t.lists(r_cut, theta)
+        return t
+
+    t = build(x)
+    a_pp = t.list_forces(G, eps, r_cut)
+    evals = [(t, x.copy())]
+    a_pm = pm_forces(x, mass, n_mesh, r_cut, G)
+    h = 0.5 * dt
+    for _ in range(steps):
+        v = v + a_pm * (0.5 * dt)
+        for sub in range(2):
+            v = v + a_pp * (0.5 * h)
+            x = x + v * h
+            if sub == 1 and refit:
+                t.refresh(x)
+            else:
+                t = build(x)
+            a_pp = t.list_forces(G, eps, r_cut)
+            evals.append((t, x.copy()))
+            v = v + a_pp * (0.5 * h)
+        a_pm = pm_forces(x, mass, n_mesh, r_cut, G)
+        v = v + a_pm * (0.5 * dt)
+    return x, v, a_pp, a_pm, evals
+
+
+def treepm_leapfrog_frozen(pos0, vel0, mass, evals, G, eps, r_cut, n_mesh, dt, steps):
+    """treepm_leapfrog with every PP evaluation's tree structure frozen to
+    `evals` (monopoles re-taken from the current positions): the function
+    whose derivative treepm_leapfrog_adjoint computes.  Returns (x_T, v_T,
+    a_PP, a_PM, xs) with xs the positions of every PP evaluation."""
+    mass = np.asarray(mass, dtype=np.float64)
+    x = np.asarray(pos0, dtype=np.float64).copy()
+    v = np.asarray(vel0, dtype=np.float64).copy()
+
+    def pp(k, xx):
+        t = evals[k][0]
+        t.refresh(xx)
+        return t.list_forces(G, eps, r_cut)
+
+    xs = [x.copy()]
+    a_pp = pp(0, x)
+    a_pm = pm_forces(x, mass, n_mesh, r_cut, G)
+    h = 0.5 * dt
+    k = 1
+    for _ in range(steps):
+        v = v + a_pm * (0.5 * dt)
+        for _sub in range(2):
+            v = v + a_pp * (0.5 * h)
+            x = x + v * h
+            xs.append(x.copy())
+            a_pp = pp(k, x)
+            k += 1
+            v = v + a_pp * (0.5 * h)
+        a_pm = pm_forces(x, mass, n_mesh, r_cut, G)
+        v = v + a_pm * (0.5 * dt)
+    return x, v, a_pp, a_pm, xs
+
+
+def treepm_leapfrog_adjoint(pos0, vel0, mass, evals, G, eps, r_cut, n_mesh, dt, steps,
+                            g_x, g_v, g_app, g_apm):
+    """Reverse-mode derivative of treepm_leapfrog_frozen: given dL/dx_T,
+    dL/dv_T, dL/da_PP(x_T) and dL/da_PM(x_T), returns (dL/dx_0, dL/dv_0).
+    Each operation of the step is reversed in turn; a force a = F(x) sends
+    its cotangent g_a to g_x += VJP_F(x)[g_a] (the list adjoint of the frozen
+    tree for PP, pm_vjp for PM)."""
+    mass = np.asarray(mass, dtype=np.float64)
+    *_, xs = treepm_leapfrog_frozen(pos0, vel0, mass, evals, G, eps, r_cut, n_mesh, dt, steps)
+
+    def pp_vjp(k, ga):
+        t = evals[k][0]
+        t.refresh(xs[k])
+        return t.list_vjp(G, eps, r_cut, ga)
+
+    h = 0.5 * dt
+    gx, gv = np.asarray(g_x, dtype=np.float64).copy(), np.asarray(g_v, dtype=np.float64).copy()
+    g_pp, g_pm = np.asarray(g_app, dtype=np.float64).copy(), np.asarray(g_apm, dtype=np.float64).copy()
+    for s in range(steps, 0, -1):
+        x_end = xs[2 * s]
+        # v += a_PM(x_end) dt/2 ;  a_PM = PM(x_end)
+        g_pm = g_pm + gv * (0.5 * dt)
+        gx = gx + pm_vjp(x_end, mass, n_mesh, r_cut, G, g_pm)
+        g_pm = np.zeros_like(g_pm)
+        for k in (2 * s, 2 * s - 1):
+            # v += a_PP dt/4 ; a_PP = PP(x_k)
+            g_pp = g_pp + gv * (0.5 * h)
+            gx = gx + pp_vjp(k, g_pp)
+            # x += v h
+            gv = gv + gx * h
+            # v += a_PP(previous) dt/4
+            g_pp = gv * (0.5 * h)
+        # v += a_PM(x_start) dt/2
+        g_pm = gv * (0.5 * dt)
+    gx = gx + pp_vjp(0, g_pp) + pm_vjp(xs[0], mass, n_mesh, r_cut, G, g_pm)
+    return gx, gv

@@ -148,3 +148,43 @@ def test_pm_vjp_matches_central_differences():
         # jumps, so the central difference there is only first order in h
         tol = 1e-5 if i == 0 else 1e-7
         assert abs(fd - g[i, c]) <= tol * max(abs(fd), rms), (i, c, fd, g[i, c])
+
+
+@pytest.mark.parametrize("refit", [False, True])
+def test_treepm_leapfrog_adjoint_matches_frozen_central_differences(refit):
+    """The multiple-stepsize TreePM integrator's adjoint (PM kicks around two
+    PP sub-steps) against central differences of the same integration with
+    every PP tree structure frozen, for L = w_x.x_T + w_v.v_T + w_a.a_PP(x_T)
+    + w_m.a_PM(x_T); the second sub-step rebuilt, or refitted."""
+    from paper_1211_4406_gb300 import inputs
+    pos, mass = inputs.clustered_box(400, 4, 61)
+    rng = np.random.default_rng(62)
+    vel = 0.05 * rng.normal(size=pos.shape)
+    G, eps, rc, theta, n_mesh, dt, steps = 1.0, 1e-2, 3 / 16, 0.5, 16, 2e-4, 3
+    xT, vT, aT, mT, evals = pm.treepm_leapfrog(pos, vel, mass, G, eps, rc, theta, n_mesh, dt, steps,
+                                               n_crit=32, refit=refit)
+    assert len(evals) == 1 + 2 * steps
+    if refit:
+        assert evals[1][0] is evals[2][0] and evals[3][0] is evals[4][0]
+    # the frozen run reproduces the free one at the base point
+    fx, fv, fa, fm, _ = pm.treepm_leapfrog_frozen(pos, vel, mass, evals, G, eps, rc, n_mesh, dt, steps)
+    assert np.abs(fx - xT).max() <= 1e-14 and np.abs(fa - aT).max() <= 1e-9 * np.abs(aT).max()
+    w = [rng.normal(size=pos.shape) for _ in range(4)]
+    gx, gv = pm.treepm_leapfrog_adjoint(pos, vel, mass, evals, G, eps, rc, n_mesh, dt, steps, *w)
+
+    def loss(p, q):
+        x, v, a, m, _ = pm.treepm_leapfrog_frozen(p, q, mass, evals, G, eps, rc, n_mesh, dt, steps)
+        return (w[0] * x).sum() + (w[1] * v).sum() + (w[2] * a).sum() + (w[3] * m).sum()
+
+    for grad, which in ((gx, 0), (gv, 1)):
+        rms = np.sqrt(np.mean(grad ** 2))
+        for _ in range(6):
+            i, c = int(rng.integers(400)), int(rng.integers(3))
+            vals = []
+            for hh in (1e-3 * eps, 0.5e-3 * eps):
+                args_p, args_m = [pos.copy(), vel.copy()], [pos.copy(), vel.copy()]
+                args_p[which][i, c] += hh
+                args_m[which][i, c] -= hh
+                vals.append((loss(*args_p) - loss(*args_m)) / (2 * hh))
+            assert abs(vals[0] - vals[1]) <= 1e-5 * max(abs(vals[0]), rms)          # converged
+            assert abs(grad[i, c] - vals[1]) <= 1e-5 * max(abs(vals[1]), rms), (which, i, c)
