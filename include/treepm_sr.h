@@ -294,9 +294,29 @@ tp_status tp_pm_create(int32_t n_mesh, double r_cut, double G, void *stream, tp_
 tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
                       int32_t accumulate, void *stream);
 
-/* Copies a mesh of the last tp_pm_force call to host memory (synchronous):
- * which = 0 the potential [n_mesh^3], which = 1 the mesh acceleration
- * -grad(phi) [n_mesh^3][3]; layout (i n_mesh + j) n_mesh + k.               */
+/* The adjoint of tp_pm_force: dL/dx of L = sum_i cot_i . a_i (positions in
+ * input order), through the TSC interpolation and the TSC assignment:
+ *   dL/dx_k = sum_c grad W_k(c) [cot_k . A(c) + m_k B(c)],
+ * A the mesh force, B = K div(U) with U the TSC assignment of the cotangent
+ * vectors, div the four-point divergence and K the potential solve (FFT,
+ * Green's function, FFT^-1).  The masses are held fixed.
+ *   cot   device FP32 [n][3] = dL/da
+ *   grad  device FP64 [n][3]; overwritten, or added to when accumulate != 0
+ *         (e.g. onto tp_short_range_vjp's output)
+ * The first adjoint call on a tp_pm allocates 16 more bytes per mesh cell
+ * (make it before any stream capture).  Asynchronous.                      */
+tp_status tp_pm_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, const float *cot,
+                    double *grad, int32_t accumulate, void *stream);
+
+/* tp_pm_force and tp_pm_vjp in one call: the mesh force of the positions
+ * is computed once.  accumulate applies to both acc and grad.               */
+tp_status tp_pm_force_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
+                          const float *cot, double *grad, int32_t accumulate, void *stream);
+
+/* Copies a mesh of the last call to host memory (synchronous): which = 0 the
+ * potential [n_mesh^3] (after tp_pm_vjp or tp_pm_force_vjp: the adjoint's B
+ * instead), which = 1 the mesh acceleration -grad(phi) [n_mesh^3][3]; layout
+ * (i n_mesh + j) n_mesh + k.                                                */
 tp_status tp_pm_export_mesh(tp_pm *pm, int32_t which, float *host);
 
 /* Releases the mesh and plans (synchronises the device).  NULL is a no-op.  */

@@ -72,6 +72,8 @@ SIGNATURES = {
     "tp_launch_count": ([], _I64),
     "tp_pm_create": ([_I32, _D, _D, _V, C.POINTER(_V)], C.c_int),
     "tp_pm_force": ([_V, _V, _V, _I64, _V, _I32, _V], C.c_int),
+    "tp_pm_vjp": ([_V, _V, _V, _I64, _V, _V, _I32, _V], C.c_int),
+    "tp_pm_force_vjp": ([_V, _V, _V, _I64, _V, _V, _V, _I32, _V], C.c_int),
     "tp_pm_export_mesh": ([_V, _I32, _V], C.c_int),
     "tp_pm_free": ([_V], C.c_int),
     "tp_status_string": ([C.c_int], C.c_char_p),

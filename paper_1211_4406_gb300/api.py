@@ -276,6 +276,56 @@ class PMSolver:
         _lib.check(code, "tp_pm_force")
         return out
 
+    def vjp(self, pos: torch.Tensor, mass: torch.Tensor | None, cot: torch.Tensor, out: torch.Tensor | None = None,
+            accumulate: bool = False, stream=None) -> torch.Tensor:
+        """dL/dx (float64 [n, 3]) of L = sum_i cot_i . a_i over the PM cycle;
+        added to `out` when accumulate is set (e.g. onto the short-range VJP)."""
+        pos, mass, cot, out = self._adjoint_args(pos, mass, cot, out, accumulate)
+        code = _lib.load().tp_pm_vjp(self._h, C.c_void_p(pos.data_ptr()),
+                                     C.c_void_p(mass.data_ptr()) if mass is not None else None, int(pos.shape[0]),
+                                     C.c_void_p(cot.data_ptr()), C.c_void_p(out.data_ptr()), int(bool(accumulate)),
+                                     _stream(stream))
+        _lib.check(code, "tp_pm_vjp")
+        return out
+
+    def force_vjp(self, pos: torch.Tensor, mass: torch.Tensor | None, cot: torch.Tensor,
+                  acc: torch.Tensor | None = None, grad: torch.Tensor | None = None, accumulate: bool = False,
+                  stream=None):
+        """force() and vjp() with one mesh-force computation; returns (acc, grad)."""
+        pos, mass, cot, grad = self._adjoint_args(pos, mass, cot, grad, accumulate)
+        n = int(pos.shape[0])
+        if acc is None:
+            if accumulate:
+                raise ValueError("accumulate needs acc")
+            acc = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
+        if acc.dtype != torch.float32 or not acc.is_contiguous() or tuple(acc.shape) != (n, 3):
+            raise ValueError("acc must be a contiguous float32 [n,3] tensor")
+        code = _lib.load().tp_pm_force_vjp(self._h, C.c_void_p(pos.data_ptr()),
+                                           C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
+                                           C.c_void_p(acc.data_ptr()), C.c_void_p(cot.data_ptr()),
+                                           C.c_void_p(grad.data_ptr()), int(bool(accumulate)), _stream(stream))
+        _lib.check(code, "tp_pm_force_vjp")
+        return acc, grad
+
+    def _adjoint_args(self, pos, mass, cot, out, accumulate):
+        if self._h is None:
+            raise RuntimeError("PM solver has been freed")
+        pos = _dev_f64(pos, 3)
+        if mass is not None:
+            mass = _dev_f64(mass)
+        n = int(pos.shape[0])
+        if not isinstance(cot, torch.Tensor) or not cot.is_cuda or cot.dtype != torch.float32 \
+                or tuple(cot.shape) != (n, 3):
+            raise ValueError("cot must be a float32 CUDA tensor [n,3]")
+        cot = cot.contiguous()
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate needs out")
+            out = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != (n, 3):
+            raise ValueError("out must be a contiguous float64 [n,3] tensor")
+        return pos, mass, cot, out
+
     def export_mesh(self, which: str = "potential") -> np.ndarray:
         """The potential [N,N,N] or the mesh acceleration [N,N,N,3] of the last
         force() call (synchronous copy)."""

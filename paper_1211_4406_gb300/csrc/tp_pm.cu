@@ -187,6 +187,119 @@ __global__ void k_pm_interp(const double *pos, int64_t n, int N, const float4 *a
     }
 }
 
+// ---------------------------------------------------------------------------
+// The adjoint of the PM cycle.  For L = sum_i w_i . a_i:
+//   dL/dx_k = sum_c grad W_k(c) [w_k . A(c) + m_k B(c)]
+// with A = -grad(phi) the mesh force, U the TSC assignment of the cotangent
+// vectors, and B = K div(U): the same potential solve K (symmetric: a real,
+// even Green's function) applied to the four-point divergence of U (the
+// four-point difference is antisymmetric, so it is its own transpose up to
+// sign).  grad W_k is the derivative of particle k's weight at c.
+// ---------------------------------------------------------------------------
+__global__ void k_pm_assign_vec(const double *pos, const float *cot, int64_t n, int N, float4 *umesh)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        float wx[3], wy[3], wz[3];
+        tsc(pos[3 * p], N, ix, wx);
+        tsc(pos[3 * p + 1], N, iy, wy);
+        tsc(pos[3 * p + 2], N, iz, wz);
+        const float cx = cot[3 * p], cy = cot[3 * p + 1], cz = cot[3 * p + 2];
+        for (int a = 0; a < 3; a++) {
+            const int64_t ra = (int64_t)wrapi(ix + a - 1, N) * N;
+            for (int b = 0; b < 3; b++) {
+                const int64_t rb = (ra + wrapi(iy + b - 1, N)) * N;
+                const float wab = wx[a] * wy[b];
+                for (int c = 0; c < 3; c++) {
+                    float *u = reinterpret_cast<float *>(umesh + rb + wrapi(iz + c - 1, N));
+                    const float w = wab * wz[c];
+                    atomicAdd(u, w * cx);
+                    atomicAdd(u + 1, w * cy);
+                    atomicAdd(u + 2, w * cz);
+                }
+            }
+        }
+    }
+}
+
+// div(U) by the four-point difference along each axis.
+__global__ void k_pm_divergence(const float4 *umesh, float *out, int N)
+{
+    const int64_t total = (int64_t)N * N * N;
+    const float s = (float)N / 12.0f;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(q % N);
+        const int j = (int)((q / N) % N);
+        const int i = (int)(q / ((int64_t)N * N));
+        auto U = [&](int a, int b, int c) { return umesh[((int64_t)wrapi(a, N) * N + wrapi(b, N)) * N + wrapi(c, N)]; };
+        const float dx = 8.0f * (U(i + 1, j, k).x - U(i - 1, j, k).x) - (U(i + 2, j, k).x - U(i - 2, j, k).x);
+        const float dy = 8.0f * (U(i, j + 1, k).y - U(i, j - 1, k).y) - (U(i, j + 2, k).y - U(i, j - 2, k).y);
+        const float dz = 8.0f * (U(i, j, k + 1).z - U(i, j, k - 1).z) - (U(i, j, k + 2).z - U(i, j, k - 2).z);
+        out[q] = s * (dx + dy + dz);
+    }
+}
+
+// B (the potential solve of div U, in bmesh) into the w lane of the force mesh.
+__global__ void k_pm_pack_w(float4 *amesh, const float *bmesh, int64_t total)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        amesh[q].w = bmesh[q];
+}
+
+__device__ __forceinline__ void tsc_d(double x, int N, int &i0, float w[3], float dw[3])
+{
+    const double u = pm_wrap(x) * N;
+    const double c = rint(u);
+    const double d = u - c;
+    i0 = (int)c;
+    const double a = 0.5 - d, b = 0.5 + d;
+    w[0] = (float)(0.5 * a * a);
+    w[1] = (float)(0.75 - d * d);
+    w[2] = (float)(0.5 * b * b);
+    dw[0] = (float)(-a * N);
+    dw[1] = (float)(-2.0 * d * N);
+    dw[2] = (float)(b * N);
+}
+
+__global__ void k_pm_vjp_interp(const double *pos, const double *mass, float m_default, const float *cot, int64_t n,
+                                int N, const float4 *amesh, double *grad, int accumulate)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        float wx[3], wy[3], wz[3], dx[3], dy[3], dz[3];
+        tsc_d(pos[3 * p], N, ix, wx, dx);
+        tsc_d(pos[3 * p + 1], N, iy, wy, dy);
+        tsc_d(pos[3 * p + 2], N, iz, wz, dz);
+        const float cx = cot[3 * p], cy = cot[3 * p + 1], cz = cot[3 * p + 2];
+        const float m = mass ? (float)mass[p] : m_default;
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int a = 0; a < 3; a++) {
+            const int64_t ra = (int64_t)wrapi(ix + a - 1, N) * N;
+            for (int b = 0; b < 3; b++) {
+                const int64_t rb = (ra + wrapi(iy + b - 1, N)) * N;
+                for (int c = 0; c < 3; c++) {
+                    const float4 v = __ldg(amesh + rb + wrapi(iz + c - 1, N));
+                    const float sv = fmaf(cx, v.x, fmaf(cy, v.y, fmaf(cz, v.z, m * v.w)));
+                    gx = fmaf(dx[a] * wy[b] * wz[c], sv, gx);
+                    gy = fmaf(wx[a] * dy[b] * wz[c], sv, gy);
+                    gz = fmaf(wx[a] * wy[b] * dz[c], sv, gz);
+                }
+            }
+        }
+        if (accumulate) {
+            grad[3 * p] += gx;
+            grad[3 * p + 1] += gy;
+            grad[3 * p + 2] += gz;
+        } else {
+            grad[3 * p] = gx;
+            grad[3 * p + 1] = gy;
+            grad[3 * p + 2] = gz;
+        }
+    }
+}
+
 bool is_dev(const void *p)
 {
     if (!p) return false;
@@ -213,7 +326,8 @@ struct tp_pm {
     float *rho = nullptr;           // [N^3] mass per cell, then (in place of it) the potential
     cufftComplex *spec = nullptr;   // [N][N][N/2+1]
     float *green = nullptr;         // [N][N][N/2+1]
-    float4 *amesh = nullptr;        // [N^3] -grad(phi), w unused
+    float4 *amesh = nullptr;        // [N^3] -grad(phi); w: the adjoint's B
+    float4 *umesh = nullptr;        // [N^3] assigned cotangent vectors (adjoint; allocated on first use)
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
 };
@@ -227,6 +341,7 @@ static void pm_release(tp_pm *pm)
     cudaFree(pm->spec);
     cudaFree(pm->green);
     cudaFree(pm->amesh);
+    cudaFree(pm->umesh);
     delete pm;
 }
 
@@ -276,6 +391,63 @@ extern "C" tp_status tp_pm_create(int32_t n_mesh, double r_cut, double G, void *
     return TP_OK;
 }
 
+// The potential solve K in place: rho -> FFT -> x Green's function -> FFT^-1 -> rho.
+static tp_status pm_solve(tp_pm *pm, cudaStream_t s)
+{
+    const int N = pm->N;
+    const int64_t half = (int64_t)N * N * (N / 2 + 1);
+    if (cufftSetStream(pm->fwd, s) != CUFFT_SUCCESS || cufftExecR2C(pm->fwd, pm->rho, pm->spec) != CUFFT_SUCCESS)
+        return TP_ERR_CUDA;
+    TP_LAUNCH(k_pm_green, pm_grid(half, kPmThreads), kPmThreads, 0, s, pm->spec, pm->green, half);
+    if (cufftSetStream(pm->inv, s) != CUFFT_SUCCESS || cufftExecC2R(pm->inv, pm->spec, pm->rho) != CUFFT_SUCCESS)
+        return TP_ERR_CUDA;
+    return TP_OK;
+}
+
+// Steps 1-3 of the cycle: the mesh force of the current positions in amesh.
+static tp_status pm_mesh_force(tp_pm *pm, const double *pos, const double *mass, int64_t n, cudaStream_t s)
+{
+    const int N = pm->N;
+    const int64_t cells = (int64_t)N * N * N;
+    cudaMemsetAsync(pm->rho, 0, sizeof(float) * cells, s);
+    TP_LAUNCH(k_pm_assign, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, mass, n, N, (float)(1.0 / (double)n),
+              pm->rho);
+    const tp_status e = pm_solve(pm, s);
+    if (e != TP_OK) return e;
+    TP_LAUNCH(k_pm_gradient, pm_grid(cells, kPmThreads), kPmThreads, 0, s, pm->rho, pm->amesh, N);
+    return TP_OK;
+}
+
+// The adjoint given the mesh force in amesh: U, div U, B = K div U, and the
+// per-particle gradient.
+static tp_status pm_adjoint(tp_pm *pm, const double *pos, const double *mass, int64_t n, const float *cot,
+                            double *grad, int32_t accumulate, cudaStream_t s)
+{
+    const int N = pm->N;
+    const int64_t cells = (int64_t)N * N * N;
+    cudaMemsetAsync(pm->umesh, 0, sizeof(float4) * cells, s);
+    TP_LAUNCH(k_pm_assign_vec, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, cot, n, N, pm->umesh);
+    TP_LAUNCH(k_pm_divergence, pm_grid(cells, kPmThreads), kPmThreads, 0, s, pm->umesh, pm->rho, N);
+    const tp_status e = pm_solve(pm, s);
+    if (e != TP_OK) return e;
+    TP_LAUNCH(k_pm_pack_w, pm_grid(cells, kPmThreads), kPmThreads, 0, s, pm->amesh, pm->rho, cells);
+    TP_LAUNCH(k_pm_vjp_interp, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, mass, (float)(1.0 / (double)n), cot,
+              n, N, pm->amesh, grad, accumulate);
+    return TP_OK;
+}
+
+static tp_status pm_need_umesh(tp_pm *pm)
+{
+    if (pm->umesh) return TP_OK;
+    const int64_t N = pm->N;
+    if (cudaMalloc(&pm->umesh, sizeof(float4) * N * N * N) != cudaSuccess) {
+        cudaGetLastError();
+        pm->umesh = nullptr;
+        return TP_ERR_OOM;
+    }
+    return TP_OK;
+}
+
 extern "C" tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
                                  int32_t accumulate, void *stream)
 {
@@ -283,18 +455,42 @@ extern "C" tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mas
     if (n == 0) return TP_OK;
     if (!is_dev(pos) || !is_dev(acc) || (mass && !is_dev(mass))) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int N = pm->N;
-    const int64_t cells = (int64_t)N * N * N, half = (int64_t)N * N * (N / 2 + 1);
-    cudaMemsetAsync(pm->rho, 0, sizeof(float) * cells, s);
-    TP_LAUNCH(k_pm_assign, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, mass, n, N, (float)(1.0 / (double)n),
-              pm->rho);
-    if (cufftSetStream(pm->fwd, s) != CUFFT_SUCCESS || cufftExecR2C(pm->fwd, pm->rho, pm->spec) != CUFFT_SUCCESS)
-        return TP_ERR_CUDA;
-    TP_LAUNCH(k_pm_green, pm_grid(half, kPmThreads), kPmThreads, 0, s, pm->spec, pm->green, half);
-    if (cufftSetStream(pm->inv, s) != CUFFT_SUCCESS || cufftExecC2R(pm->inv, pm->spec, pm->rho) != CUFFT_SUCCESS)
-        return TP_ERR_CUDA;
-    TP_LAUNCH(k_pm_gradient, pm_grid(cells, kPmThreads), kPmThreads, 0, s, pm->rho, pm->amesh, N);
-    TP_LAUNCH(k_pm_interp, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, n, N, pm->amesh, acc, accumulate);
+    const tp_status e = pm_mesh_force(pm, pos, mass, n, s);
+    if (e != TP_OK) return e;
+    TP_LAUNCH(k_pm_interp, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, n, pm->N, pm->amesh, acc, accumulate);
+    return cudaGetLastError() == cudaSuccess ? TP_OK : TP_ERR_CUDA;
+}
+
+extern "C" tp_status tp_pm_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, const float *cot,
+                               double *grad, int32_t accumulate, void *stream)
+{
+    if (!pm || n < 0) return TP_ERR_INVALID_ARG;
+    if (n == 0) return TP_OK;
+    if (!is_dev(pos) || !is_dev(cot) || !is_dev(grad) || (mass && !is_dev(mass))) return TP_ERR_INVALID_ARG;
+    tp_status e = pm_need_umesh(pm);
+    if (e != TP_OK) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = pm_mesh_force(pm, pos, mass, n, s);
+    if (e == TP_OK) e = pm_adjoint(pm, pos, mass, n, cot, grad, accumulate, s);
+    if (e != TP_OK) return e;
+    return cudaGetLastError() == cudaSuccess ? TP_OK : TP_ERR_CUDA;
+}
+
+extern "C" tp_status tp_pm_force_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
+                                     const float *cot, double *grad, int32_t accumulate, void *stream)
+{
+    if (!pm || n < 0) return TP_ERR_INVALID_ARG;
+    if (n == 0) return TP_OK;
+    if (!is_dev(pos) || !is_dev(acc) || !is_dev(cot) || !is_dev(grad) || (mass && !is_dev(mass)))
+        return TP_ERR_INVALID_ARG;
+    tp_status e = pm_need_umesh(pm);
+    if (e != TP_OK) return e;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = pm_mesh_force(pm, pos, mass, n, s);
+    if (e != TP_OK) return e;
+    TP_LAUNCH(k_pm_interp, pm_grid(n, kPmThreads), kPmThreads, 0, s, pos, n, pm->N, pm->amesh, acc, accumulate);
+    e = pm_adjoint(pm, pos, mass, n, cot, grad, accumulate, s);
+    if (e != TP_OK) return e;
     return cudaGetLastError() == cudaSuccess ? TP_OK : TP_ERR_CUDA;
 }
 
