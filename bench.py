@@ -879,9 +879,78 @@ def run_treepm(args, rank, world, local_rank):
     tree.close()
 
 
+def run_treepm_leapfrog(args, rank, world, local_rank):
+    """Multiple-stepsize TreePM integration of the clustered 2M box (the
+    paper's schedule: per step one PM cycle on the 128^3 mesh and two PP
+    kick-drift-kick sub-steps of dt/2), timed per step; the second sub-step's
+    tree rebuilt (as the paper does) or refitted from the first (lists kept)."""
+    import torch
+
+    from paper_1211_4406_gb300 import build as libbuild
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, PMSolver, launch_count
+    from paper_1211_4406_gb300.autograd import treepm_leapfrog
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    box = inputs.config_box(CONFIG_K)
+    dt = 1e-4
+    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32")
+    pm = PMSolver(128, box.r_cut, box.G)
+    x0 = torch.tensor(box.pos, device=dev)
+    v0 = torch.zeros_like(x0)
+    mass = torch.tensor(box.mass, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    launches = 0
+    clk = None
+    for refit in (True, False):
+        def steps(k):
+            with torch.no_grad():
+                treepm_leapfrog(x0, v0, mass, prm, pm, dt, k, refit=refit)
+        for _ in range(args.warmup):
+            steps(1)
+        torch.cuda.synchronize()
+        # time k steps and 1 step: their difference is k - 1 steps without the initial forces
+        k = max(2, args.steps // 4)
+        if refit:
+            clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+            clocks.start()
+            clocks.mark()
+            l0 = launch_count()
+        t_k = _timed_replays(lambda: steps(k), 3, flush, stream)
+        t_1 = _timed_replays(lambda: steps(1), 3, flush, stream)
+        if refit:
+            launches = launch_count() - l0
+            clk = clocks.stop()
+        res[refit] = (sorted(t_k)[1] - sorted(t_1)[1]) / (k - 1)
+    ms_step, = max_over_ranks([res[True]], device=dev)
+    if rank != 0:
+        return
+    line = {
+        "metric": "particles x steps/s (multiple-stepsize TreePM integration, PM + 2 PP sub-steps per step, "
+                  "clustered 2M box)",
+        "value": world * box.n / (ms_step * 1e-3), "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "treepm-leapfrog-2M", "n": box.n, "r_cut": "3/128", "eps": "1/6400", "theta": 0.5,
+                   "n_crit": box.n_crit, "n_mesh": 128, "dt": dt,
+                   "step": "PM kick, 2 x (PP kick, drift, tree, PP force, PP kick), PM force, PM kick",
+                   "second_sub_step": "refit (lists kept)",
+                   "l2": "flushed (256 MiB write) before every timed run"},
+        "ms_per_step_rebuild_both_sub_steps": res[False],
+        "ms_per_step_refit_second_sub_step": res[True],
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    pm.close()
+
+
 WORKLOADS = {"clustered-2M": run_ours, "batched-64": run_batched, "uniform-32k": run_uniform_fp64,
              "clustered-134M": run_large, "paper-regime-2M": run_paper_regime, "leapfrog-262k": run_leapfrog,
-             "treepm-2M": run_treepm}
+             "treepm-2M": run_treepm, "treepm-leapfrog-2M": run_treepm_leapfrog}
 
 
 def main():
@@ -898,7 +967,8 @@ def main():
                          "the 512^3 throughput box (chunked lists); paper-regime-2M: the 2M box with the "
                          "paper's list shapes (r_cut = 7.5 spacings, n_crit = 128); leapfrog-262k: the gradient "
                          "of a 10-step KDK chain (checkpointed adjoint); treepm-2M: the whole TreePM "
-                         "acceleration (rebuild + short-range + PM on 128^3)")
+                         "acceleration (rebuild + short-range + PM on 128^3); treepm-leapfrog-2M: the "
+                         "multiple-stepsize TreePM integrator (PM once, PP twice per step)")
     ap.add_argument("--xi", default="plain", choices=["plain", "softened"],
                     help="cutoff argument of Eq. 3 for clustered-2M and paper-regime-2M: plain r (default) "
                          "or the softened sqrt(r^2+eps^2) of the paper's kernel")
