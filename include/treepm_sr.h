@@ -254,7 +254,7 @@ tp_status tp_short_range_force_noalloc(const double *pos, const double *mass, in
                                        const tp_params *p, float *acc, void *stream);
 
 /* ------------------------------------------------------------------------
- * The long-range (PM) half of TreePM (Sec. II).  Each tp_pm_force call runs
+ * The long-range (PM) half of TreePM (Sec. II, cycle of Sec. II-B).  Each tp_pm_force call runs
  * the PM cycle on one GPU over an n_mesh^3 periodic mesh of the unit box
  * (mesh point (i,j,k) at (i,j,k)/n_mesh):
  *   1. TSC assignment of the masses to the 27 mesh points around each

@@ -3,7 +3,7 @@ ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline leg may import this module; the CUDA library shares no code with
 it.
 
-It follows the PM cycle of Sec. II (Ishiyama, Nitadori & Makino, SC12) step by
+It follows the PM cycle of Sec. II-B (Ishiyama, Nitadori & Makino, SC12) step by
 step, in plain numpy over an N^3 periodic mesh of the unit box (spacing
 h = 1/N, mesh point (i, j, k) at (i h, j h, k h)):
 
@@ -188,7 +188,7 @@ def pm_vjp(pos, mass, n_mesh, r_cut, G, w):
 
 
 # ---------------------------------------------------------------------------
-# TreePM time integration with multiple step sizes (the paper's Sec. IV-A
+# TreePM time integration with multiple step sizes (the paper's Sec. III-A
 # schedule: one PM cycle and two PP cycles per step).  The slow PM force
 # kicks at the step's ends; the short-range force is integrated with two
 # kick-drift-kick sub-steps of dt/2 in between:

@@ -1,5 +1,6 @@
-// tp_pm.cu -- the long-range (PM) half of TreePM (Sec. II): the PM cycle the
-// paper runs every step, on one GPU and an N^3 periodic mesh of the unit box.
+// tp_pm.cu -- the long-range (PM) half of TreePM (the density split of
+// Sec. II, the PM cycle of Sec. II-B): the cycle the paper runs every step,
+// on one GPU and an N^3 periodic mesh of the unit box.
 //
 //   k_pm_assign   TSC mass assignment: each particle adds its mass to the 27
 //                 mesh points around its nearest one (FP32 atomics, L2)

@@ -1,4 +1,4 @@
-"""Pins of the PM (long-range) oracle, Sec. II's PM cycle.
+"""Pins of the PM (long-range) oracle, the PM cycle of Sec. II-B.
 
 Independent pins:
 - S(k) against a numerical quadrature of the S2 density of Eq. 1;
