@@ -192,6 +192,7 @@ static bool alloc_nodes(tp_tree *t, int64_t cap)
     D.cenx = P.get<double>(c); D.ceny = P.get<double>(c); D.cenz = P.get<double>(c);
     D.hfx = P.get<double>(c); D.hfy = P.get<double>(c); D.hfz = P.get<double>(c);
     D.cX = P.get<uint64_t>(c); D.cY = P.get<uint64_t>(c); D.cZ = P.get<uint64_t>(c);
+    D.nsrc = P.get<SrcRec>(c);
     D.wn = P.get<WNode>(c);
     t->nch = P.get<uint32_t>(c);
     t->nofs = P.get<uint32_t>(c);
@@ -597,6 +598,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.X = B.get<uint64_t>(nn); D.Y = B.get<uint64_t>(nn); D.Z = B.get<uint64_t>(nn);
     D.P32 = B.get<uint4>(nn);
     D.rx = B.get<double>(nn); D.ry = B.get<double>(nn); D.rz = B.get<double>(nn);
+    D.psrc = B.get<SrcRec>(nn);
     t->radix_tmp = B.get<char>(tp::radix_tmp_bytes(n));
     t->scan_tmp = B.get<char>(tp::scan_tmp_bytes());
     t->flag = B.get<uint32_t>(nn); t->gofs = B.get<uint32_t>(nn);

@@ -67,7 +67,9 @@ __global__ void k_gather(const double *pos, const double *mass, TreeDev T)
         const uint64_t X = tp_fixed64(x), Y = tp_fixed64(y), Z = tp_fixed64(z);
         T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
         T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
-        T.m[s] = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
+        const double m = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
+        T.m[s] = m;
+        T.psrc[s] = SrcRec{X, Y, Z, m};
     }
 }
 
@@ -91,7 +93,12 @@ __global__ void k_refit_gather(const double *pos, const double *mass, TreeDev T)
         const uint64_t X = tp_fixed64(wrap01(x[0])), Y = tp_fixed64(wrap01(x[1])), Z = tp_fixed64(wrap01(x[2]));
         T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
         T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
-        if (mass) T.m[s] = mass[i];
+        double m = T.m[s];
+        if (mass) {
+            m = mass[i];
+            T.m[s] = m;
+        }
+        T.psrc[s] = SrcRec{X, Y, Z, m};
     }
 }
 
@@ -278,7 +285,9 @@ __global__ void k_moments(TreeDev T, int L)
         T.comx[i] = mx; T.comy[i] = my; T.comz[i] = mz;
         // images of the centres (in [0,1) after a build; after a refit they
         // may lie just outside, hence the wrap)
-        T.cX[i] = tp_fixed64(wrap01(mx)); T.cY[i] = tp_fixed64(wrap01(my)); T.cZ[i] = tp_fixed64(wrap01(mz));
+        const uint64_t CX = tp_fixed64(wrap01(mx)), CY = tp_fixed64(wrap01(my)), CZ = tp_fixed64(wrap01(mz));
+        T.cX[i] = CX; T.cY[i] = CY; T.cZ[i] = CZ;
+        T.nsrc[i] = SrcRec{CX, CY, CZ, M};
         WNode w;
         w.cx = (uint32_t)(tp_fixed64(wrap01(cx)) >> 32);
         w.cy = (uint32_t)(tp_fixed64(wrap01(cy)) >> 32);

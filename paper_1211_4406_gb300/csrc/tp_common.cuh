@@ -51,6 +51,14 @@ struct __align__(16) WNode {
     int32_t level, pad;
 };
 
+// The 32-byte record an interaction-list entry is made from: the source's
+// fixed-point image and mass, one aligned sector per gather (particles and
+// node monopoles alike).
+struct __align__(32) SrcRec {
+    uint64_t X, Y, Z;
+    double m;
+};
+
 struct TreeDev {
     int64_t n;
     int32_t nbox;
@@ -65,6 +73,7 @@ struct TreeDev {
     uint64_t *X, *Y, *Z;
     uint4 *P32;                       // {X, Y, Z} >> 32 per particle: the walk's 2^-32 grid
     double *rx, *ry, *rz;             // sorted positions of the last build (refit reference)
+    SrcRec *psrc;                     // {X, Y, Z, m} per particle
     // nodes
     int32_t *first, *count, *child, *nchild, *parent, *skip, *nbx;
     uint8_t *level;
@@ -73,6 +82,7 @@ struct TreeDev {
     double *lox, *loy, *loz, *hix, *hiy, *hiz;
     double *cenx, *ceny, *cenz, *hfx, *hfy, *hfz;
     uint64_t *cX, *cY, *cZ;           // COM fixed-point images
+    SrcRec *nsrc;                     // {cX, cY, cZ, M} per node
     WNode *wn;
     int64_t *lstart, *lcount;         // [TP_NLEVELS + 1] each, device
     int64_t *n_nodes;                 // device scalar

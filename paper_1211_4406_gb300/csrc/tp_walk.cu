@@ -72,16 +72,9 @@ struct WalkGroup {
 __device__ __forceinline__ float4 entry_record(const TreeDev &T, uint64_t GX, uint64_t GY, uint64_t GZ, float sc,
                                               int32_t e)
 {
-    uint64_t ex, ey, ez;
-    double m;
-    if (e >= 0) {
-        ex = T.X[e]; ey = T.Y[e]; ez = T.Z[e]; m = T.m[e];
-    } else {
-        const int32_t nd = -e - 1;
-        ex = T.cX[nd]; ey = T.cY[nd]; ez = T.cZ[nd]; m = T.M[nd];
-    }
-    return make_float4(__ll2float_rn((long long)(ex - GX)) * sc, __ll2float_rn((long long)(ey - GY)) * sc,
-                       __ll2float_rn((long long)(ez - GZ)) * sc, (float)m);
+    const SrcRec q = e >= 0 ? T.psrc[e] : T.nsrc[-e - 1];
+    return make_float4(__ll2float_rn((long long)(q.X - GX)) * sc, __ll2float_rn((long long)(q.Y - GY)) * sc,
+                       __ll2float_rn((long long)(q.Z - GZ)) * sc, (float)q.m);
 }
 
 __device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g)
