@@ -926,6 +926,18 @@ def run_treepm_leapfrog(args, rank, world, local_rank):
             launches = launch_count() - l0
             clk = clocks.stop()
         res[refit] = (sorted(t_k)[1] - sorted(t_1)[1]) / (k - 1)
+    # one gradient through 3 steps (refitted second sub-steps): d(sum w . a_T)/dx0
+    w = torch.tensor(inputs.cotangent(box.n, box.seed + 7), device=dev).double()
+    xg = x0.clone().requires_grad_(True)
+
+    def grad_once():
+        xg.grad = None
+        _, _, a_pp, a_pm = treepm_leapfrog(xg, v0, mass, prm, pm, dt, 3, refit=True)
+        ((a_pp.double() + a_pm.double()) * w).sum().backward()
+
+    grad_once()
+    torch.cuda.synchronize()
+    t_grad = sorted(_timed_replays(grad_once, 3, flush, stream))[1]
     ms_step, = max_over_ranks([res[True]], device=dev)
     if rank != 0:
         return
@@ -942,6 +954,9 @@ def run_treepm_leapfrog(args, rank, world, local_rank):
                    "l2": "flushed (256 MiB write) before every timed run"},
         "ms_per_step_rebuild_both_sub_steps": res[False],
         "ms_per_step_refit_second_sub_step": res[True],
+        "ms_per_gradient_3_steps": t_grad,
+        "gradient": "d(sum w . (a_PP + a_PM)(x_T))/dx_0 through 3 steps, one checkpoint per step: 7 PP and 4 PM "
+                    "forces forward; recomputation, 7 PP and 4 PM adjoints backward",
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

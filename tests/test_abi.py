@@ -55,3 +55,16 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     p = _lib.params(r_cut=0.1)
     assert _lib.load().tp_build_tree(None, None, -1, ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert _lib.load().tp_tree_free(None) == 0
+
+
+def test_pm_invalid_arguments_rejected_without_touching_the_gpu(lib):
+    from paper_1211_4406_gb300 import _lib
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    assert L.tp_pm_create(15, 0.2, 1.0, None, ctypes.byref(h)) == -1      # odd mesh
+    assert L.tp_pm_create(4, 0.2, 1.0, None, ctypes.byref(h)) == -1       # below 8
+    assert L.tp_pm_create(16, 0.5, 1.0, None, ctypes.byref(h)) == -1      # r_cut must be < 1/2
+    assert L.tp_pm_create(16, 0.2, float("nan"), None, ctypes.byref(h)) == -1
+    assert L.tp_pm_force(None, None, None, 10, None, 0, None) == -1
+    assert L.tp_pm_vjp(None, None, None, 10, None, None, 0, None) == -1
+    assert L.tp_pm_free(None) == 0
