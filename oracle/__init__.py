@@ -57,6 +57,8 @@ def _load():
                                           C.c_int64, _I64, _D, C.c_int]
     lib.or_brute_vjp.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, _D,
                                  C.c_int]
+    lib.or_brute_vjp_sample.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D,
+                                        C.c_int64, _I64, _D, C.c_int]
     lib.or_morton.restype = C.c_uint64
     lib.or_morton.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
     lib.or_key_of.restype = C.c_uint64
@@ -155,6 +157,16 @@ def brute_vjp(pos, mass, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
     grad = np.zeros_like(pos)
     _load().or_brute_vjp(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), _dp(grad),
                          int(xi_softened))
+    return grad
+
+
+def brute_vjp_sample(pos, mass, G, eps, rcut, w, idx, xi_softened=False) -> np.ndarray:
+    """Rows idx of brute_vjp (each O(N)), for boxes too large for the full sum."""
+    pos, mass, w = _f64(pos), _f64(mass), _f64(w)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    grad = np.zeros((idx.size, 3))
+    _load().or_brute_vjp_sample(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), idx.size,
+                                idx.ctypes.data_as(_I64), _dp(grad), int(xi_softened))
     return grad
 
 

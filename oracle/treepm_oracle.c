@@ -259,6 +259,30 @@ void or_brute_vjp(int64_t n, const double *pos, const double *mass, double G, do
     free(x);
 }
 
+/* The same gradient for a sample of particles idx[0..ns) only (large boxes):
+ * row s of the result is dL/dx_{idx[s]}. */
+void or_brute_vjp_sample(int64_t n, const double *pos, const double *mass, double G, double eps,
+                         double rcut, const double *wv, int64_t ns, const int64_t *idx, double *grad,
+                         int xi_soft)
+{
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t s = 0; s < ns; s++) {
+        int64_t k = idx[s];
+        double xk = wrap01(pos[3 * k]), yk = wrap01(pos[3 * k + 1]), zk = wrap01(pos[3 * k + 2]);
+        double gk[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == k) continue;
+            double u[3], v[3];
+            for (int c = 0; c < 3; c++) u[c] = mass[k] * wv[3 * j + c] - mass[j] * wv[3 * k + c];
+            pair_jw(minimg(wrap01(pos[3 * j]) - xk), minimg(wrap01(pos[3 * j + 1]) - yk),
+                    minimg(wrap01(pos[3 * j + 2]) - zk), 1.0, u, &P, v);
+            gk[0] += v[0]; gk[1] += v[1]; gk[2] += v[2];
+        }
+        grad[3 * s] = gk[0]; grad[3 * s + 1] = gk[1]; grad[3 * s + 2] = gk[2];
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Morton keys (tree algorithm, Sec. I): 21 bits per axis, x bit highest.    */
 /* ------------------------------------------------------------------------ */

@@ -113,3 +113,12 @@ def test_sampled_brute_force_equals_full():
     full = oracle.brute_force(pos, mass, 1.0, 1e-3, 0.1)
     idx = np.array([0, 17, 599, 1199])
     assert np.array_equal(oracle.brute_force_sample(pos, mass, 1.0, 1e-3, 0.1, idx), full[idx])
+
+
+def test_sampled_brute_vjp_equals_full_rows():
+    pos, mass = inputs.clustered_box(900, 5, 13)
+    mass = mass * np.linspace(0.5, 1.5, mass.size)
+    w = inputs.cotangent(900, 14).astype(np.float64)
+    full = oracle.brute_vjp(pos, mass, 1.0, 1e-3, 0.1, w)
+    idx = np.array([0, 5, 448, 899])
+    assert np.array_equal(oracle.brute_vjp_sample(pos, mass, 1.0, 1e-3, 0.1, w, idx), full[idx])
