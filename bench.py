@@ -226,7 +226,7 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     from paper_1211_4406_gb300 import autotune
     from paper_1211_4406_gb300 import build as libbuild
     from paper_1211_4406_gb300 import inputs
-    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count, measure_peak
+    from paper_1211_4406_gb300.api import CapturedStep, Params, ShortRangeTree, launch_count, measure_peak
     from paper_1211_4406_gb300.profile_step import traffic_for
 
     libbuild.build()
@@ -292,25 +292,46 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
+    # The step replayed from one CUDA graph (the library's batched-launch
+    # path): the same kernels as the direct calls, without a host launch per
+    # kernel.  Kernel timing is on during the capture, so every replay also
+    # times the one-pass kernel (external event nodes).
     tree.set_kernel_timing(True)
-    launches0 = launch_count()
-    per, k_fused_ms = [], []
+    l0 = launch_count()
+    graph_step = CapturedStep(tree, pos, mass, cot, acc, grad)    # warm-up body + captured body
+    kernels_per_step = (launch_count() - l0) // 2
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph_step.replay()
+    torch.cuda.synchronize()
+    t_step, k_fused_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        graph_step.replay()
+        e1.record(stream)
+        e1.synchronize()
+        t_step.append(e0.elapsed_time(e1))
+        k_fused_ms.append(tree.kernel_ms()[1])   # the one-pass kernel of this replay
+    launches = kernels_per_step * args.steps
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    if tree.status() != 0:
+        raise RuntimeError("tree status after the timed region")
+
+    # ---- the same step as direct calls, with its phases ------------------------
+    per = []
     for _ in range(args.steps):
         flush.zero_()
         evs = [ev() for _ in range(3)]
         step(pos, mass, cot, evs)
         per.append(evs)
-        k_fused_ms.append(tree.kernel_ms()[1])   # events around the one-pass kernel (waits for it)
     torch.cuda.synchronize()
-    launches = launch_count() - launches0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
     t_build = [e[0].elapsed_time(e[1]) for e in per]
     t_fused = [e[1].elapsed_time(e[2]) for e in per]
-    t_step = [e[0].elapsed_time(e[2]) for e in per]
-    if tree.status() != 0:
-        raise RuntimeError("tree status after the timed region")
+    t_direct = [e[0].elapsed_time(e[2]) for e in per]
 
     # ---- the separate calls, each kernel timed by its own events ---------------
     sep, k_pair_ms, k_vjp_ms = [], [], []
@@ -328,15 +349,13 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     # ---- end to end from host buffers ---------------------------------------
     acc_h = torch.empty((box.n, 3), dtype=torch.float32).pin_memory()
     grad_h = torch.empty((box.n, 3), dtype=torch.float64).pin_memory()
-    pos_d = torch.empty_like(pos)
-    mass_d = torch.empty_like(mass)
-    cot_d = torch.empty_like(cot)
 
     def e2e_step():
-        pos_d.copy_(pos_h, non_blocking=True)
-        mass_d.copy_(mass_h, non_blocking=True)
-        cot_d.copy_(cot_h, non_blocking=True)
-        step(pos_d, mass_d, cot_d)
+        # host inputs into the tensors the graph reads, one replay, results back
+        pos.copy_(pos_h, non_blocking=True)
+        mass.copy_(mass_h, non_blocking=True)
+        cot.copy_(cot_h, non_blocking=True)
+        graph_step.replay()
         acc_h.copy_(acc, non_blocking=True)
         grad_h.copy_(grad, non_blocking=True)
 
@@ -401,7 +420,10 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},
         "gpu_launches": launches,
+        "gpu_launches_basis": f"{kernels_per_step} kernels per graph replay x {args.steps} replays",
+        "step": "one CUDA-graph replay (CapturedStep) of tp_rebuild_tree + tp_short_range_force_vjp",
         "clocks": clk,
+        "direct_calls": {"ms_per_step": mean(t_direct), "value": per_step_inter / (mean(t_direct) * 1e-3)},
         "phases_ms": {"build": mean(t_build), "force_and_vjp_one_pass": mean(t_fused),
                       "force_fp32_separate": mean([e[1].elapsed_time(e[2]) for e in sep]),
                       "vjp_fp32_separate": mean([e[2].elapsed_time(e[3]) for e in sep]),

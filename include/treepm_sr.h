@@ -225,7 +225,9 @@ tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entrie
 tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable);
 /* Durations in ms of those two launches in the last force and vjp calls made
  * with timing on; -1 for a call that recorded nothing (timing off, FP64 tree,
- * n = 0).  Synchronises on the events.                                      */
+ * n = 0).  Synchronises on the events.  The events are recorded as external
+ * events, so calls captured in a CUDA graph with timing on time the kernels
+ * of each replay (read after the replay).                                   */
 tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms);
 
 /* Largest particle count tp_short_range_force_noalloc accepts.              */

@@ -948,6 +948,17 @@ __global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
 
 // Launchers, instantiated for the plain (SOFT = false) and the softened
 // (SOFT = true) cutoff argument; the tp:: entry points pick one per tree.
+// The optional timing events bracket the pair kernel.  Under stream capture
+// they are recorded as external events, which become event nodes of the
+// graph, so each replay times the kernel too; otherwise as plain records.
+void record_timing_event(cudaEvent_t ev, cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
 using tp::num_sms;
 using tp::occupancy;
 
@@ -964,7 +975,7 @@ void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *o
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
     };
-    if (ev0) cudaEventRecord(ev0, s);
+    if (ev0) record_timing_event(ev0, s);
     if (fwd_particles == 1) {
         auto kp = k_pair_packed<1, SOFT>;
         TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
@@ -975,7 +986,7 @@ void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *o
         auto kp = k_pair_packed<2, SOFT>;
         TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
     }
-    if (ev1) cudaEventRecord(ev1, s);
+    if (ev1) record_timing_event(ev1, s);
     auto k = k_pair<float, true, SOFT>;
     TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
 }
@@ -1012,12 +1023,12 @@ void vjp_pairs_t(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *qu
     };
     if (sizeof(R) == 4) {
         cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
-        if (ev0) cudaEventRecord(ev0, s);
+        if (ev0) record_timing_event(ev0, s);
         if (adj_entries == 2)
             launch_vjp_fused<2, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
         else
             launch_vjp_fused<4, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
-        if (ev1) cudaEventRecord(ev1, s);
+        if (ev1) record_timing_event(ev1, s);
     } else {
         cudaMemsetAsync(queue, 0, sizeof(int32_t), s);
     }
