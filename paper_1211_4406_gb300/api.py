@@ -379,18 +379,20 @@ def launch_count() -> int:
 class CapturedStep:
     """One whole hot-path step -- rebuild, then the forces and their adjoint
     for the fixed cotangent `cot` in one pass -- captured once in a CUDA graph
-    and replayed with a single launch.  `pos` (and `mass`,
+    and replayed with a single launch.  With a PMSolver `pm` (same r_cut and
+    G) the long-range force and adjoint are added onto both outputs in the
+    same graph: the whole TreePM step.  `pos` (and `mass`,
     `cot`) are read in place at every replay; `acc` and `grad` are written.
     The tree keeps the capacities of its allocating build: check
     tree.status() after replays whose particles moved far."""
 
     def __init__(self, tree: ShortRangeTree, pos: torch.Tensor, mass, cot: torch.Tensor,
-                 acc: torch.Tensor, grad: torch.Tensor, with_vjp: bool = True):
+                 acc: torch.Tensor, grad: torch.Tensor, with_vjp: bool = True, pm: "PMSolver | None" = None):
         if tree.stats()["n_windows"] > 1:
             raise ValueError("a tree in chunked mode (bounded list memory) plans its windows with a host "
                              "synchronisation and cannot be captured in a CUDA graph")
         self.tree, self.pos, self.mass, self.cot, self.acc, self.grad = tree, pos, mass, cot, acc, grad
-        self.with_vjp = with_vjp
+        self.with_vjp, self.pm = with_vjp, pm
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -405,8 +407,12 @@ class CapturedStep:
         self.tree.rebuild(self.pos, self.mass)
         if self.with_vjp:                    # the cotangent is fixed: forces and adjoint in one pass
             self.tree.force_vjp(self.cot, self.acc, self.grad)
+            if self.pm is not None:          # the long-range half added onto both
+                self.pm.force_vjp(self.pos, self.mass, self.cot, acc=self.acc, grad=self.grad, accumulate=True)
         else:
             self.tree.force(self.acc)
+            if self.pm is not None:
+                self.pm.force(self.pos, self.mass, out=self.acc, accumulate=True)
 
     def replay(self):
         self.graph.replay()
