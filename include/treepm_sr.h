@@ -223,6 +223,14 @@ tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entrie
  * half the box, with eps > 0; not in chunked mode).  Creates the events on
  * first use (TP_ERR_CUDA if that fails).  enable = 0 stops the recording.   */
 tp_status tp_tree_set_kernel_timing(tp_tree *t, int32_t enable);
+/* Failure injection for tests (no counterpart in the paper): caps the node
+ * visits of every walk of later builds at `budget` (0 restores the default,
+ * n_nodes + 1, which a depth-first walk over skip pointers never exceeds).
+ * A walk that runs out ends its list there and latches TP_ERR_TIMEOUT,
+ * which tp_tree_status and the next call return; nothing waits or faults.
+ * budget < 0: TP_ERR_INVALID_ARG.                                           */
+tp_status tp_tree_set_walk_budget(tp_tree *t, int64_t budget);
+
 /* Durations in ms of those two launches in the last force and vjp calls made
  * with timing on; -1 for a call that recorded nothing (timing off, FP64 tree,
  * n = 0).  Synchronises on the events.  The events are recorded as external

@@ -63,6 +63,7 @@ SIGNATURES = {
     "tp_export_lists": ([_V, _V, _V], C.c_int),
     "tp_tree_free": ([_V], C.c_int),
     "tp_tree_set_tile": ([_V, _I32, _I32], C.c_int),
+    "tp_tree_set_walk_budget": ([_V, _I64], C.c_int),
     "tp_tree_set_kernel_timing": ([_V, _I32], C.c_int),
     "tp_tree_kernel_ms": ([_V, C.POINTER(_D), C.POINTER(_D)], C.c_int),
     "tp_axpy": ([_V, _V, _I32, _D, _I64, _V], C.c_int),

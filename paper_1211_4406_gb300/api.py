@@ -179,6 +179,11 @@ class ShortRangeTree:
                    "tp_tree_set_tile")
         self.tile = (int(fwd_particles), int(adj_entries))
 
+    def set_walk_budget(self, budget: int = 0) -> None:
+        """Failure injection: cap the node visits of every walk of later builds
+        (0 restores the default); a walk that runs out latches TP_ERR_TIMEOUT."""
+        _lib.check(_lib.load().tp_tree_set_walk_budget(self.handle, int(budget)), "tp_tree_set_walk_budget")
+
     def set_kernel_timing(self, enable: bool = True) -> None:
         _lib.check(_lib.load().tp_tree_set_kernel_timing(self.handle, 1 if enable else 0),
                    "tp_tree_set_kernel_timing")

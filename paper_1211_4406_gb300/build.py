@@ -34,7 +34,7 @@ def _sources() -> list[str]:
 
 
 def _deps() -> list[str]:
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [
+    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + [
         os.path.join(os.path.dirname(HERE), "include", "treepm_sr.h")]
 
 

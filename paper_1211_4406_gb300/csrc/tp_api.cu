@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "tp_common.cuh"
+#include "tp_nvtx.h"
 
 namespace tp {
 void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, uint64_t *key2,
@@ -444,6 +445,7 @@ static tp_status build_chunked(tp_tree *t, cudaStream_t s, int64_t budget)
 static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cudaStream_t s, bool sync)
 {
     TreeDev &D = t->D;
+    NvtxRange construction("tree construction");
     cudaMemsetAsync(D.status, 0, sizeof(int32_t), s);
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
@@ -476,6 +478,8 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     }
     TP_LAUNCH(k_clamp_groups, 1, 1, 0, s, D);
     tp::build_groups(D, t->flag, t->gofs, s);
+    construction.end();
+    NvtxRange traversal("tree traversal");
     // walk: top items per group, then subtree tasks, then the entries
     tp::walk_top_count(D, t->split, t->scan_tmp, s);
     if (!sync && t->chunked) {             // the next force/vjp call plans the windows
@@ -674,6 +678,7 @@ tp_status tp_refit_tree(tp_tree *t, const double *pos, const double *mass, void 
 
 tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
 {
+    NvtxRange range("force calculation");
     if (!t || (t->n > 0 && !is_device_ptr(acc))) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     t->last = s;
@@ -706,6 +711,7 @@ tp_status tp_short_range_force(tp_tree *t, void *acc, void *stream)
 
 tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *stream)
 {
+    NvtxRange range("force calculation (adjoint)");
     if (!t) return TP_ERR_INVALID_ARG;
     if (t->n > 0 && (!is_device_ptr(cot) || !is_device_ptr(grad))) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -739,6 +745,7 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
 
 tp_status tp_short_range_force_vjp(tp_tree *t, void *acc, const void *cot, double *grad, void *stream)
 {
+    NvtxRange range("force calculation (forward and adjoint)");
     if (!t) return TP_ERR_INVALID_ARG;
     if (t->n > 0 && (!is_device_ptr(acc) || !is_device_ptr(cot) || !is_device_ptr(grad)))
         return TP_ERR_INVALID_ARG;
@@ -889,6 +896,13 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries)
     if (e == TP_OK && st.n_entries > 0)
         e = cuda_status(cudaMemcpy(entries, t->D.ent, sizeof(int32_t) * st.n_entries, cudaMemcpyDeviceToHost));
     return e;
+}
+
+tp_status tp_tree_set_walk_budget(tp_tree *t, int64_t budget)
+{
+    if (!t || budget < 0) return TP_ERR_INVALID_ARG;
+    t->D.walk_budget = budget;
+    return TP_OK;
 }
 
 tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entries)

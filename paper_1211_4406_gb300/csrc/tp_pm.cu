@@ -25,6 +25,7 @@
 #include <new>
 
 #include "tp_common.cuh"
+#include "tp_nvtx.h"
 
 namespace {
 
@@ -452,6 +453,7 @@ static tp_status pm_need_umesh(tp_pm *pm)
 extern "C" tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
                                  int32_t accumulate, void *stream)
 {
+    NvtxRange range("PM");
     if (!pm || n < 0) return TP_ERR_INVALID_ARG;
     if (n == 0) return TP_OK;
     if (!is_dev(pos) || !is_dev(acc) || (mass && !is_dev(mass))) return TP_ERR_INVALID_ARG;
@@ -465,6 +467,7 @@ extern "C" tp_status tp_pm_force(tp_pm *pm, const double *pos, const double *mas
 extern "C" tp_status tp_pm_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, const float *cot,
                                double *grad, int32_t accumulate, void *stream)
 {
+    NvtxRange range("PM (adjoint)");
     if (!pm || n < 0) return TP_ERR_INVALID_ARG;
     if (n == 0) return TP_OK;
     if (!is_dev(pos) || !is_dev(cot) || !is_dev(grad) || (mass && !is_dev(mass))) return TP_ERR_INVALID_ARG;
@@ -480,6 +483,7 @@ extern "C" tp_status tp_pm_vjp(tp_pm *pm, const double *pos, const double *mass,
 extern "C" tp_status tp_pm_force_vjp(tp_pm *pm, const double *pos, const double *mass, int64_t n, float *acc,
                                      const float *cot, double *grad, int32_t accumulate, void *stream)
 {
+    NvtxRange range("PM (forward and adjoint)");
     if (!pm || n < 0) return TP_ERR_INVALID_ARG;
     if (n == 0) return TP_OK;
     if (!is_dev(pos) || !is_dev(acc) || !is_dev(cot) || !is_dev(grad) || (mass && !is_dev(mass)))

@@ -151,7 +151,8 @@ __device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start,
 {
     int32_t cnt = 0;
     int32_t nd = start;
-    int64_t budget = *T.n_nodes + 1;     // a preorder walk visits each node at most once
+    // a preorder walk visits each node at most once
+    int64_t budget = T.walk_budget > 0 ? T.walk_budget : *T.n_nodes + 1;
     while (nd >= 0) {
         if (--budget < 0 || nd >= T.cap_nodes) {
             tp_latch(T.status, TP_ERR_TIMEOUT);
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
                         pcur = pend = 0;
                         cnt = 0;
                         bound = T.ibound[it];
-                        budget = *T.n_nodes + 1;
+                        budget = T.walk_budget > 0 ? T.walk_budget : *T.n_nodes + 1;
                     }
                 } else {
                     exhausted = true;

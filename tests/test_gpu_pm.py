@@ -65,10 +65,11 @@ def test_pm_matches_oracle(name, pos, mass, n_mesh, G):
     assert mesh_rel(solver.export_mesh("acceleration"), np.stack(amesh, axis=-1)) <= 1e-5
     rms, mx = rel_err(acc, ref)
     assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
-    # accumulate adds onto what is there
+    # accumulate adds onto what is there; the two calls' FP32 atomic adds into
+    # the mass mesh land in different orders (measured up to 1.3e-6 of max|a|)
     base = torch.full((n, 3), 0.25, dtype=torch.float32, device="cuda")
     solver.force(p, m, out=base, accumulate=True)
-    assert np.abs(base.double().cpu().numpy() - 0.25 - acc).max() <= 1e-6 * max(np.abs(acc).max(), 1.0)
+    assert np.abs(base.double().cpu().numpy() - 0.25 - acc).max() <= 1e-5 * max(np.abs(acc).max(), 1.0)
     solver.close()
 
 
