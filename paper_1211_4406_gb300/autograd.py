@@ -299,7 +299,7 @@ def treepm_leapfrog(x0: torch.Tensor, v0: torch.Tensor, mass, params: Params, pm
     the same r_cut and G as params); returns (x_T, v_T, a_PP(x_T), a_PM(x_T)).
     Differentiable in x0 and v0 with one checkpoint per step.  The steps share
     one tree for the forward pass and two for the backward pass, rebuilt in
-    place."""
+    place.  refit needs whole lists (a tree in chunked mode refuses it)."""
     a_pp = short_range_force(x0, mass, params)
     a_pm = pm_force(x0, mass, pm)
     slots = (_TreeSlot(), _TreeSlot(), _TreeSlot())
