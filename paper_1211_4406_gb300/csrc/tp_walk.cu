@@ -272,44 +272,80 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
             }
         }
         if (__all_sync(full, exhausted)) break;
-        if (it < 0) continue;
-        if (pcur < pend) {                             // one or two particles of an opened leaf
-            int namb = 0;
-            const bool two = pcur + 1 < pend;
-            const bool k0 = keep_particle(T, W, pcur, namb);
-            const bool k1 = two && keep_particle(T, W, pcur + 1, namb);
-            if (k0) {
-                if (cnt < bound) out[cnt] = pcur;
-                cnt++;
+        if (it >= 0) {
+            if (nd == end || nd < 0 || --budget < 0 || nd >= T.cap_nodes) {
+                if (budget < 0 || (nd != end && nd >= T.cap_nodes)) tp_latch(T.status, TP_ERR_TIMEOUT);
+                if (cnt > bound) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+                T.icnt2[it] = cnt;
+                it = -1;
+            } else {                                   // one node decision
+                const WNode w = T.wn[nd];
+                int namb = 0;
+                const int d = decide_node(T, W, nd, w, namb);
+                ambig += namb;
+                if (d == kPrune) {
+                    nd = w.skip;
+                } else if (d == kAccept) {
+                    if (cnt < bound) out[cnt] = -(nd + 1);
+                    cnt++;
+                    nd = w.skip;
+                } else if (w.child < 0) {              // an opened leaf: its particles below
+                    pcur = w.first;
+                    pend = w.first + w.count;
+                    nd = w.skip;
+                } else {
+                    nd = w.child;
+                }
             }
-            if (k1) {
-                if (cnt < bound) out[cnt] = pcur + 1;
-                cnt++;
+        }
+        // The particles of the leaves opened above, tested by the whole warp,
+        // 32 at a time: lane k takes the k-th pending particle in lane order
+        // and its owner's group by shuffles; a ballot ranks the kept ones
+        // within each owner, which writes them in particle order after its
+        // entries so far (the list order of a lane-by-lane walk).
+        for (;;) {
+            const bool has = it >= 0 && pcur < pend;
+            if (!__ballot_sync(full, has)) break;
+            const int32_t mine = has ? pend - pcur : 0;
+            int32_t incl = mine;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += y;
             }
-            ambig += namb;
-            pcur += two ? 2 : 1;
-        } else if (nd == end || nd < 0 || --budget < 0 || nd >= T.cap_nodes) {
-            if (budget < 0 || (nd != end && nd >= T.cap_nodes)) tp_latch(T.status, TP_ERR_TIMEOUT);
-            if (cnt > bound) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
-            T.icnt2[it] = cnt;
-            it = -1;
-        } else {                                       // one node decision
-            const WNode w = T.wn[nd];
+            const int32_t start = incl - mine;
+            const int32_t total = __shfl_sync(full, incl, 31);
+            int j = 0;                                 // owner of slot `lane`: first lane with incl > lane
+            for (int st = 16; st > 0; st >>= 1)
+                if (__shfl_sync(full, incl, j + st - 1) <= lane) j += st;
+            j &= 31;
+            WalkGroup Wj;
+            Wj.gx = __shfl_sync(full, W.gx, j); Wj.gy = __shfl_sync(full, W.gy, j); Wj.gz = __shfl_sync(full, W.gz, j);
+            Wj.hx = __shfl_sync(full, W.hx, j); Wj.hy = __shfl_sync(full, W.hy, j); Wj.hz = __shfl_sync(full, W.hz, j);
+            Wj.g = __shfl_sync(full, W.g, j);
+            Wj.P = reinterpret_cast<const BoxPrm *>(
+                __shfl_sync(full, reinterpret_cast<unsigned long long>(W.P), j));
+            Wj.g0 = Wj.g1 = 0;
+            const int32_t sj = __shfl_sync(full, start, j), pj = __shfl_sync(full, pcur, j);
+            const int32_t cj = __shfl_sync(full, cnt, j), bj = __shfl_sync(full, bound, j);
+            int32_t *oj = reinterpret_cast<int32_t *>(
+                __shfl_sync(full, reinterpret_cast<unsigned long long>(out), j));
+            const bool tester = lane < total;
+            const int32_t p = pj + (lane - sj);
             int namb = 0;
-            const int d = decide_node(T, W, nd, w, namb);
+            const bool keep = tester && keep_particle(T, Wj, p, namb);
             ambig += namb;
-            if (d == kPrune) {
-                nd = w.skip;
-            } else if (d == kAccept) {
-                if (cnt < bound) out[cnt] = -(nd + 1);
-                cnt++;
-                nd = w.skip;
-            } else if (w.child < 0) {
-                pcur = w.first;
-                pend = w.first + w.count;
-                nd = w.skip;
-            } else {
-                nd = w.child;
+            const unsigned kept = __ballot_sync(full, keep);
+            if (keep) {
+                const unsigned lo = sj > 0 ? ~((1u << sj) - 1u) : full;
+                const int32_t pos = cj + __popc(kept & lo & below);
+                if (pos < bj) oj[pos] = p;
+            }
+            if (has && start < 32) {                   // this lane's share of the round
+                const int32_t e = incl < 32 ? incl : 32;
+                const unsigned hi = e >= 32 ? full : ((1u << e) - 1u);
+                const unsigned lo = ~((1u << start) - 1u);
+                cnt += __popc(kept & hi & lo);
+                pcur += e - start;
             }
         }
     }
