@@ -175,3 +175,16 @@ def test_captured_treepm_step_equals_direct_calls():
     assert float((grad - g_ref).abs().max()) <= 1e-4 * sg
     pm.close()
     tree.close()
+
+
+def test_single_particle_feels_no_pm_force():
+    """One particle anywhere: the TSC assignment and interpolation with the
+    antisymmetric four-point difference conserve momentum, so m a = 0."""
+    rng = np.random.default_rng(21)
+    s = PMSolver(16, 3 / 16, 1.0)
+    for _ in range(4):
+        p = torch.tensor(rng.random((1, 3)), device="cuda")
+        a = s.force(p, torch.ones(1, dtype=torch.float64, device="cuda")).double().cpu().numpy()
+        # scale: the force of a unit mass at one mesh spacing, G m / h^2 = 256
+        assert np.abs(a).max() <= 1e-5 * 256.0, a
+    s.close()
