@@ -138,7 +138,7 @@ struct tp_tree {
     cudaStream_t last = nullptr;
     // allocations: base (particles, workspace), nodes, groups, walk items, lists
     Pool base, nodes, groups, items, pad, lists;
-    int32_t split = 512;              // largest subtree a single walk task expands
+    int32_t split = 1024;             // largest subtree a single walk task expands
     TreeDev D;
     // scratch
     uint64_t *key2 = nullptr;
