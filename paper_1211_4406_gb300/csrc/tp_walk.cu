@@ -379,18 +379,31 @@ __global__ void k_compact(TreeDev T)
         const int64_t sbase = v ? T.ibpos[it] - (incl - cnt) : 0;
         const int32_t g = v ? T.igrp[it] : 0;
         const float sc = v ? T.box[T.gbox[g]].scale : 0.f;
-        for (int32_t k0 = 0; k0 < total; k0 += 32) {
-            const int32_t k = k0 + lane;
-            int j = 0;                                // lanes whose running count is <= k
-            for (int st = 16; st > 0; st >>= 1)
-                if (__shfl_sync(full, incl, j + st - 1) <= k) j += st;
-            const int64_t sb = __shfl_sync(full, sbase, j);
-            const int32_t gj = __shfl_sync(full, g, j);
-            const float scj = __shfl_sync(full, sc, j);
-            if (k < total) {
-                const int32_t e = T.pent[sb + k];
-                T.ent[out0 + k] = e;
-                T.rec[out0 + k] = entry_record(T, T.gX[gj], T.gY[gj], T.gZ[gj], scj, e);
+        // two entries per lane and round (k and k + 32), so that two chains of
+        // dependent loads (slot, then source record) are in flight at once
+        for (int32_t k0 = 0; k0 < total; k0 += 64) {
+            const int32_t ka = k0 + lane, kb = ka + 32;
+            int ja = 0, jb = 0;                       // lanes whose running count is <= k
+            for (int st = 16; st > 0; st >>= 1) {
+                const int32_t ya = __shfl_sync(full, incl, ja + st - 1);
+                const int32_t yb = __shfl_sync(full, incl, jb + st - 1);
+                if (ya <= ka) ja += st;
+                if (yb <= kb) jb += st;
+            }
+            jb &= 31;
+            const int64_t sba = __shfl_sync(full, sbase, ja), sbb = __shfl_sync(full, sbase, jb);
+            const int32_t ga = __shfl_sync(full, g, ja), gb = __shfl_sync(full, g, jb);
+            const float sca = __shfl_sync(full, sc, ja), scb = __shfl_sync(full, sc, jb);
+            const bool va = ka < total, vb = kb < total;
+            const int32_t ea = va ? T.pent[sba + ka] : 0;
+            const int32_t eb = vb ? T.pent[sbb + kb] : 0;
+            if (va) {
+                T.ent[out0 + ka] = ea;
+                T.rec[out0 + ka] = entry_record(T, T.gX[ga], T.gY[ga], T.gZ[ga], sca, ea);
+            }
+            if (vb) {
+                T.ent[out0 + kb] = eb;
+                T.rec[out0 + kb] = entry_record(T, T.gX[gb], T.gY[gb], T.gZ[gb], scb, eb);
             }
         }
     }
