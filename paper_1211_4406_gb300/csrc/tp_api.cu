@@ -448,6 +448,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     NvtxRange construction("tree construction");
     cudaMemsetAsync(D.status, 0, sizeof(int32_t), s);
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(D.n_general, 0xff, sizeof(unsigned long long), s);   // counted again by the LPT pass
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
     if (D.n > 0) {                            // the refit reference: this build's sorted positions
         cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
@@ -611,6 +612,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.n_items = B.get<int64_t>(1);
     D.n_pad = B.get<int64_t>(1);
     D.n_ambig = B.get<unsigned long long>(1);
+    D.n_general = B.get<unsigned long long>(1);
     D.status = B.get<int32_t>(1);
     t->queue = B.get<int32_t>(4);
     t->gs = B.get<double>(3 * nn);

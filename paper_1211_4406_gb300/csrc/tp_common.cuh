@@ -114,6 +114,7 @@ struct TreeDev {
                                       // scaled by 2/r_cut (FP32 x, y, z) and mass (w)
     int64_t *n_entries;               // device scalar
     unsigned long long *n_ambig;      // device scalar
+    unsigned long long *n_general;    // device scalar: groups the general FP32 pair kernels take
     int32_t *status;                  // first latched error
 };
 

@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
     __shared__ JTile<R> J;
     __shared__ double red[3][kThreads];
     __shared__ int s_item;
+    if (sizeof(R) == 4 && *T.n_general == 0) return;     // every group went to the packed kernel
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     for (int64_t item = next_item<QUEUE>(queue, -1, &s_item); item < G_n;
@@ -575,6 +576,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
     __shared__ uint64_t iX[kThreads], iY[kThreads], iZ[kThreads];
     __shared__ R part[kThreads / 32][4][kThreads];   // per-warp i-side sums of one tile
     __shared__ int s_item;
+    if (sizeof(R) == 4 && *T.n_general == 0) return;     // every group went to the packed kernel
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

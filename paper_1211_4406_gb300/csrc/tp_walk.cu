@@ -441,6 +441,13 @@ __global__ void k_lpt_keys(TreeDev T, uint64_t *key, uint32_t *val)
         }
         key[g] = g < G ? 0xffffffffull - cost : 0xffffffffull + 1;   // padding sorts last
         val[g] = (uint32_t)g;
+        if (g < G) {
+            // groups whose pairs the packed FP32 kernels leave to the general ones:
+            // offsets that may need the minimum image per pair, or eps = 0
+            const BoxPrm &P = T.box[T.gbox[g]];
+            const double hm = fmax(T.ghx[g], fmax(T.ghy[g], T.ghz[g]));
+            if (2.0 * hm + P.rcut >= 0.5 - 1e-9 || !(P.eps2s > 0.f)) atomicAdd(T.n_general, 1ull);
+        }
     }
 }
 
@@ -537,6 +544,7 @@ void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_
                void *radix_tmp, cudaStream_t s)
 {
     if (T.cap_groups <= 0) return;
+    cudaMemsetAsync(T.n_general, 0, sizeof(unsigned long long), s);
     TP_LAUNCH(k_lpt_keys, grid_for(T.cap_groups, 256), 256, 0, s, T, key, val);
     radix_sort(key, val, key2, val2, T.cap_groups, 40, nullptr, 1, radix_tmp, s);
 }
