@@ -395,7 +395,7 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     def roofline(kernel, ms, flops, note):
         ach = flops * inter / (ms * 1e-3)
         return {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic_for(kernel, box.n), "kernel": f"{kernel} ({note})",
+                "frac": ach / fp32_peak, "traffic": traffic_for(kernel, box.n, wl), "kernel": f"{kernel} ({note})",
                 "ms_per_launch": ms, "flops_per_interaction": flops, "peak_basis": peak_basis}
 
     kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)

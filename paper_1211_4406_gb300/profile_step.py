@@ -70,7 +70,8 @@ def record_traffic(csv_path: str, n: int) -> dict:
         k["launches"] += 1
         k["dram_bytes"] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
         k["ns"] += d.get("gpu__time_duration.sum", 0.0)
-    rec = {"n": n, "digest": kernel_source_digest(),
+    rec = {"workload": "clustered-2M" if n == 128 ** 3 else f"clustered-{n}", "n": n,
+           "digest": kernel_source_digest(),
            "kernels": {k: {"bytes_per_launch": v["dram_bytes"] / v["launches"],
                            "ncu_ms_per_launch": v["ns"] / v["launches"] / 1e6}
                        for k, v in out.items()},
@@ -84,15 +85,16 @@ def record_traffic(csv_path: str, n: int) -> dict:
     return rec
 
 
-def traffic_for(kernel: str, n: int):
+def traffic_for(kernel: str, n: int, workload: str = "clustered-2M"):
     """DRAM bytes per launch of `kernel` (its name with template arguments, as
-    ncu prints it) at particle count n, or None when no capture exists for n
-    or the device code has changed since it was taken."""
+    ncu prints it) on `workload` at particle count n, or None when no capture
+    exists for that workload and n or the device code has changed since it
+    was taken."""
     try:
         rec = json.load(open(TRAFFIC_JSON))
     except (OSError, ValueError):
         return None
-    if rec.get("n") != n or rec.get("digest") != kernel_source_digest():
+    if rec.get("n") != n or rec.get("workload") != workload or rec.get("digest") != kernel_source_digest():
         return None
     k = rec.get("kernels", {}).get(kernel_key(kernel))
     return None if k is None else k.get("bytes_per_launch")
