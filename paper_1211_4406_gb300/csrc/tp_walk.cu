@@ -223,9 +223,9 @@ __global__ void k_item_bounds(TreeDev T)
 // Each lane expands one item at a time by a stackless depth-first walk of the
 // task's subtree and takes its next item from a global counter as soon as it
 // is done, so lanes with short tasks do not wait for the warp's longest one.
-// Every loop iteration does one unit of work -- one node decision, or the
-// tests of the next two particles of an opened leaf -- so lanes at different
-// stages of their walks diverge by at most one branch per iteration.
+// Every loop iteration makes one node decision per lane; the particles of the
+// leaves opened in it are then tested by the whole warp, 32 per round (see
+// below), so particle tests do not wait on the lanes that own them.
 __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long long *counter)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
