@@ -177,25 +177,28 @@ __global__ void k_split_count(TreeDev T, int L, uint32_t *nch, int32_t *cb)
     }
 }
 
-__global__ void k_level_finish(TreeDev T, int L)
-{
-    if (blockIdx.x || threadIdx.x) return;
-    const int64_t next = T.lstart[L] + T.lcount[L];
-    T.lstart[L + 1] = next;
-    if (next + T.lcount[L + 1] > T.cap_nodes) {
-        tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
-        T.lcount[L + 1] = 0;
-    }
-    *T.n_nodes = T.lstart[L + 1] + T.lcount[L + 1];
-}
-
 // a4 (write): children of level-L nodes at lstart[L+1] + scan offset, in
 // octant order; skip pointers make the breadth-first array walkable depth
-// first without a stack (next sibling, else the parent's skip).
+// first without a stack (next sibling, else the parent's skip).  Level L+1
+// starts right after level L; a level that would pass cap_nodes is dropped
+// whole (status TP_ERR_LIST_OVERFLOW).  Every thread derives the start and
+// the kept count itself; block 0 stores them.  Its zeroing of an overflowing
+// count may race with other blocks' reads, and either value they see gives
+// nnext = 0.
 __global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint32_t *ofs, const int32_t *cb)
 {
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
-    const int64_t nnext = T.lcount[L + 1], base0 = T.lstart[L + 1];
+    const int64_t base0 = s0 + nl, counted = T.lcount[L + 1];
+    const bool overflow = base0 + counted > T.cap_nodes;
+    const int64_t nnext = overflow ? 0 : counted;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        T.lstart[L + 1] = base0;
+        if (overflow) {
+            tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+            T.lcount[L + 1] = 0;
+        }
+        *T.n_nodes = base0 + nnext;
+    }
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = (int32_t)(s0 + t);
@@ -234,6 +237,20 @@ __global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint3
     }
 }
 
+// Order-preserving keys of finite doubles (negative values: all bits flipped;
+// others: the sign bit set), so that the tight boxes' min/max run as exact
+// integer comparisons instead of on the FP64 pipe.
+__device__ __forceinline__ uint64_t ord_key(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_value(uint64_t k)
+{
+    const uint64_t b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
 // a5: monopoles bottom-up in canonical order (leaf: particles in key order;
 // internal: children in octant order), tight boxes, fixed-point images and
 // the walk record.
@@ -244,8 +261,7 @@ __global__ void k_moments(TreeDev T, int L)
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = (int32_t)(s0 + t);
         double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-        double lx = INFINITY, ly = INFINITY, lz = INFINITY;
-        double hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        uint64_t klx = ~0ull, kly = ~0ull, klz = ~0ull, khx = 0ull, khy = 0ull, khz = 0ull;
         const int32_t nc = T.nchild[i];
         if (nc == 0) {
             const int32_t f = T.first[i], e = f + T.count[i];
@@ -255,8 +271,9 @@ __global__ void k_moments(TreeDev T, int L)
                 Sx = __dadd_rn(Sx, __dmul_rn(mp, xp));
                 Sy = __dadd_rn(Sy, __dmul_rn(mp, yp));
                 Sz = __dadd_rn(Sz, __dmul_rn(mp, zp));
-                lx = fmin(lx, xp); ly = fmin(ly, yp); lz = fmin(lz, zp);
-                hx = fmax(hx, xp); hy = fmax(hy, yp); hz = fmax(hz, zp);
+                const uint64_t kx = ord_key(xp), ky = ord_key(yp), kz = ord_key(zp);
+                klx = kx < klx ? kx : klx; kly = ky < kly ? ky : kly; klz = kz < klz ? kz : klz;
+                khx = kx > khx ? kx : khx; khy = ky > khy ? ky : khy; khz = kz > khz ? kz : khz;
             }
         } else {
             const int32_t c0 = T.child[i];
@@ -265,10 +282,14 @@ __global__ void k_moments(TreeDev T, int L)
                 Sx = __dadd_rn(Sx, T.Sx[c]);
                 Sy = __dadd_rn(Sy, T.Sy[c]);
                 Sz = __dadd_rn(Sz, T.Sz[c]);
-                lx = fmin(lx, T.lox[c]); ly = fmin(ly, T.loy[c]); lz = fmin(lz, T.loz[c]);
-                hx = fmax(hx, T.hix[c]); hy = fmax(hy, T.hiy[c]); hz = fmax(hz, T.hiz[c]);
+                const uint64_t ax = ord_key(T.lox[c]), ay = ord_key(T.loy[c]), az = ord_key(T.loz[c]);
+                const uint64_t bx = ord_key(T.hix[c]), by = ord_key(T.hiy[c]), bz = ord_key(T.hiz[c]);
+                klx = ax < klx ? ax : klx; kly = ay < kly ? ay : kly; klz = az < klz ? az : klz;
+                khx = bx > khx ? bx : khx; khy = by > khy ? by : khy; khz = bz > khz ? bz : khz;
             }
         }
+        double lx = ord_value(klx), ly = ord_value(kly), lz = ord_value(klz);
+        double hx = ord_value(khx), hy = ord_value(khy), hz = ord_value(khz);
         if (T.count[i] == 0) { lx = ly = lz = hx = hy = hz = 0.0; }
         T.M[i] = M; T.Sx[i] = Sx; T.Sy[i] = Sy; T.Sz[i] = Sz;
         T.lox[i] = lx; T.loy[i] = ly; T.loz[i] = lz;
@@ -422,7 +443,6 @@ void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void 
     for (int L = 0; L < TP_MAX_LEVEL; L++) {
         TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch, cb);
         scan_u32(nch, ofs, 0, T.lcount + L, T.lcount + L + 1, scan_tmp, s);
-        TP_LAUNCH(k_level_finish, 1, 32, 0, s, T, L);
         TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs, cb);
     }
     build_moments(T, s);

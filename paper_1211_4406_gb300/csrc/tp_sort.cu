@@ -46,29 +46,12 @@ __global__ void k_scan_reduce(const Tin *in, int64_t n_host, const int64_t *d_n,
     }
 }
 
-// One block: exclusive scan of nb partials in place; *total = their sum.
-template <class Tout>
-__global__ void k_scan_partials(Tout *partial, int nb, int64_t *total)
-{
-    __shared__ Tout buf[kScanBlocks];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) buf[i] = partial[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Tout run = 0;
-        for (int i = 0; i < nb; i++) {
-            Tout v = buf[i];
-            buf[i] = run;
-            run += v;
-        }
-        if (total) *total = (int64_t)run;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) partial[i] = buf[i];
-}
-
+// Each block first sums the partials of the blocks before it (its carry; the
+// last block also writes the grand total), then scans its own chunk.  Integer
+// sums, so the order of the additions does not change the result.
 template <class Tin, class Tout>
 __global__ void k_scan_apply(const Tin *in, Tout *out, int64_t n_host, const int64_t *d_n,
-                             const Tout *partial)
+                             const Tout *partial, int64_t *total)
 {
     __shared__ Tout warp_tot[32];
     const int64_t n = d_n ? *d_n : n_host;
@@ -77,7 +60,17 @@ __global__ void k_scan_apply(const Tin *in, Tout *out, int64_t n_host, const int
     const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    Tout carry = partial[blockIdx.x];
+    Tout c = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += blockDim.x) c += partial[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) warp_tot[warp] = c;
+    __syncthreads();
+    Tout carry = 0;
+    for (int w = 0; w < nw; w++) carry += warp_tot[w];
+    __syncthreads();
+    if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1)
+        *total = (int64_t)(carry + partial[blockIdx.x]);
     for (int64_t base = b0; base < b1; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         Tout v = i < b1 ? (Tout)in[i] : Tout(0);
@@ -103,11 +96,9 @@ void scan_impl(const Tin *in, Tout *out, int64_t n_host, const int64_t *d_n, int
 {
     Tout *partial = reinterpret_cast<Tout *>(tmp);
     auto reduce = k_scan_reduce<Tin, Tout>;
-    auto partials = k_scan_partials<Tout>;
     auto apply = k_scan_apply<Tin, Tout>;
     TP_LAUNCH(reduce, kScanBlocks, kScanThreads, 0, s, in, n_host, d_n, partial);
-    TP_LAUNCH(partials, 1, 256, 0, s, partial, kScanBlocks, total);
-    TP_LAUNCH(apply, kScanBlocks, kScanThreads, 0, s, in, out, n_host, d_n, (const Tout *)partial);
+    TP_LAUNCH(apply, kScanBlocks, kScanThreads, 0, s, in, out, n_host, d_n, (const Tout *)partial, total);
 }
 
 // ------------------------------------------------------------------------
