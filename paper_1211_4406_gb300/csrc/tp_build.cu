@@ -239,7 +239,9 @@ __global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint3
 
 // Order-preserving keys of finite doubles (negative values: all bits flipped;
 // others: the sign bit set), so that the tight boxes' min/max run as exact
-// integer comparisons instead of on the FP64 pipe.
+// integer comparisons instead of on the FP64 pipe.  They order -0.0 below
+// +0.0, but wrapped coordinates are never -0.0 (x - floor(x) rounds an exact
+// zero to +0.0), so the result is the comparison min/max bit for bit.
 __device__ __forceinline__ uint64_t ord_key(double x)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
