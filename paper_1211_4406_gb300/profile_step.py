@@ -50,11 +50,22 @@ def kernel_source_digest() -> str:
     return h.hexdigest()
 
 
-def record_traffic(csv_path: str, n: int) -> dict:
+# ncu's metric units, as multiples of a byte or a nanosecond
+UNIT_SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+              "ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6,
+              "s": 1e9, "second": 1e9}
+
+
+def record_traffic(csv_path: str, n: int, out_path: str | None = None) -> dict:
+    """Per-launch DRAM bytes and ncu time of the pair kernels from an ncu CSV
+    (one row per launch and metric), written to `out_path` (default: the
+    committed traffic record).  Values are scaled by their unit column; an
+    unknown unit raises ValueError."""
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
     hdr = rows[hi]
     ki, mi, ni = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Name")
+    ui = hdr.index("Metric Unit") if "Metric Unit" in hdr else None
     per = {}
     for r in rows[hi + 1:]:
         if len(r) <= mi:
@@ -62,8 +73,11 @@ def record_traffic(csv_path: str, n: int) -> dict:
         name = kernel_key(r[ki].split("(")[0].replace("<unnamed>::", "").replace("void ", ""))
         if name.split("<")[0] not in TRAFFIC_KERNELS:
             continue
+        unit = r[ui] if ui is not None else ""
+        if unit and unit not in UNIT_SCALE:
+            raise ValueError(f"unknown ncu unit {unit!r} for {r[ni]}")
         d = per.setdefault((name, r[0]), {})
-        d[r[ni]] = float(r[mi].replace(",", ""))
+        d[r[ni]] = float(r[mi].replace(",", "")) * UNIT_SCALE.get(unit, 1.0)
     out = {}
     for (name, _), d in per.items():
         k = out.setdefault(name, {"launches": 0, "dram_bytes": 0.0, "ns": 0.0})
@@ -78,20 +92,21 @@ def record_traffic(csv_path: str, n: int) -> dict:
            "command": ("ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
                        "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused\" -c 3 --csv --log-file "
                        f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1 --what all")}
-    os.makedirs(os.path.dirname(TRAFFIC_JSON), exist_ok=True)
-    with open(TRAFFIC_JSON, "w") as f:
+    out_path = out_path or TRAFFIC_JSON
+    os.makedirs(os.path.dirname(out_path), exist_ok=True)
+    with open(out_path, "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
     return rec
 
 
-def traffic_for(kernel: str, n: int, workload: str = "clustered-2M"):
+def traffic_for(kernel: str, n: int, workload: str = "clustered-2M", path: str | None = None):
     """DRAM bytes per launch of `kernel` (its name with template arguments, as
     ncu prints it) on `workload` at particle count n, or None when no capture
     exists for that workload and n or the device code has changed since it
     was taken."""
     try:
-        rec = json.load(open(TRAFFIC_JSON))
+        rec = json.load(open(path or TRAFFIC_JSON))
     except (OSError, ValueError):
         return None
     if rec.get("n") != n or rec.get("workload") != workload or rec.get("digest") != kernel_source_digest():
