@@ -161,7 +161,7 @@ def whole_job_rate(world, units_per_step, steps, total_ms):
 # ---------------------------------------------------------------------------
 # the reference arm: the CPU FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None):
+def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None, xi_softened=False):
     """Time the oracle: build + lists once, then `steps` samples of forward +
     adjoint over a contiguous range of groups holding ~target_fraction of the
     interactions.  Each step is charged its share of the build + lists time."""
@@ -181,8 +181,8 @@ def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=N
     times = []
     for s in range(warmup + steps):
         t0 = time.perf_counter()
-        ot.list_forces_range(0, g1, box.G, box.eps, box.r_cut)
-        ot.list_vjp_range(0, g1, box.G, box.eps, box.r_cut, w64)
+        ot.list_forces_range(0, g1, box.G, box.eps, box.r_cut, xi_softened=xi_softened)
+        ot.list_vjp_range(0, g1, box.G, box.eps, box.r_cut, w64, xi_softened=xi_softened)
         dt = time.perf_counter() - t0 + frac * t_build
         if s >= warmup:
             times.append(dt)
@@ -200,13 +200,16 @@ def run_reference(args, rank, world):
     from paper_1211_4406_gb300 import inputs
     box = inputs.config_box(CONFIG_K)
     w = inputs.cotangent(box.n, box.seed + 7)
-    r = oracle_sample_rate(box, w, steps=args.steps, warmup=args.warmup)
+    r = oracle_sample_rate(box, w, steps=args.steps, warmup=args.warmup,
+                           xi_softened=getattr(args, "xi", "plain") == "softened")
     total_t = sum(r["times"])
     value = r["per_step_interactions"] * len(r["times"]) / total_t
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(r["times"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference", "config": workload_config(),
+            "data": "synthetic", "impl": "reference",
+            "config": dict(workload_config(), **({} if getattr(args, "xi", "plain") == "plain" else
+                                                 {"xi": "softened: cutoff argument 2 sqrt(r^2+eps^2)/r_cut"})),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -440,7 +443,7 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
                                     "n_ambiguous", "mean_ni", "mean_nj", "max_nj")},
     }
     if world == 1 and not args.no_cpu_baseline and not paper_regime:
-        r = oracle_sample_rate(box, w, steps=1)
+        r = oracle_sample_rate(box, w, steps=1, xi_softened=args.xi == "softened")
         line["cpu_baseline"] = {"value": r["per_step_interactions"] / r["times"][0], "unit": UNIT,
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
     tree.close()
@@ -1021,6 +1024,8 @@ def main():
                     help="cutoff argument of Eq. 3 for clustered-2M and paper-regime-2M: plain r (default) "
                          "or the softened sqrt(r^2+eps^2) of the paper's kernel")
     args = ap.parse_args()
+    if args.xi != "plain" and args.workload not in ("clustered-2M", "paper-regime-2M"):
+        ap.error(f"--xi {args.xi} applies to the clustered-2M and paper-regime-2M workloads only")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -12,6 +12,7 @@ and cached under a caller-given key.
 """
 from __future__ import annotations
 
+import dataclasses
 import json
 import math
 import os
@@ -33,8 +34,15 @@ def gpu_key() -> str:
     return f"{p.name}|{p.multi_processor_count}"
 
 
-def bucket_key(n: int, kind: str) -> str:
-    return f"{gpu_key()}|n2^{int(round(math.log2(max(n, 1))))}|{kind}"
+def bucket_key(n: int, kind: str, params: Params | None = None) -> str:
+    """Tuning bucket of a box: GPU, size to the nearest power of two, kind,
+    and the kernel variant where it is not the default (FP32, plain xi)."""
+    key = f"{gpu_key()}|n2^{int(round(math.log2(max(n, 1))))}|{kind}"
+    if params is not None and params.precision != "fp32":
+        key += f"|{params.precision}"
+    if params is not None and params.xi != "plain":
+        key += f"|xi-{params.xi}"
+    return key
 
 
 def load_cache(path: str) -> dict:
@@ -77,7 +85,7 @@ def time_step(pos, mass, params: Params, cot, reps: int = 3) -> float:
 def tune_box(pos, mass, base: Params, cot, candidates=CANDIDATES, reps: int = 3) -> tuple[int, dict]:
     times = {}
     for c in candidates:
-        p = Params(base.G, base.eps, base.r_cut, base.theta, c, base.n_leaf, base.precision)
+        p = dataclasses.replace(base, n_crit=c)     # every other field (precision, xi, chunked) kept
         times[c] = time_step(pos, mass, p, cot, reps)
     best = min(times, key=times.get)
     return best, times
@@ -90,7 +98,7 @@ def tune_boxes(boxes, kinds, base_params, cache_path: str | None = None, candida
     cache = load_cache(cache_path)
     out = []
     for box, kind, prm in zip(boxes, kinds, base_params):
-        key = bucket_key(box.n, kind)
+        key = bucket_key(box.n, kind, prm)
         if key not in cache:
             pos = torch.tensor(box.pos, device=device)
             mass = torch.tensor(box.mass, device=device)
