@@ -31,6 +31,34 @@ def _dev_f64(x: torch.Tensor, shape_last=None) -> torch.Tensor:
     return x
 
 
+def _dev_mass(mass, n: int):
+    """Masses as a float64 CUDA tensor [n], or None (every mass 1/n).  The
+    library reads n values, so the length is checked here."""
+    if mass is None:
+        return None
+    mass = _dev_f64(mass)
+    if mass.dim() != 1 or mass.shape[0] != n:
+        raise ValueError(f"mass must be a float64 CUDA tensor [n] with n = {n}")
+    return mass
+
+
+def _dev_vec3(x, n: int, dtype, name: str) -> torch.Tensor:
+    """A contiguous CUDA buffer [n, 3] of `dtype` that the library reads or
+    writes in full."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != dtype or not x.is_contiguous() \
+            or tuple(x.shape) != (n, 3):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor [n, 3] with n = {n}")
+    return x
+
+
+def _dev_cot(cot, n: int, dtype) -> torch.Tensor:
+    """A cotangent dL/da [n, 3] (any float dtype, converted to `dtype`)."""
+    if not isinstance(cot, torch.Tensor) or not cot.is_cuda or not cot.is_floating_point() \
+            or tuple(cot.shape) != (n, 3):
+        raise ValueError(f"cot must be a floating-point CUDA tensor [n, 3] with n = {n}")
+    return cot.to(dtype).contiguous()
+
+
 @dataclass
 class Params:
     """Short-range parameters of one periodic unit box (Sec. II, III-A)."""
@@ -62,9 +90,8 @@ class ShortRangeTree:
                  box_offsets=None, stream=None):
         lib = _lib.load()
         pos = _dev_f64(pos, 3)
-        if mass is not None:
-            mass = _dev_f64(mass)
         self.n = int(pos.shape[0])
+        mass = _dev_mass(mass, self.n)
         if isinstance(params, Params):
             params = [params]
         params = list(params)
@@ -111,6 +138,7 @@ class ShortRangeTree:
         pos = _dev_f64(pos, 3)
         if pos.shape[0] != self.n:
             raise ValueError("rebuild needs the same particle count")
+        mass = _dev_mass(mass, self.n)
         self._pos, self._mass = pos, mass
         code = _lib.load().tp_rebuild_tree(self.handle, C.c_void_p(pos.data_ptr()),
                                            C.c_void_p(mass.data_ptr()) if mass is not None else None,
@@ -123,8 +151,7 @@ class ShortRangeTree:
         pos = _dev_f64(pos, 3)
         if pos.shape[0] != self.n:
             raise ValueError("refit needs the same particle count")
-        if mass is not None:
-            mass = _dev_f64(mass)
+        mass = _dev_mass(mass, self.n)
         self._pos, self._mass = pos, mass
         code = _lib.load().tp_refit_tree(self.handle, C.c_void_p(pos.data_ptr()),
                                          C.c_void_p(mass.data_ptr()) if mass is not None else None,
@@ -135,17 +162,17 @@ class ShortRangeTree:
         """Short-range accelerations (Eq. 2), [n, 3] in input order."""
         if out is None:
             out = torch.empty((self.n, 3), dtype=self.acc_dtype, device=self._pos.device)
-        if out.dtype != self.acc_dtype or not out.is_contiguous() or tuple(out.shape) != (self.n, 3):
-            raise ValueError("out must be a contiguous [n,3] tensor of the tree's precision")
+        _dev_vec3(out, self.n, self.acc_dtype, "out (the tree's precision)")
         code = _lib.load().tp_short_range_force(self.handle, C.c_void_p(out.data_ptr()), _stream(stream))
         _lib.check(code, "tp_short_range_force")
         return out
 
     def vjp(self, cot: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """dL/dx (float64 [n,3]) for the cotangent dL/da of the force."""
-        cot = cot.to(self.acc_dtype).contiguous()
+        cot = _dev_cot(cot, self.n, self.acc_dtype)
         if out is None:
             out = torch.empty((self.n, 3), dtype=torch.float64, device=self._pos.device)
+        _dev_vec3(out, self.n, torch.float64, "out")
         code = _lib.load().tp_short_range_vjp(self.handle, C.c_void_p(cot.data_ptr()),
                                               C.c_void_p(out.data_ptr()), _stream(stream))
         _lib.check(code, "tp_short_range_vjp")
@@ -154,14 +181,14 @@ class ShortRangeTree:
     def force_vjp(self, cot: torch.Tensor, acc: torch.Tensor | None = None, grad: torch.Tensor | None = None,
                   stream=None) -> tuple[torch.Tensor, torch.Tensor]:
         """(forces, dL/dx) in one pass over the lists, for a cotangent known in advance."""
-        cot = cot.to(self.acc_dtype).contiguous()
+        cot = _dev_cot(cot, self.n, self.acc_dtype)
         dev = self._pos.device
         if acc is None:
             acc = torch.empty((self.n, 3), dtype=self.acc_dtype, device=dev)
         if grad is None:
             grad = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
-        if acc.dtype != self.acc_dtype or not acc.is_contiguous() or tuple(acc.shape) != (self.n, 3):
-            raise ValueError("acc must be a contiguous [n,3] tensor of the tree's precision")
+        _dev_vec3(acc, self.n, self.acc_dtype, "acc (the tree's precision)")
+        _dev_vec3(grad, self.n, torch.float64, "grad")
         code = _lib.load().tp_short_range_force_vjp(self.handle, C.c_void_p(acc.data_ptr()),
                                                     C.c_void_p(cot.data_ptr()), C.c_void_p(grad.data_ptr()),
                                                     _stream(stream))
@@ -266,15 +293,13 @@ class PMSolver:
         if self._h is None:
             raise RuntimeError("PM solver has been freed")
         pos = _dev_f64(pos, 3)
-        if mass is not None:
-            mass = _dev_f64(mass)
         n = int(pos.shape[0])
+        mass = _dev_mass(mass, n)
         if out is None:
             if accumulate:
                 raise ValueError("accumulate needs out")
             out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
-        if out.dtype != torch.float32 or not out.is_contiguous() or tuple(out.shape) != (n, 3):
-            raise ValueError("out must be a contiguous float32 [n,3] tensor")
+        _dev_vec3(out, n, torch.float32, "out")
         code = _lib.load().tp_pm_force(self._h, C.c_void_p(pos.data_ptr()),
                                        C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
                                        C.c_void_p(out.data_ptr()), int(bool(accumulate)), _stream(stream))
@@ -303,8 +328,7 @@ class PMSolver:
             if accumulate:
                 raise ValueError("accumulate needs acc")
             acc = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
-        if acc.dtype != torch.float32 or not acc.is_contiguous() or tuple(acc.shape) != (n, 3):
-            raise ValueError("acc must be a contiguous float32 [n,3] tensor")
+        _dev_vec3(acc, n, torch.float32, "acc")
         code = _lib.load().tp_pm_force_vjp(self._h, C.c_void_p(pos.data_ptr()),
                                            C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
                                            C.c_void_p(acc.data_ptr()), C.c_void_p(cot.data_ptr()),
@@ -316,9 +340,8 @@ class PMSolver:
         if self._h is None:
             raise RuntimeError("PM solver has been freed")
         pos = _dev_f64(pos, 3)
-        if mass is not None:
-            mass = _dev_f64(mass)
         n = int(pos.shape[0])
+        mass = _dev_mass(mass, n)
         if not isinstance(cot, torch.Tensor) or not cot.is_cuda or cot.dtype != torch.float32 \
                 or tuple(cot.shape) != (n, 3):
             raise ValueError("cot must be a float32 CUDA tensor [n,3]")
@@ -327,8 +350,7 @@ class PMSolver:
             if accumulate:
                 raise ValueError("accumulate needs out")
             out = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
-        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != (n, 3):
-            raise ValueError("out must be a contiguous float64 [n,3] tensor")
+        _dev_vec3(out, n, torch.float64, "out")
         return pos, mass, cot, out
 
     def export_mesh(self, which: str = "potential") -> np.ndarray:
@@ -354,16 +376,28 @@ def short_range_force(pos: torch.Tensor, mass: torch.Tensor | None, params: Para
 
 
 def axpy(y: torch.Tensor, x: torch.Tensor, a: float, stream=None) -> None:
-    """y += a * x in the library (y float64; x float32 or float64)."""
+    """y += a * x in the library (y float64; x float32 or float64, as many
+    elements as y; both contiguous CUDA tensors)."""
+    if not (isinstance(y, torch.Tensor) and isinstance(x, torch.Tensor) and y.is_cuda and x.is_cuda):
+        raise TypeError("x and y must be CUDA tensors")
     if y.dtype != torch.float64 or not y.is_contiguous() or not x.is_contiguous():
         raise TypeError("y must be contiguous float64, x contiguous")
+    if x.dtype not in (torch.float32, torch.float64) or x.numel() != y.numel():
+        raise ValueError("x must be float32 or float64 with as many elements as y")
     code = _lib.load().tp_axpy(C.c_void_p(y.data_ptr()), C.c_void_p(x.data_ptr()),
                                1 if x.dtype == torch.float32 else 0, float(a), y.numel(), _stream(stream))
     _lib.check(code, "tp_axpy")
 
 
 def scale(out: torch.Tensor, x: torch.Tensor, a: float, stream=None) -> None:
-    """out = a * x in the library (x float64; out float32 or float64)."""
+    """out = a * x in the library (x float64; out float32 or float64, as many
+    elements as x; both contiguous CUDA tensors)."""
+    if not (isinstance(out, torch.Tensor) and isinstance(x, torch.Tensor) and out.is_cuda and x.is_cuda):
+        raise TypeError("out and x must be CUDA tensors")
+    if x.dtype != torch.float64 or not x.is_contiguous() or not out.is_contiguous():
+        raise TypeError("x must be contiguous float64, out contiguous")
+    if out.dtype not in (torch.float32, torch.float64) or out.numel() != x.numel():
+        raise ValueError("out must be float32 or float64 with as many elements as x")
     code = _lib.load().tp_scale(C.c_void_p(out.data_ptr()), 1 if out.dtype == torch.float32 else 0,
                                 C.c_void_p(x.data_ptr()), float(a), x.numel(), _stream(stream))
     _lib.check(code, "tp_scale")
