@@ -205,6 +205,10 @@ tp_status tp_export_groups(tp_tree *t, int64_t *ints, double *dbl);
  * index), < 0 a node -(id+1); each group's list in depth-first order.       */
 tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries);
 
+/* Releases the tree and all its device memory.  Synchronises the stream of
+ * the tree's last call first, so work still in flight finishes; clears any
+ * pending CUDA error.  The handle is invalid afterwards; NULL is a no-op.
+ * Always TP_OK.                                                             */
 tp_status tp_tree_free(tp_tree *t);
 
 /* Tile shape of the FP32 pair kernels, a tuning knob with no counterpart in
@@ -348,6 +352,8 @@ tp_status tp_measure_peak(int32_t kind, double *flops, void *stream);
 /* Number of kernels this library launched since it was loaded.             */
 int64_t tp_launch_count(void);
 
+/* A static, NUL-terminated English description of s ("unknown status" for a
+ * value outside the enum); never NULL, never to be freed; no GPU needed.   */
 const char *tp_status_string(tp_status s);
 
 #ifdef __cplusplus
