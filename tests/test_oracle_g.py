@@ -200,3 +200,19 @@ def test_tidal_trace_closed_form():
     d = np.array([1e-4, 0, 0])
     tr0 = sum(oracle.pair_jw(d, 1.0, np.eye(3)[k], 1.0, 0.0, rc)[k] for k in range(3))
     assert abs(tr0 / (-192 / (5 * rc ** 3)) - 1) < 1e-3
+
+
+@pytest.mark.parametrize("xi", [False, True])
+def test_pair_is_odd_and_its_jacobian_even(xi):
+    """a(-d) = -a(d) and J(-d) = J(d), bit for bit (r, g and s depend on |d|
+    only; the minimum image commutes with negation)."""
+    rng = np.random.default_rng(8)
+    for _ in range(40):
+        d = rng.normal(size=3)
+        d *= rng.uniform(1e-3, 0.19) / np.linalg.norm(d)
+        d += rng.integers(-2, 3, size=3)                # far images of the same offset
+        w = rng.normal(size=3)
+        a, b = oracle.pair(d, 0.7, 1.3, 2e-3, 0.2, xi), oracle.pair(-d, 0.7, 1.3, 2e-3, 0.2, xi)
+        assert np.array_equal(a, -b)
+        assert np.array_equal(oracle.pair_jw(d, 0.7, w, 1.3, 2e-3, 0.2, xi),
+                              oracle.pair_jw(-d, 0.7, w, 1.3, 2e-3, 0.2, xi))

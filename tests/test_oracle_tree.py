@@ -329,3 +329,34 @@ def test_leapfrog_adjoint_matches_frozen_central_differences():
         lm = np.sum(w * oracle.leapfrog_frozen(m, v0, trees, G, eps, rc, dt, steps)[2])
         fd = (lp - lm) / (2 * h)
         assert abs(gx[k, c] - fd) <= 1e-6 * max(abs(fd), rms)
+
+
+@pytest.mark.parametrize("theta,rc", [(0.0, 2.3 / 16), (0.5, 0.49)])
+def test_lattice_lists_are_translates_of_one_another(theta, rc):
+    """On a 16^3 lattice (coordinates multiples of 1/32, so every offset, gap
+    and centre of mass is exact) with 2x2x2 leaves as groups, every group is a
+    translate of every other: its list, as a set of minimum-image offsets from
+    the group centre (particles and node centres of mass), must be the same
+    set.  A sign or minimum-image mistake near a face breaks this."""
+    side = 16
+    pos, mass = inputs.lattice_box(side)
+    ot = oracle.OracleTree(pos, mass, 8, 8)
+    ot.lists(rc, theta)                               # r_cut^2 is no sum of squares of k/32: no ties
+    ex = ot.export()
+    assert ex.gfirst.size == side ** 3 // 8 and np.all(ex.gcount == 8)
+    sorted_pos = pos[ex.perm]
+    ref = None
+    for g in range(ex.gfirst.size):
+        e = ex.ent[ex.loff[g]:ex.loff[g + 1]]
+        src = np.where((e >= 0)[:, None], sorted_pos[np.maximum(e, 0)], ex.com[np.maximum(-e - 1, 0)])
+        d = src - ex.gcen[g]
+        d -= np.round(d)
+        key = np.concatenate([d * 32.0, (e < 0)[:, None]], axis=1)
+        key = key[np.lexsort(key.T[::-1])]
+        if ref is None:
+            ref = key
+            # theta = 0 opens every node; at r_cut = 0.49, theta = 0.5 accepts leaves whose
+            # gap exceeds 2 l = 0.25 and whose farthest point stays inside r_cut
+            assert (theta == 0.0) == bool(np.all(e >= 0))
+        else:
+            assert key.shape == ref.shape and np.array_equal(key, ref), g
