@@ -73,6 +73,8 @@ def _load():
                                          C.c_double, _D, C.c_int]
     lib.or_list_vjp_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                       C.c_double, _D, _D, C.c_int]
+    lib.or_count_useful.restype = C.c_int64
+    lib.or_count_useful.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
     lib.or_refresh_moments.argtypes = [C.c_void_p, _D]
     lib.or_sizes.argtypes = [C.c_void_p, _I64]
     lib.or_export_keys.argtypes = [C.c_void_p, _U64, _I64]
@@ -264,6 +266,14 @@ class OracleTree:
         _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad),
                                   int(xi_softened))
         return grad
+
+    def count_useful(self, eps, rcut, xi_softened=False) -> int:
+        """Pairs (group particle, list entry other than itself) at a positive
+        distance whose cutoff distance (r, or sqrt(r^2 + eps^2) with
+        xi_softened) is below r_cut: the evaluated pairs whose Eq. 2 term is not
+        identically zero."""
+        assert self.has_lists
+        return int(_load().or_count_useful(self._h, eps, rcut, int(xi_softened)))
 
     def refresh(self, pos) -> None:
         """Re-take monopoles from new positions with the structure frozen."""

@@ -23,6 +23,7 @@
  *                       opening criterion theta (Sec. I and II)
  *   or_list_forces      Eq. 2 over each group's list (nodes as monopoles)
  *   or_list_vjp         the vector-Jacobian product of or_list_forces
+ *   or_count_useful     how many evaluated pairs lie inside the cutoff
  *
  * Readings where the paper is silent (every one is listed in the design notes):
  *   - softening: 1/|r|^3 -> 1/(r^2+eps^2)^{3/2}; the cutoff argument uses the
@@ -678,6 +679,38 @@ void or_list_forces(const or_tree *t, double G, double eps, double rcut, double 
                     int xi_soft)
 {
     or_list_forces_range(t, 0, t->n_groups, G, eps, rcut, acc, xi_soft);
+}
+
+/* Pairs of the lists whose Eq. 2 term is not identically zero: over every
+ * group, every member particle i and every list entry (particle or monopole)
+ * other than i itself, count the pair when its distance r is positive and its
+ * cutoff distance -- r, or s = sqrt(r^2 + eps^2) in the softened-xi variant --
+ * is below r_cut (Eq. 3 vanishes at and beyond the cutoff).  The sum over
+ * groups of n_i * n_j counts every evaluated pair; this counts the useful ones
+ * among them.  The decision is taken in FP64 exactly as pair_acc takes it. */
+int64_t or_count_useful(const or_tree *t, double eps, double rcut, int xi_soft)
+{
+    or_prm P = make_prm_xi(1.0, eps, rcut, xi_soft);
+    int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : total)
+    for (int64_t g = 0; g < t->n_groups; g++) {
+        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            for (int64_t q = t->loff[g]; q < t->loff[g + 1]; q++) {
+                int64_t e = t->ent[q];
+                if (e == i) continue;
+                double xj[3], mj;
+                entry_src(t, e, xj, &mj);
+                double dx = minimg(xj[0] - t->xb[0][i]);
+                double dy = minimg(xj[1] - t->xb[1][i]);
+                double dz = minimg(xj[2] - t->xb[2][i]);
+                double r2 = (dx * dx + dy * dy) + dz * dz;
+                if (r2 == 0.0) continue;
+                double c2 = P.soft ? r2 + P.eps2 : r2;
+                if (c2 < P.rc2) total++;
+            }
+        }
+    }
+    return total;
 }
 
 /* Vector-Jacobian product of or_list_forces for fixed lists: w = dL/da (input

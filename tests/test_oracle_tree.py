@@ -360,3 +360,53 @@ def test_lattice_lists_are_translates_of_one_another(theta, rc):
             assert (theta == 0.0) == bool(np.all(e >= 0))
         else:
             assert key.shape == ref.shape and np.array_equal(key, ref), g
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_count_useful_matches_neighbour_counts(kind):
+    """At theta = 0 every source within r_cut of a particle appears once in its
+    group's list as a particle, so the useful pairs are the ordered pairs at
+    0 < r < r_cut, which a periodic cKDTree counts independently; in the
+    softened-xi variant they are the pairs with r^2 + eps^2 < r_cut^2."""
+    n, rc, eps = 3000, 0.09, 0.01
+    if kind == "uniform":
+        pos, mass = inputs.uniform_box(n, 11)
+    else:
+        pos, mass = inputs.clustered_box(n, 20, 12)
+    t = oracle.OracleTree(pos, mass, 8, 48)
+    t.lists(rc, 0.0)
+    kd = cKDTree(np.mod(pos, 1.0), boxsize=1.0)
+    assert t.count_useful(eps, rc) == 2 * len(kd.query_pairs(rc))
+    assert t.count_useful(eps, rc, xi_softened=True) == 2 * len(kd.query_pairs(np.sqrt(rc * rc - eps * eps)))
+    ex = t.export()
+    assert t.count_useful(eps, rc) < int((ex.gcount * np.diff(ex.loff)).sum())
+
+
+def test_count_useful_brute_force_with_monopoles():
+    """theta = 0.5 lists hold monopoles too: a direct count over the exported
+    lists (particle entries at their positions, node entries at their centres
+    of mass, the particle itself skipped) agrees; every accepted monopole lies
+    inside r_cut of every member of its group, so it always counts."""
+    pos, mass = inputs.clustered_box(1500, 6, 13)
+    rc, eps = 0.12, 0.004
+    t = oracle.OracleTree(pos, mass, 4, 16)
+    t.lists(rc, 0.5)
+    ex = t.export()
+    w = np.mod(pos, 1.0)
+    w[w >= 1.0] = 0.0
+    xs = w[ex.perm]
+    n_nodes_entries = 0
+    count = 0
+    for g in range(ex.gfirst.size):
+        ent = ex.ent[ex.loff[g]:ex.loff[g + 1]]
+        src = np.where(ent[:, None] >= 0, xs[np.maximum(ent, 0)], ex.com[np.maximum(-ent - 1, 0)])
+        for i in range(ex.gfirst[g], ex.gfirst[g] + ex.gcount[g]):
+            d = src - xs[i]
+            d -= np.rint(d)
+            r = np.sqrt((d * d).sum(axis=1))
+            keep = (ent != i) & (r > 0) & (r < rc)
+            count += int(keep.sum())
+            n_nodes_entries += int((ent < 0).sum())
+            assert keep[ent < 0].all()
+    assert n_nodes_entries > 0
+    assert t.count_useful(eps, rc) == count
