@@ -43,9 +43,19 @@ FLOPS_PER_INTERACTION = 42
 VJP_FLOPS_PER_INTERACTION = 76
 FUSED_FLOPS_PER_INTERACTION = 82   # the adjoint's 76 + the forward's a += alpha d (3 FMA)
 PAPER_FLOPS_PER_INTERACTION = 51 # the paper's convention (Sec. II-A)
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ = 2070.0      # GB300's maximum SM clock; the clock sampler's reading replaces it
+
+
+def fp32_peak(dev, clk=None):
+    """Nominal FP32 peak of this GPU (FLOP/s) and its basis: SMs as the device
+    reports them x 128 FP32 lanes x 2 (an FMA) x the maximum SM clock that
+    nvidia-smi reports during the run (GB300's 2070 MHz if it reported none)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ
+    basis = f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz (maximum SM clock)"
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6, basis
 CONFIG_K = 2
 
 
@@ -390,15 +400,14 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         return
     mean = lambda xs: sum(xs) / len(xs)
     sep_step = mean([e[0].elapsed_time(e[3]) for e in sep])
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
-    peak_basis = "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal max clock)"
+    fp32_pk, peak_basis = fp32_peak(dev, clk)
     # every group of this workload takes the packed kernels (none spans half
     # the box and eps > 0), so each launch processes all interactions
 
     def roofline(kernel, ms, flops, note):
         ach = flops * inter / (ms * 1e-3)
-        return {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic_for(kernel, box.n, wl), "kernel": f"{kernel} ({note})",
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_pk / 1e12, "unit": "TFLOP/s",
+                "frac": ach / fp32_pk, "traffic": traffic_for(kernel, box.n, wl), "kernel": f"{kernel} ({note})",
                 "ms_per_launch": ms, "flops_per_interaction": flops, "peak_basis": peak_basis}
 
     kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)
@@ -436,11 +445,14 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         "adjoint_interactions_per_s": inter / (kv_ms * 1e-3),
         "fp64_forward_interactions_per_s": inter / (mean(f64_ms) * 1e-3),
         "fp32_over_fp64_forward_speedup": mean(f64_ms) / kp_ms,
-        "forward_paper_convention_frac": PAPER_FLOPS_PER_INTERACTION * inter / (kp_ms * 1e-3) / fp32_peak,
+        "forward_paper_convention_frac": PAPER_FLOPS_PER_INTERACTION * inter / (kp_ms * 1e-3) / fp32_pk,
         "measured_peaks_tflops": {"ffma": meas_ffma / 1e12, "ffma2": meas_ffma2 / 1e12,
                                   "dfma": meas_dfma / 1e12},
-        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions",
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "n_useful",
                                     "n_ambiguous", "mean_ni", "mean_nj", "max_nj")},
+        "useful_fraction": st["n_useful"] / max(1, st["n_interactions"]),
+        "useful_fraction_basis": "pairs with a non-zero Eq. 2 term (0 < r < r_cut, decided in FP64) among "
+                                 "the sum over groups of n_i * n_j that value counts",
     }
     if world == 1 and not args.no_cpu_baseline and not paper_regime:
         r = oracle_sample_rate(box, w, steps=1, xi_softened=args.xi == "softened")
@@ -554,8 +566,9 @@ def run_batched(args, rank, world, local_rank):
                 "ms_per_step": tot_e2e / args.steps},
         "gpu_launches": per_replay * args.steps, "clocks": clk,
         "autotune_s": t_tune,
-        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "mean_ni",
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "n_useful", "mean_ni",
                                     "mean_nj", "max_nj", "nbox")},
+        "useful_fraction": st["n_useful"] / max(1, st["n_interactions"]),
     }
     print(json.dumps(line), flush=True)
 
@@ -632,8 +645,9 @@ def run_uniform_fp64(args, rank, world, local_rank):
                 "ms_per_step": tot_e2e / args.steps},
         "gpu_launches": res["fp64"]["launches"],
         "fp32_step_ms": fp32_ms, "fp32_over_fp64_step_speedup": (tot_ms / args.steps) / fp32_ms,
-        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "mean_ni",
+        "tree": {k: st[k] for k in ("n_nodes", "n_groups", "n_entries", "n_interactions", "n_useful", "mean_ni",
                                     "mean_nj", "max_nj")},
+        "useful_fraction": st["n_useful"] / max(1, st["n_interactions"]),
     }
     print(json.dumps(line), flush=True)
 
@@ -886,7 +900,7 @@ def run_treepm(args, rank, world, local_rank):
           "short_range_force": mean([e[1].elapsed_time(e[2]) for e in phases]),
           "pm_force": mean([e[2].elapsed_time(e[3]) for e in phases]),
           "pm_force_alone_l2_flushed": mean(pm_only)}
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    fp32_pk, _ = fp32_peak(dev, clk)
     ach = FLOPS_PER_INTERACTION * st["n_interactions"] / (ph["short_range_force"] * 1e-3)
     line = {
         "metric": "particles/s (whole TreePM acceleration: rebuild + FP32 short-range + PM on 128^3, clustered 2M box)",
@@ -896,8 +910,8 @@ def run_treepm(args, rank, world, local_rank):
         "config": {"workload": "treepm-2M", "n": box.n, "halos": 2000, "r_cut": "3/128", "eps": "1/6400",
                    "theta": 0.5, "n_crit": box.n_crit, "n_mesh": n_mesh,
                    "l2": "flushed (256 MiB write) before every timed step"},
-        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": ach / fp32_peak, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_pk / 1e12, "unit": "TFLOP/s",
+                     "frac": ach / fp32_pk, "traffic": None,
                      "kernel": "short-range force call (k_pair_packed + general kernel), the largest share",
                      "flops_per_interaction": FLOPS_PER_INTERACTION},
         "phases_ms": ph,

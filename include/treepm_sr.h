@@ -105,11 +105,18 @@ typedef struct {
 typedef struct tp_tree tp_tree; /* opaque, library-owned */
 
 /* Statistics of a built tree (Table I reports the same quantities).
- * n_interactions = sum over groups of n_i * n_j, the paper's count.  In
+ * n_interactions = sum over groups of n_i * n_j, the paper's count of the
+ * pairs the force loop evaluates (Sec. III-B).  n_useful = how many of those
+ * pairs have a non-zero Eq. 2 term: a positive distance r and a cutoff
+ * distance (r, or sqrt(r^2 + eps^2) with TP_FLAG_XI_SOFTENED) below r_cut,
+ * decided in FP64 from the FP64 positions and centres of mass; counted by a
+ * pass over the lists on each tp_tree_stats call (about a quarter of a force
+ * call's time), -1 for a tree in chunked mode (its lists are not kept).  In
  * chunked mode the list quantities are those of the last build or force
  * call.                                                                     */
 typedef struct {
     int64_t n, n_nodes, n_groups, n_entries, n_interactions;
+    int64_t n_useful;      /* evaluated pairs inside the cutoff (see above)  */
     int64_t n_ambiguous;   /* walk decisions settled by the exact FP64 test  */
     double mean_ni, mean_nj;
     int32_t max_nj, nbox;
@@ -250,20 +257,28 @@ tp_status tp_tree_kernel_ms(tp_tree *t, double *force_ms, double *vjp_ms);
  * callers that must not let a library call cudaMalloc -- an application whose
  * device memory is carved from its own pool, or a latency-critical loop that
  * cannot afford an allocation's implicit synchronisation.  Its scratch (the
- * particles' fixed-point images and masses, 28 bytes per particle) is one
- * statically sized device array of TP_NOALLOC_MAX_N entries (1.8 MB), which
- * every GPU that loads the library holds until the process exits.
- *   pos   device FP64 [n][3], finite; mass device FP64 [n] or NULL (1/n)
+ * particles' fixed-point images and masses, 28 bytes per particle, and a
+ * status word) is one statically sized device array of TP_NOALLOC_MAX_N
+ * entries (1.8 MB), which every GPU that loads the library holds until the
+ * process exits.  It computes the exact cutoff sum over all pairs: the same
+ * force as tp_build_tree + tp_short_range_force at theta = 0, up to FP32
+ * rounding.
+ *   pos   device FP64 [n][3], memory of the current device (or managed)
+ *   mass  device FP64 [n] or NULL (every mass 1/n)
  *   n     0 <= n <= TP_NOALLOC_MAX_N, else TP_ERR_INVALID_ARG
- *   p     host; precision must be TP_FP32 and flags 0; theta, n_crit and
- *         n_leaf are not used: the sum runs over all pairs (Eq. 2 with Eq. 3,
- *         exact cutoff)
+ *   p     host; precision must be TP_FP32 and flags 0, 0 < r_cut < 0.5,
+ *         eps >= 0, G finite (else TP_ERR_INVALID_ARG); theta, n_crit and
+ *         n_leaf are not used
  *   acc   device FP32 [n][3], input order, overwritten
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call rewrites the scratch it reads, so nothing needs
- * clearing, but all calls share the one array: calls that overlap on the GPU
- * (on different streams, or from different threads) race.  Asynchronous.     */
+ * A NaN or infinite position returns TP_ERR_NONFINITE and leaves acc
+ * unwritten: to return it, the call synchronises `stream` once, after the
+ * positions are converted and before the pair sum is enqueued.  The pair sum
+ * itself is asynchronous.  The first call on a device looks up the array's
+ * device address (once per device, with that device current) and keeps it
+ * for the life of the process; a cudaDeviceReset invalidates it, so do not
+ * call this entry point after one.  Every call rewrites the scratch it reads,
+ * so nothing needs clearing, but all calls share the one array: calls that
+ * overlap on the GPU (on different streams, or from different threads) race. */
 tp_status tp_short_range_force_noalloc(const double *pos, const double *mass, int64_t n,
                                        const tp_params *p, float *acc, void *stream);
 

@@ -30,7 +30,8 @@ class TPParams(C.Structure):
 
 class TPStats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_nodes", C.c_int64), ("n_groups", C.c_int64),
-                ("n_entries", C.c_int64), ("n_interactions", C.c_int64), ("n_ambiguous", C.c_int64),
+                ("n_entries", C.c_int64), ("n_interactions", C.c_int64), ("n_useful", C.c_int64),
+                ("n_ambiguous", C.c_int64),
                 ("mean_ni", C.c_double), ("mean_nj", C.c_double), ("max_nj", C.c_int32),
                 ("nbox", C.c_int32), ("n_windows", C.c_int64)]
 

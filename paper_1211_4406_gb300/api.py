@@ -20,6 +20,24 @@ def _stream(stream=None) -> C.c_void_p:
     return C.c_void_p(s.cuda_stream)
 
 
+def _order(stream, *tensors) -> None:
+    """Make a call on `stream` safe for tensors prepared on torch's current
+    stream.  The conversions and allocations of the binding (contiguous
+    copies, dtype casts, outputs) run on the current stream; when the library
+    is given another stream, that stream first waits for the current one, and
+    each tensor is recorded on it, so that the caching allocator does not hand
+    its memory to someone else while the library still reads or writes it."""
+    if stream is None:
+        return
+    cur = torch.cuda.current_stream(stream.device)
+    if stream == cur:
+        return
+    stream.wait_stream(cur)
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
+
+
 def _dev_f64(x: torch.Tensor, shape_last=None) -> torch.Tensor:
     if not isinstance(x, torch.Tensor) or not x.is_cuda:
         raise TypeError("expected a CUDA tensor")
@@ -105,6 +123,7 @@ class ShortRangeTree:
         self.precision = params[0].precision
         self.acc_dtype = torch.float32 if self.precision == "fp32" else torch.float64
         self._pos, self._mass = pos, mass          # keep alive until the build completes
+        _order(stream, pos, mass)
         arr = (C.c_int64 * len(box_offsets))(*box_offsets)
         prm = (_lib.TPParams * len(params))(*[p.c() for p in params])
         h = C.c_void_p()
@@ -140,6 +159,7 @@ class ShortRangeTree:
             raise ValueError("rebuild needs the same particle count")
         mass = _dev_mass(mass, self.n)
         self._pos, self._mass = pos, mass
+        _order(stream, pos, mass)
         code = _lib.load().tp_rebuild_tree(self.handle, C.c_void_p(pos.data_ptr()),
                                            C.c_void_p(mass.data_ptr()) if mass is not None else None,
                                            _stream(stream))
@@ -153,6 +173,7 @@ class ShortRangeTree:
             raise ValueError("refit needs the same particle count")
         mass = _dev_mass(mass, self.n)
         self._pos, self._mass = pos, mass
+        _order(stream, pos, mass)
         code = _lib.load().tp_refit_tree(self.handle, C.c_void_p(pos.data_ptr()),
                                          C.c_void_p(mass.data_ptr()) if mass is not None else None,
                                          _stream(stream))
@@ -163,6 +184,7 @@ class ShortRangeTree:
         if out is None:
             out = torch.empty((self.n, 3), dtype=self.acc_dtype, device=self._pos.device)
         _dev_vec3(out, self.n, self.acc_dtype, "out (the tree's precision)")
+        _order(stream, out)
         code = _lib.load().tp_short_range_force(self.handle, C.c_void_p(out.data_ptr()), _stream(stream))
         _lib.check(code, "tp_short_range_force")
         return out
@@ -173,6 +195,7 @@ class ShortRangeTree:
         if out is None:
             out = torch.empty((self.n, 3), dtype=torch.float64, device=self._pos.device)
         _dev_vec3(out, self.n, torch.float64, "out")
+        _order(stream, cot, out)
         code = _lib.load().tp_short_range_vjp(self.handle, C.c_void_p(cot.data_ptr()),
                                               C.c_void_p(out.data_ptr()), _stream(stream))
         _lib.check(code, "tp_short_range_vjp")
@@ -189,6 +212,7 @@ class ShortRangeTree:
             grad = torch.empty((self.n, 3), dtype=torch.float64, device=dev)
         _dev_vec3(acc, self.n, self.acc_dtype, "acc (the tree's precision)")
         _dev_vec3(grad, self.n, torch.float64, "grad")
+        _order(stream, cot, acc, grad)
         code = _lib.load().tp_short_range_force_vjp(self.handle, C.c_void_p(acc.data_ptr()),
                                                     C.c_void_p(cot.data_ptr()), C.c_void_p(grad.data_ptr()),
                                                     _stream(stream))
@@ -300,6 +324,7 @@ class PMSolver:
                 raise ValueError("accumulate needs out")
             out = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
         _dev_vec3(out, n, torch.float32, "out")
+        _order(stream, pos, mass, out)
         code = _lib.load().tp_pm_force(self._h, C.c_void_p(pos.data_ptr()),
                                        C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
                                        C.c_void_p(out.data_ptr()), int(bool(accumulate)), _stream(stream))
@@ -311,6 +336,7 @@ class PMSolver:
         """dL/dx (float64 [n, 3]) of L = sum_i cot_i . a_i over the PM cycle;
         added to `out` when accumulate is set (e.g. onto the short-range VJP)."""
         pos, mass, cot, out = self._adjoint_args(pos, mass, cot, out, accumulate)
+        _order(stream, pos, mass, cot, out)
         code = _lib.load().tp_pm_vjp(self._h, C.c_void_p(pos.data_ptr()),
                                      C.c_void_p(mass.data_ptr()) if mass is not None else None, int(pos.shape[0]),
                                      C.c_void_p(cot.data_ptr()), C.c_void_p(out.data_ptr()), int(bool(accumulate)),
@@ -329,6 +355,7 @@ class PMSolver:
                 raise ValueError("accumulate needs acc")
             acc = torch.empty((n, 3), dtype=torch.float32, device=pos.device)
         _dev_vec3(acc, n, torch.float32, "acc")
+        _order(stream, pos, mass, cot, acc, grad)
         code = _lib.load().tp_pm_force_vjp(self._h, C.c_void_p(pos.data_ptr()),
                                            C.c_void_p(mass.data_ptr()) if mass is not None else None, n,
                                            C.c_void_p(acc.data_ptr()), C.c_void_p(cot.data_ptr()),

@@ -33,6 +33,7 @@ void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, d
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s);
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s);
+void count_useful(TreeDev &T, unsigned long long *useful, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles);
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s);
@@ -153,7 +154,7 @@ struct tp_tree {
     uint32_t *lpt_val2 = nullptr;
     void *lpt_tmp = nullptr;
     double *gs = nullptr, *ncot = nullptr;
-    unsigned long long *d_inter = nullptr;
+    unsigned long long *d_inter = nullptr, *d_useful = nullptr;
     int32_t *d_maxnj = nullptr;
     // host copies of the sizes (valid after a synchronising build)
     int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_pad = 0, h_entries = 0;
@@ -617,6 +618,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     t->queue = B.get<int32_t>(4);
     t->gs = B.get<double>(3 * nn);
     t->d_inter = B.get<unsigned long long>(1);
+    t->d_useful = B.get<unsigned long long>(1);
     t->d_maxnj = B.get<int32_t>(1);
     t->d_etot = B.get<int64_t>(1);
     t->d_wsz = B.get<int64_t>(kMaxWindows);
@@ -789,16 +791,23 @@ tp_status tp_tree_status(tp_tree *t)
     return (tp_status)st;
 }
 
-tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
+// Statistics; the useful-pair count (a pass over every pair of the lists)
+// only when asked for: the parity exports read the sizes alone.
+static tp_status tree_stats(tp_tree *t, tp_stats *out, bool count)
 {
     if (!t || !out) return TP_ERR_INVALID_ARG;
     cudaStream_t s = t->last;
+    const bool whole = !t->chunked && t->D.gfirst;
     if (!t->chunked) {
         cudaMemsetAsync(t->d_inter, 0, sizeof(unsigned long long), s);
         cudaMemsetAsync(t->d_maxnj, 0, sizeof(int32_t), s);
         if (t->D.gfirst) tp::list_stats(t->D, t->d_inter, t->d_maxnj, s);
     }
-    unsigned long long inter = 0, amb = 0;
+    if (count && whole) {
+        cudaMemsetAsync(t->d_useful, 0, sizeof(unsigned long long), s);
+        tp::count_useful(t->D, t->d_useful, s);
+    }
+    unsigned long long inter = 0, amb = 0, useful = 0;
     int32_t mx = 0;
     int64_t nn = 0, ng = 0, ne = 0;
     cudaMemcpyAsync(&inter, t->d_inter, sizeof(inter), cudaMemcpyDeviceToHost, s);
@@ -807,6 +816,7 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
     cudaMemcpyAsync(&nn, t->D.n_nodes, sizeof(nn), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&ng, t->D.n_groups, sizeof(ng), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&ne, t->chunked ? t->d_etot : t->D.n_entries, sizeof(ne), cudaMemcpyDeviceToHost, s);
+    if (count && whole) cudaMemcpyAsync(&useful, t->d_useful, sizeof(useful), cudaMemcpyDeviceToHost, s);
     tp_status e = cuda_status(cudaStreamSynchronize(s));
     if (e != TP_OK) return e;
     if (t->n == 0) nn = ng = ne = 0;
@@ -815,6 +825,7 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
     out->n_groups = ng;
     out->n_entries = ne;
     out->n_interactions = (int64_t)inter;
+    out->n_useful = t->chunked ? -1 : (int64_t)useful;
     out->n_ambiguous = (int64_t)amb;
     out->mean_ni = ng ? (double)t->n / (double)ng : 0.0;
     out->mean_nj = ng ? (double)ne / (double)ng : 0.0;
@@ -823,6 +834,8 @@ tp_status tp_tree_stats(tp_tree *t, tp_stats *out)
     out->n_windows = t->chunked ? (int64_t)t->win_count.size() : 1;
     return TP_OK;
 }
+
+tp_status tp_tree_stats(tp_tree *t, tp_stats *out) { return tree_stats(t, out, true); }
 
 tp_status tp_export_keys(tp_tree *t, uint64_t *keys, int64_t *perm)
 {
@@ -840,7 +853,7 @@ tp_status tp_export_nodes(tp_tree *t, int64_t *ints, double *dbl)
 {
     if (!t) return TP_ERR_INVALID_ARG;
     tp_stats st;
-    tp_status e = tp_tree_stats(t, &st);
+    tp_status e = tree_stats(t, &st, false);
     if (e != TP_OK) return e;
     const int64_t nn = st.n_nodes;
     if (nn > 0 && (!ints || !dbl)) return TP_ERR_INVALID_ARG;
@@ -866,7 +879,7 @@ tp_status tp_export_groups(tp_tree *t, int64_t *ints, double *dbl)
 {
     if (!t) return TP_ERR_INVALID_ARG;
     tp_stats st;
-    tp_status e = tp_tree_stats(t, &st);
+    tp_status e = tree_stats(t, &st, false);
     if (e != TP_OK) return e;
     const int64_t ng = st.n_groups;
     if (ng > 0 && (!ints || !dbl)) return TP_ERR_INVALID_ARG;
@@ -887,7 +900,7 @@ tp_status tp_export_lists(tp_tree *t, int64_t *offsets, int32_t *entries)
 {
     if (!t || !offsets || t->chunked) return TP_ERR_INVALID_ARG;
     tp_stats st;
-    tp_status e = tp_tree_stats(t, &st);
+    tp_status e = tree_stats(t, &st, false);
     if (e != TP_OK) return e;
     if (st.n_entries > 0 && !entries) return TP_ERR_INVALID_ARG;
     offsets[0] = 0;

@@ -5,19 +5,23 @@
 // device memory is carved from its own pool and forbids other allocations, or
 // a latency-critical loop where an allocation's implicit synchronisation is
 // not acceptable.  For them this entry point keeps its scratch -- the 64-bit
-// fixed-point images and the masses of the particles -- in one statically
-// sized device array that the CUDA driver places when the library's module is
-// loaded.  Every GPU that loads the library holds that array (28 bytes per
-// particle x TP_NOALLOC_MAX_N = 1.8 MB) until the process exits.
+// fixed-point images and the masses of the particles, and one status word --
+// in one statically sized device array that the CUDA driver places when the
+// library's module is loaded.  Every GPU that loads the library holds that
+// array (28 bytes per particle x TP_NOALLOC_MAX_N = 1.8 MB) until the process
+// exits.
 //
-// The sum is taken directly over all pairs (no tree, so it is Eq. 2 exactly,
-// up to FP32 rounding): each pair's minimum-image offset is the wrap-around
-// difference of the two fixed-point images, converted once to FP32 and scaled
-// by k = 2/r_cut; Eq. 3 is evaluated in the cancellation-free form
-// u^5 h(xi) + v^6 c(xi) used by the tree path; tile sums are accumulated in
-// FP64.  Every call fully rewrites the part of the scratch it reads, so nothing
-// has to be cleared between calls; calls that overlap on the GPU share the
-// array and race.
+// The sum is taken directly over all pairs (no tree): the exact cutoff sum,
+// the same force as the tree path at theta = 0, up to FP32 rounding.  Each
+// pair's minimum-image offset is the wrap-around difference of the two
+// fixed-point images, converted once to FP32 and scaled by k = 2/r_cut; the
+// cutoff function is evaluated in the cancellation-free form u^5 h(xi) +
+// v^6 c(xi) used by the tree path; tile sums are accumulated in FP64.  A
+// non-finite position is detected while the images are taken: the call then
+// returns TP_ERR_NONFINITE (it synchronises its stream once for that) and
+// leaves acc unwritten.  Every call fully rewrites the part of the scratch it
+// reads and clears the status word first, so nothing has to be cleared
+// between calls; calls that overlap on the GPU share the array and race.
 #include <cmath>
 #include <mutex>
 
@@ -28,12 +32,14 @@ namespace {
 constexpr int kNaThreads = 128;
 constexpr size_t kNaBytes = (size_t)TP_NOALLOC_MAX_N * (3 * sizeof(uint64_t) + sizeof(float));
 
-// Layout: X[max], Y[max], Z[max] (uint64), then M[max] (float).
-static __device__ __align__(256) unsigned char tp_noalloc_scratch[kNaBytes];
+// Layout: X[max], Y[max], Z[max] (uint64), M[max] (float), then the status
+// word (int32) of the last call.
+static __device__ __align__(256) unsigned char tp_noalloc_scratch[kNaBytes + 256];
 
 struct NaView {
     uint64_t *X, *Y, *Z;
     float *M;
+    int32_t *status;
 };
 
 __host__ __device__ inline NaView na_view(unsigned char *base)
@@ -43,6 +49,7 @@ __host__ __device__ inline NaView na_view(unsigned char *base)
     v.Y = v.X + TP_NOALLOC_MAX_N;
     v.Z = v.Y + TP_NOALLOC_MAX_N;
     v.M = reinterpret_cast<float *>(v.Z + TP_NOALLOC_MAX_N);
+    v.status = reinterpret_cast<int32_t *>(base + kNaBytes);
     return v;
 }
 
@@ -62,9 +69,17 @@ __device__ __forceinline__ float na_sqrt_approx(float x)
 __global__ void k_na_images(const double *pos, const double *mass, int n, float inv_n, NaView S)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        S.X[i] = tp_fixed64(na_wrap(pos[3 * (int64_t)i]));
-        S.Y[i] = tp_fixed64(na_wrap(pos[3 * (int64_t)i + 1]));
-        S.Z[i] = tp_fixed64(na_wrap(pos[3 * (int64_t)i + 2]));
+        const double x = pos[3 * (int64_t)i], y = pos[3 * (int64_t)i + 1], z = pos[3 * (int64_t)i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+            // no image of a non-finite coordinate exists: record the error
+            // (the host refuses the call) and write a defined value
+            atomicCAS(S.status, 0, (int32_t)TP_ERR_NONFINITE);
+            S.X[i] = S.Y[i] = S.Z[i] = 0ull;
+        } else {
+            S.X[i] = tp_fixed64(na_wrap(x));
+            S.Y[i] = tp_fixed64(na_wrap(y));
+            S.Z[i] = tp_fixed64(na_wrap(z));
+        }
         S.M[i] = mass ? (float)mass[i] : inv_n;
     }
 }
@@ -122,29 +137,30 @@ __global__ void __launch_bounds__(kNaThreads) k_na_pairs(NaView S, int n, float 
     }
 }
 
-bool na_is_device_ptr(const void *p)
+// Device (or managed) memory that belongs to the current device: the kernels
+// run there and must not read another GPU's memory through this path.
+bool na_is_device_ptr(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device address of the scratch array, looked up once per device (host code
-// cannot use the array's name as a device pointer).
+// cannot use the array's name as a device pointer) and kept for the life of
+// the process; a cudaDeviceReset unloads the module, so the cached address
+// does not survive one.
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mutex;
 unsigned char *g_na_ptr[kNaMaxDevices] = {};
 
-tp_status na_scratch(unsigned char **out)
+tp_status na_scratch(int dev, unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
-        cudaGetLastError();
-        return TP_ERR_NO_DEVICE;
-    }
+    if (dev < 0 || dev >= kNaMaxDevices) return TP_ERR_NO_DEVICE;
     std::lock_guard<std::mutex> lock(g_na_mutex);
     if (!g_na_ptr[dev]) {
         void *p = nullptr;
@@ -169,10 +185,15 @@ extern "C" tp_status tp_short_range_force_noalloc(const double *pos, const doubl
         !std::isfinite(p->G) || p->precision != TP_FP32 || p->flags != 0)
         return TP_ERR_INVALID_ARG;
     if (n == 0) return TP_OK;
-    if (!na_is_device_ptr(pos) || !na_is_device_ptr(acc) || (mass && !na_is_device_ptr(mass)))
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TP_ERR_NO_DEVICE;
+    }
+    if (!na_is_device_ptr(pos, dev) || !na_is_device_ptr(acc, dev) || (mass && !na_is_device_ptr(mass, dev)))
         return TP_ERR_INVALID_ARG;
     unsigned char *base = nullptr;
-    const tp_status st = na_scratch(&base);
+    const tp_status st = na_scratch(dev, &base);
     if (st != TP_OK) return st;
     const NaView S = na_view(base);
     const double k = 2.0 / p->r_cut;
@@ -182,7 +203,19 @@ extern "C" tp_status tp_short_range_force_noalloc(const double *pos, const doubl
     const int ni = (int)n;
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = (ni + kNaThreads - 1) / kNaThreads;
+    if (cudaMemsetAsync(S.status, 0, sizeof(int32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return TP_ERR_CUDA;
+    }
     TP_LAUNCH(k_na_images, blocks, kNaThreads, 0, s, pos, mass, ni, (float)(1.0 / (double)n), S);
+    // the status of the positions, read back before the pair sum is enqueued
+    int32_t status = 0;
+    if (cudaMemcpyAsync(&status, S.status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TP_ERR_CUDA;
+    }
+    if (status != 0) return (tp_status)status;
     TP_LAUNCH(k_na_pairs, blocks, kNaThreads, 0, s, S, ni, sc, eps2, gk2, acc);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TP_OK : TP_ERR_CUDA;

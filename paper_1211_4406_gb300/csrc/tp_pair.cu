@@ -30,6 +30,18 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return r;
 }
 
+// The MUFU reciprocal square root without denormal handling.  The packed pair
+// kernels take it of s'^2 = |d'|^2 + (k eps)^2 >= (k eps)^2 > 0, always a
+// normal number; rsqrtf() would wrap the same MUFU operation in a test and two
+// scalar multiplies for denormal inputs (measured: 4 extra FMA-pipe cycles per
+// packed pair step, about 6 % of the forward kernel's FMA-pipe work).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Packed FP32 pairs (two lanes of one 64-bit register): Blackwell executes
 // add/sub/mul/fma.f32x2 as one instruction, halving the issue slots of the
 // pair arithmetic.
@@ -245,7 +257,7 @@ __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4
             const f2 s2 = SOFT ? r2 : f2add(r2, E2);
             float s2a, s2b;
             f2unpack(s2, s2a, s2b);
-            const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+            const f2 ri = f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
             f2 x;                                   // the cutoff argument xi
             if (SOFT) {
                 x = f2pack(sqrt_approx(s2a), sqrt_approx(s2b));
@@ -436,17 +448,29 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 }
 
 // The FP32 forward kernel for ordinary groups with eps > 0: packed pair math
-// fed by the entry records.  Tiles are double buffered in shared memory: while
-// tile t is computed from one buffer, each thread stores its entry pair of tile
-// t+1 (loaded one tile earlier into registers) into the other buffer and loads
-// its pair of tile t+2, so one barrier per tile suffices.  Each tile's FP32
-// partial enters an FP64 sum per particle.
-template <int NI, bool SOFT>
+// fed by the entry records.  Each of the 128 threads holds NI particles of
+// the group and takes a slice of the entry pairs of every tile (256 entries):
+// the group's particle columns (NI particles each) and the slices make a grid
+// of columns x floor(128 / columns) threads, and the threads left over idle.
+// Tiles are double buffered in shared memory:
+// while tile t is computed from one buffer, each thread stores its entry pair
+// of tile t+1 (loaded one tile earlier into registers) into the other buffer
+// and loads its pair of tile t+2, so one barrier per tile suffices.  A tile
+// holds 2 ns floor(128 / ns) entries (at most 256), so that each of the ns
+// slices takes the same number of pairs from it.  The FP32
+// partials of TS consecutive tiles enter an FP64 sum per particle: on GB300 a
+// warp's FP64 add occupies its scheduler's FP64 unit for about 77 cycles, so
+// adding every tile (TS = 1) stalls each warp for several hundred cycles per
+// tile; TS = 8 (FP32 runs of at most 8 x 256 / slices entries per thread)
+// measured 2 % faster on the clustered 2M box with the FP32 error unchanged
+// (rms 4.1e-7 against the FP64 path on the same lists).
+template <int NI, int TS, bool SOFT>
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
-    __shared__ float4 SA[2][kTile / 2], SB[2][kTile / 2];
-    __shared__ double red[3 * NI][kThreads];
+    constexpr int NT = kThreads;
+    __shared__ float4 SA[2][NT], SB[2][NT];
+    __shared__ double red[3 * NI][NT];
     __shared__ int s_item;
     const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
@@ -458,14 +482,18 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
         const int ne = bad ? 0 : G.ne;
-        for (int i0 = 0; i0 < G.ni; i0 += NI * kThreads) {
+        for (int i0 = 0; i0 < G.ni; i0 += NI * NT) {
             // particle k*nip + il of this chunk goes to the threads il, il + nip, ... (slices)
-            const int nic = min(NI * kThreads, G.ni - i0);
+            const int nic = min(NI * NT, G.ni - i0);
             const int nip = (nic + NI - 1) / NI;
-            const int ns = kThreads / nip;
+            const int ns = NT / nip;
             const int slot = threadIdx.x;
             const bool active = slot < nip * ns;
             const int il = active ? slot % nip : 0, st = active ? slot / nip : 0;
+            // entries per tile: a multiple of 2 ns, so that every slice takes
+            // the same number of pairs of each full tile (the barrier after a
+            // tile waits for the longest slice)
+            const int kT = 2 * ns * (NT / ns);
             float xi[NI], yi[NI], zi[NI];
 #pragma unroll
             for (int k = 0; k < NI; k++) {
@@ -480,36 +508,47 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
                 }
             }
             double sax[NI], say[NI], saz[NI];
+            float ax[NI], ay[NI], az[NI];
 #pragma unroll
-            for (int k = 0; k < NI; k++) sax[k] = say[k] = saz[k] = 0.0;
+            for (int k = 0; k < NI; k++) {
+                sax[k] = say[k] = saz[k] = 0.0;
+                ax[k] = ay[k] = az[k] = 0.f;
+            }
             float4 n0 = pad, n1 = pad;
             auto fetch = [&](int t1) {
-                const int nt1 = min(kTile, ne - t1), q = 2 * (int)threadIdx.x;
+                const int nt1 = min(kT, ne - t1), q = 2 * (int)threadIdx.x;
                 n0 = q < nt1 ? T.rec[G.e0 + t1 + q] : pad;
                 n1 = q + 1 < nt1 ? T.rec[G.e0 + t1 + q + 1] : pad;
+            };
+            // this thread's entry pair of a tile, staged as {x0, x1, y0, y1}, {z0, z1, m0, m1}
+            auto stage = [&](int bb) {
+                SA[bb][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
+                SB[bb][threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
             };
             __syncthreads();
             if (ne > 0) {
                 fetch(0);
-                SA[0][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
-                SB[0][threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
-                if (kTile < ne) fetch(kTile);
+                stage(0);
+                if (kT < ne) fetch(kT);
             }
             __syncthreads();
-            for (int t0 = 0, b = 0; t0 < ne; t0 += kTile, b ^= 1) {
-                const int nt = min(kTile, ne - t0);
+            int tc = 0;                                     // tiles in the current FP32 partial
+            for (int t0 = 0, b = 0; t0 < ne; t0 += kT, b ^= 1) {
+                const int nt = min(kT, ne - t0);
                 if (active) {
-                    float ax[NI], ay[NI], az[NI];
-#pragma unroll
-                    for (int k = 0; k < NI; k++) ax[k] = ay[k] = az[k] = 0.f;
                     force_tile_packed<NI, SOFT>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+                    if (++tc == TS || t0 + kT >= ne) {
 #pragma unroll
-                    for (int k = 0; k < NI; k++) { sax[k] += ax[k]; say[k] += ay[k]; saz[k] += az[k]; }
+                        for (int k = 0; k < NI; k++) {
+                            sax[k] += ax[k]; say[k] += ay[k]; saz[k] += az[k];
+                            ax[k] = ay[k] = az[k] = 0.f;
+                        }
+                        tc = 0;
+                    }
                 }
-                if (t0 + kTile < ne) {
-                    SA[b ^ 1][threadIdx.x] = make_float4(n0.x, n1.x, n0.y, n1.y);
-                    SB[b ^ 1][threadIdx.x] = make_float4(n0.z, n1.z, n0.w, n1.w);
-                    if (t0 + 2 * kTile < ne) fetch(t0 + 2 * kTile);
+                if (t0 + kT < ne) {
+                    stage(b ^ 1);
+                    if (t0 + 2 * kT < ne) fetch(t0 + 2 * kT);
                 }
                 __syncthreads();
             }
@@ -518,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
                 red[3 * k][slot] = sax[k]; red[3 * k + 1][slot] = say[k]; red[3 * k + 2][slot] = saz[k];
             }
             __syncthreads();
-            for (int i = slot; i < nic; i += kThreads) {
+            for (int i = slot; i < nic; i += NT) {
                 const int k = i / nip, l = i % nip;
                 double sxx = 0, syy = 0, szz = 0;
                 for (int s2 = 0; s2 < ns; s2++) {
@@ -541,7 +580,9 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
 //   J' = phi I + psi d' d'^T,  psi = (g'/xi)/s'^3 - 3 g/s'^5,
 //   v  = m_j J' w_i = alpha w_i + beta d',  alpha = m_j phi, beta = m_j psi (d'.w_i)
 // and dL/dx_i -= G k^3 v, dL/dx_j += G k^3 v (a node passes its share to its
-// centre-of-mass cotangent).  Threads hold list entries (j) and loop over the
+// centre-of-mass cotangent); the kernels add -v and +v, and the common factor
+// G k^3 of a box is applied per particle at the end (k_unsort3).  Threads hold
+// list entries (j) and loop over the
 // group's particles (i) held in shared memory, so the j side sums in
 // registers; the i side (A_i = sum alpha, B_i = sum beta d') is a full-warp
 // butterfly per i, added into FP64 shared accumulators.
@@ -586,7 +627,6 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
         const Group G = load_group(T, g);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
         if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_vjp_fused takes these
-        const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
         const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
@@ -661,9 +701,9 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
                 }
                 if (valid) {
                     double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
-                    atomicAdd(dst, gk3 * (double)vx);
-                    atomicAdd(dst + 1, gk3 * (double)vy);
-                    atomicAdd(dst + 2, gk3 * (double)vz);
+                    atomicAdd(dst, (double)vx);
+                    atomicAdd(dst + 1, (double)vy);
+                    atomicAdd(dst + 2, (double)vz);
                 }
                 __syncthreads();
                 if (threadIdx.x < nic) {
@@ -677,9 +717,9 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
             }
             if (threadIdx.x < nic) {
                 const int32_t p = G.first + i0 + threadIdx.x;
-                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)iwx[threadIdx.x] + sBx));
-                atomicAdd(gs + 3 * (int64_t)p + 1, -gk3 * (sA * (double)iwy[threadIdx.x] + sBy));
-                atomicAdd(gs + 3 * (int64_t)p + 2, -gk3 * (sA * (double)iwz[threadIdx.x] + sBz));
+                atomicAdd(gs + 3 * (int64_t)p, -(sA * (double)iwx[threadIdx.x] + sBx));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -(sA * (double)iwy[threadIdx.x] + sBy));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -(sA * (double)iwz[threadIdx.x] + sBz));
             }
             __syncthreads();
         }
@@ -725,11 +765,11 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
         const Group G = load_group(T, g);
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
-        const double gk3 = G.P->gk2 * (2.0 / G.P->rcut);
         const int ne = bad ? 0 : G.ne;
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
             const int nic = min(kThreads, G.ni - i0);
-            const int npe = (((nic + 1) >> 1) + 1) & ~1;      // particle pairs, rounded up to even
+            const int npr = (nic + 1) >> 1;                    // particle pairs holding particles
+            const int npe = (npr + 1) & ~1;                    // particle pairs, rounded up to even
             __syncthreads();
             if (threadIdx.x < 2 * npe) {
                 const int l = threadIdx.x & 1;
@@ -781,16 +821,20 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                         const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(&IC[pp + P]);
                         const f2 WX = b.y, WY = c.x, WZ = c.y;
                         f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa, sfx = sa, sfy = sa, sfz = sa;
+                        // warp-uniform skips, whose terms would be exact zeros: the
+                        // padding pair of an odd count of particle pairs, and the
+                        // entry slots past the end of the list
+                        const bool live = P == 0 || pp + 1 < npr;
 #pragma unroll
                         for (int u = 0; u < E; u++) {
-                            if (u > 0 && t0 + u * kThreads + warp * 32 >= ne) break;   // warp-uniform: no entries left
+                            if (!live || t0 + u * kThreads + warp * 32 >= ne) break;
                             const f2 dx = f2sub(XJ[u], a.x), dy = f2sub(YJ[u], a.y), dz = f2sub(ZJ[u], b.x);
                             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
                             const f2 s2 = f2add(r2, E2);
                             float r2a, r2b, s2a, s2b;
                             f2unpack(r2, r2a, r2b);
                             f2unpack(s2, s2a, s2b);
-                            const f2 ri = f2pack(rsqrtf(s2a), rsqrtf(s2b));
+                            const f2 ri = f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
                             const f2 x = SOFT ? f2pack(sqrt_approx(s2a), sqrt_approx(s2b))   // xi
                                               : f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
                             f2 gv, gp;
@@ -854,9 +898,9 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                     if (t0 + u * kThreads + (int)threadIdx.x < ne) {
                         float l, h;
                         double *dst = e[u] >= 0 ? gs + 3 * (int64_t)e[u] : ncot + 3 * (int64_t)(-e[u] - 1);
-                        f2unpack(vx[u], l, h); atomicAdd(dst, gk3 * (double)(l + h));
-                        f2unpack(vy[u], l, h); atomicAdd(dst + 1, gk3 * (double)(l + h));
-                        f2unpack(vz[u], l, h); atomicAdd(dst + 2, gk3 * (double)(l + h));
+                        f2unpack(vx[u], l, h); atomicAdd(dst, (double)(l + h));
+                        f2unpack(vy[u], l, h); atomicAdd(dst + 1, (double)(l + h));
+                        f2unpack(vz[u], l, h); atomicAdd(dst + 2, (double)(l + h));
                     }
                 }
                 __syncthreads();
@@ -875,11 +919,9 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                 const int32_t p = G.first + i0 + threadIdx.x;
                 const int64_t o = T.perm[p];
                 const double sA = (double)sh[0] + (double)sl[0];
-                atomicAdd(gs + 3 * (int64_t)p, -gk3 * (sA * (double)cot[3 * o] + ((double)sh[1] + (double)sl[1])));
-                atomicAdd(gs + 3 * (int64_t)p + 1,
-                          -gk3 * (sA * (double)cot[3 * o + 1] + ((double)sh[2] + (double)sl[2])));
-                atomicAdd(gs + 3 * (int64_t)p + 2,
-                          -gk3 * (sA * (double)cot[3 * o + 2] + ((double)sh[3] + (double)sl[3])));
+                atomicAdd(gs + 3 * (int64_t)p, -(sA * (double)cot[3 * o] + ((double)sh[1] + (double)sl[1])));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -(sA * (double)cot[3 * o + 1] + ((double)sh[2] + (double)sl[2])));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -(sA * (double)cot[3 * o + 2] + ((double)sh[3] + (double)sl[3])));
                 if (FWD) {
                     const double gk2 = G.P->gk2;
 #pragma unroll
@@ -937,15 +979,99 @@ __global__ void k_pushdown_leaves(TreeDev T, double *gs, const double *P)
     }
 }
 
+// The pair kernels sum the adjoint without the factor G k^3 (k = 2/r_cut),
+// which is the same for every term of a box, so that its FP64 multiply is
+// taken once per particle here instead of once per entry and tile.
 __global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < T.n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = T.perm[s];
-        grad[3 * o] = gs[3 * s];
-        grad[3 * o + 1] = gs[3 * s + 1];
-        grad[3 * o + 2] = gs[3 * s + 2];
+        const BoxPrm &P = T.box[T.nbox > 1 ? tp_box_of(T.box_off, T.nbox, o) : 0];
+        const double gk3 = P.gk2 * (2.0 / P.rcut);
+        grad[3 * o] = gk3 * gs[3 * s];
+        grad[3 * o + 1] = gk3 * gs[3 * s + 1];
+        grad[3 * o + 2] = gk3 * gs[3 * s + 2];
     }
+}
+
+// Useful pairs (tp_stats.n_useful): the (group particle, list entry) pairs at
+// a positive distance whose cutoff distance -- r, or s = sqrt(r^2 + eps^2)
+// with the softened cutoff argument -- is below r_cut, so that their Eq. 2
+// term is not identically zero.  The decision is the FP64 one of the
+// definition: d = x_j - x_i from the FP64 positions (centres of mass for
+// monopoles), reduced to the minimum image, r^2 = (dx dx + dy dy) + dz dz
+// with every product and sum rounded separately, compared with r_cut^2.  An
+// FP32 estimate of |d'|^2 from the entry records (scaled by k = 2/r_cut)
+// settles every pair that lies clear of both thresholds (0 and the cutoff) by
+// more than its error bound; the few others take the FP64 test.
+__device__ __forceinline__ bool useful_f64(const TreeDev &T, const BoxPrm &P, int32_t i, int32_t e)
+{
+    double xj, yj, zj;
+    if (e >= 0) {
+        xj = T.x[e]; yj = T.y[e]; zj = T.z[e];
+    } else {
+        const int32_t nd = -e - 1;
+        xj = T.comx[nd]; yj = T.comy[nd]; zj = T.comz[nd];
+    }
+    double dx = __dsub_rn(xj, T.x[i]), dy = __dsub_rn(yj, T.y[i]), dz = __dsub_rn(zj, T.z[i]);
+    dx = __dsub_rn(dx, rint(dx));
+    dy = __dsub_rn(dy, rint(dy));
+    dz = __dsub_rn(dz, rint(dz));
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (r2 == 0.0) return false;
+    const double c2 = T.xi_soft ? __dadd_rn(r2, P.eps2) : r2;
+    return c2 < P.rc2;
+}
+
+__global__ void __launch_bounds__(kThreads) k_count_useful(TreeDev T, unsigned long long *useful)
+{
+    __shared__ float px[kThreads], py[kThreads], pz[kThreads];
+    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    unsigned long long cnt = 0;
+    if (*T.status != TP_ERR_LIST_OVERFLOW) {
+        for (int64_t g = blockIdx.x; g < G_n; g += gridDim.x) {
+            const Group G = load_group(T, g);
+            const BoxPrm &P = *G.P;
+            const float sc = P.scale, e2 = T.xi_soft ? P.eps2s : 0.f;
+            // Offsets are at most H = k (h + r_cut) per axis (entries lie within
+            // r_cut of the group box) and carry two FP32 roundings each, so the
+            // estimate of |d'|^2 is off by at most ~2e-6 (H + 1) near the cutoff;
+            // tol keeps a margin of five or more over that.
+            const double hm = fmax(T.ghx[g], fmax(T.ghy[g], T.ghz[g]));
+            const float H = (float)((hm + P.rcut) * (2.0 / P.rcut));
+            const float tol = 1e-5f * (H * H + 1.f);
+            for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
+                const int nic = min(kThreads, G.ni - i0);
+                __syncthreads();
+                if (threadIdx.x < nic) {
+                    const int32_t p = G.first + i0 + threadIdx.x;
+                    px[threadIdx.x] = Arith<float>::from_fixed(T.X[p], G.X, sc);
+                    py[threadIdx.x] = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
+                    pz[threadIdx.x] = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
+                }
+                __syncthreads();
+                for (int q = threadIdx.x; q < G.ne; q += kThreads) {
+                    const float4 r = T.rec[G.e0 + q];
+                    const int32_t e = T.ent[G.e0 + q];
+                    for (int k = 0; k < nic; k++) {
+                        const int32_t i = G.first + i0 + k;
+                        bool u;
+                        if (G.wrap) {
+                            u = useful_f64(T, P, i, e);
+                        } else {
+                            const float dx = r.x - px[k], dy = r.y - py[k], dz = r.z - pz[k];
+                            const float r2 = dx * dx + dy * dy + dz * dz, c2 = r2 + e2;
+                            u = (r2 > tol && fabsf(c2 - 4.f) > tol) ? c2 < 4.f : useful_f64(T, P, i, e);
+                        }
+                        cnt += u ? 1ull : 0ull;
+                    }
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(useful, cnt);
 }
 
 // Launchers, instantiated for the plain (SOFT = false) and the softened
@@ -964,33 +1090,33 @@ void record_timing_event(cudaEvent_t ev, cudaStream_t s)
 using tp::num_sms;
 using tp::occupancy;
 
+// One configuration of the packed forward kernel, on its own occupancy.
+template <int NI, int TS, bool SOFT>
+void launch_pair_packed(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
+{
+    static const int nb = occupancy(k_pair_packed<NI, TS, SOFT>, kThreads);
+    int64_t gr = (int64_t)num_sms() * nb;
+    auto kp = k_pair_packed<NI, TS, SOFT>;
+    TP_LAUNCH(kp, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
+}
+
 template <bool SOFT>
 void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
                         cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles)
 {
     cudaMemsetAsync(queue, 0, 2 * sizeof(int32_t), s);
     static const int bps = occupancy(k_pair<float, true, SOFT>, kThreads);
-    static const int bp1 = occupancy(k_pair_packed<1, SOFT>, kThreads);
-    static const int bp2 = occupancy(k_pair_packed<2, SOFT>, kThreads);
-    static const int bp4 = occupancy(k_pair_packed<4, SOFT>, kThreads);
-    auto grid_of = [&](int per_sm) {
-        int64_t gr = (int64_t)num_sms() * per_sm;
-        return (int)(gr > G ? G : gr);
-    };
     if (ev0) record_timing_event(ev0, s);
-    if (fwd_particles == 1) {
-        auto kp = k_pair_packed<1, SOFT>;
-        TP_LAUNCH(kp, grid_of(bp1), kThreads, 0, s, T, acc, queue + 1, order);
-    } else if (fwd_particles == 4) {
-        auto kp = k_pair_packed<4, SOFT>;
-        TP_LAUNCH(kp, grid_of(bp4), kThreads, 0, s, T, acc, queue + 1, order);
-    } else {
-        auto kp = k_pair_packed<2, SOFT>;
-        TP_LAUNCH(kp, grid_of(bp2), kThreads, 0, s, T, acc, queue + 1, order);
-    }
+    if (fwd_particles == 1)
+        launch_pair_packed<1, 8, SOFT>(T, acc, queue + 1, order, G, s);
+    else if (fwd_particles == 4)
+        launch_pair_packed<4, 8, SOFT>(T, acc, queue + 1, order, G, s);
+    else
+        launch_pair_packed<2, 8, SOFT>(T, acc, queue + 1, order, G, s);
     if (ev1) record_timing_event(ev1, s);
+    const int64_t gr = (int64_t)num_sms() * bps;
     auto k = k_pair<float, true, SOFT>;
-    TP_LAUNCH(k, grid_of(bps), kThreads, 0, s, T, acc, queue, order);
+    TP_LAUNCH(k, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
 }
 
 // The fused adjoint kernel with E entries per thread, with or without the
@@ -1136,6 +1262,14 @@ void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, d
         pair_rest_f32_t<true>(T, acc, queue, order, G, s);
     else
         pair_rest_f32_t<false>(T, acc, queue, order, G, s);
+}
+
+// Useful-pair count of whole lists into *useful (zeroed by the caller).
+void count_useful(TreeDev &T, unsigned long long *useful, cudaStream_t s)
+{
+    if (T.cap_groups <= 0) return;
+    const int64_t gr = (int64_t)num_sms() * 8;
+    TP_LAUNCH(k_count_useful, (int)(gr > T.cap_groups ? T.cap_groups : gr), kThreads, 0, s, T, useful);
 }
 
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,

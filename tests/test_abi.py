@@ -68,3 +68,24 @@ def test_pm_invalid_arguments_rejected_without_touching_the_gpu(lib):
     assert L.tp_pm_force(None, None, None, 10, None, 0, None) == -1
     assert L.tp_pm_vjp(None, None, None, 10, None, None, 0, None) == -1
     assert L.tp_pm_free(None) == 0
+
+
+def test_stats_struct_layout_matches_the_header(tmp_path):
+    """The binding's tp_stats mirrors the header's struct field by field: the
+    same names in the same order at the same offsets (checked by compiling
+    the header with the host C compiler)."""
+    import subprocess
+
+    from paper_1211_4406_gb300 import _lib
+    fields = [f for f, _ in _lib.TPStats._fields_]
+    assert "n_useful" in fields
+    src = tmp_path / "layout.c"
+    body = "".join(f'    printf("%s %zu\\n", "{f}", offsetof(tp_stats, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "treepm_sr.h"\nint main(void) {\n'
+                   f'{body}    printf("size %zu\\n", sizeof(tp_stats));\n    return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.TPStats, f).offset, f
+    assert int(out["size"]) == ctypes.sizeof(_lib.TPStats)

@@ -67,3 +67,35 @@ def test_wrong_sizes_and_dtypes_are_refused_before_the_library():
     axpy(y, cot, 2.0)
     torch.cuda.synchronize()
     assert torch.equal(y, 2.0 * cot.double())
+
+
+def test_calls_on_a_side_stream_match_the_current_stream():
+    """A call given another stream waits for the binding's conversions on the
+    current stream and keeps their memory alive: forces and the adjoint of a
+    float64 cotangent (converted by the binding) on a side stream equal those
+    on the current stream (the forces bit for bit), and so does the PM force
+    up to the order of its FP32 mass-assignment atomics."""
+    torch.manual_seed(5)
+    n = 4096
+    dev = torch.device("cuda")
+    pos = torch.rand((n, 3), dtype=torch.float64, device=dev)
+    mass = torch.full((n,), 1.0 / n, dtype=torch.float64, device=dev)
+    cot = torch.randn((n, 3), dtype=torch.float64, device=dev)
+    prm = Params(G=1.0, eps=1e-3, r_cut=0.1, theta=0.5, n_crit=32)
+    t = ShortRangeTree(pos, mass, prm)
+    a0, g0 = t.force(), t.vjp(cot)
+    pm = PMSolver(32, 0.1, 1.0)
+    p0 = pm.force(pos, mass)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        t.rebuild(pos.clone(), mass.clone(), stream=side)   # temporaries freed at once on this side
+        a1 = t.force(stream=side)
+        g1 = t.vjp(cot * 1.0, stream=side)
+        p1 = pm.force(pos.clone(), mass, stream=side)
+        side.synchronize()
+        assert torch.equal(a0, a1)
+        assert float((p0 - p1).abs().max()) <= 1e-5 * float(p0.abs().max())
+        assert float((g0 - g1).abs().max()) <= 1e-12 * float(g0.abs().max())
+    t.close()
+    pm.close()

@@ -149,6 +149,7 @@ def test_clustered_2M_full_size():
     ref = ot.list_forces(box.G, box.eps, box.r_cut)
     rms, mx = rel_err(gt.force().double().cpu().numpy(), ref)
     assert rms <= FP32_RMS and mx <= FP32_MAX, (rms, mx)
+    assert gt.stats()["n_useful"] == ot.count_useful(box.eps, box.r_cut)
 
 
 def test_vjp_against_oracle_adjoint():
@@ -240,3 +241,21 @@ def test_lognormal_masses_far_images_and_default_mass():
     t_none = ShortRangeTree(p, None, prm)
     t_expl = ShortRangeTree(p, torch.full((base.n,), 1.0 / base.n, dtype=torch.float64, device="cuda"), prm)
     assert torch.equal(t_none.force(), t_expl.force())
+
+
+@pytest.mark.parametrize("box", small_boxes() + [inputs.config_box(1), inputs.config_box(4)],
+                         ids=lambda b: b.name)
+def test_useful_pairs_bit_exact(box):
+    """tp_stats.n_useful (evaluated pairs with a non-zero Eq. 2 term) equals
+    the oracle's FP64 count on identical lists, for both cutoff arguments."""
+    for xi in ("plain", "softened"):
+        pos = torch.tensor(box.pos, device="cuda")
+        mass = torch.tensor(box.mass, device="cuda")
+        gt = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf,
+                                              "fp32", xi=xi))
+        st = gt.stats()
+        gt.close()
+        ot = oracle_tree(box)
+        want = ot.count_useful(box.eps, box.r_cut, xi_softened=xi == "softened")
+        assert st["n_useful"] == want, (xi, st["n_useful"], want)
+        assert 0 <= st["n_useful"] <= st["n_interactions"]
