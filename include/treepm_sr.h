@@ -351,6 +351,75 @@ tp_status tp_pm_export_mesh(tp_pm *pm, int32_t which, float *host);
 /* Releases the mesh and plans (synchronises the device).  NULL is a no-op.  */
 tp_status tp_pm_free(tp_pm *pm);
 
+/* ------------------------------------------------------------------------
+ * Spatial decomposition of one box over several GPUs (Sec. II: the box is cut
+ * into rectangular domains by a 3-D multi-section decomposition, one per
+ * process; each process evaluates the short-range forces on the particles of
+ * its domain).  Because the short-range force vanishes beyond r_cut, a
+ * domain needs, besides its own particles, only the particles within r_cut of
+ * its box ("ghosts"; the paper's processes exchange tree data for the same
+ * reason).  A tp_halo holds one geometry and selects, on the device, which
+ * particles go where:
+ *   - owner selection: every particle to the domain that holds it (the
+ *     particle exchange after the domains move);
+ *   - ghost selection: every particle of domain `self` to every other domain
+ *     whose box lies within r_cut of it, periodic distance.
+ * The tree, the walk and the pair kernels then run unchanged on each
+ * process's own particles followed by its ghosts (the forces on the ghosts
+ * are discarded, and their share of the adjoint goes back to their owners).
+ * The collectives themselves (variable all-to-all) belong to the caller.
+ *
+ * Geometry: nx slabs along x cut at xc[0..nx]; slab i is cut into ny columns
+ * at yc[i][0..ny]; column (i, j) into nz cells at zc[i][j][0..nz].  Domain
+ * d = (i ny + j) nz + k is the half-open box [xc[i], xc[i+1]) x
+ * [yc[i][j], yc[i][j+1]) x [zc[i][j][k], zc[i][j][k+1]).  Every list of cuts
+ * starts at 0, ends at 1 and is non-decreasing.  Positions are wrapped into
+ * [0,1) first, as the tree does.  Decisions are FP64 with every operation
+ * rounded separately: the owner by the largest cut <= the coordinate, the
+ * ghost test by the squared periodic point-to-box distance < r_cut^2, the
+ * per-axis distance being 0 inside the box and otherwise the shorter of
+ * (lo - p) and (p + 1) - hi when p < lo, of (p - hi) and (lo + 1) - p when
+ * p >= hi.  (No counterpart in the paper for the interface itself.)       */
+#define TP_MAX_DOMAINS 4096
+#define TP_HALO_OWNER 0
+#define TP_HALO_GHOSTS 1
+typedef struct tp_halo tp_halo; /* opaque, library-owned */
+
+/* A geometry of nx x ny x nz domains (1 <= nx ny nz <= TP_MAX_DOMAINS),
+ * without cuts yet.  Allocates a few device buffers.                        */
+tp_status tp_halo_create(int32_t nx, int32_t ny, int32_t nz, tp_halo **out);
+
+/* Sets the cuts: xc host [nx+1], yc host [nx][ny+1], zc host [nx][ny][nz+1]
+ * (layout above).  TP_ERR_INVALID_ARG unless every list starts at 0, ends at
+ * 1 and is non-decreasing.  Synchronous (copies to the device).            */
+tp_status tp_halo_set_cuts(tp_halo *h, const double *xc, const double *yc, const double *zc);
+
+/* Selects particles of pos (device FP64 [n][3], finite) for each domain:
+ * mode TP_HALO_OWNER (self and r_cut ignored) or TP_HALO_GHOSTS (0 <= self <
+ * ndom, 0 < r_cut < 0.5).  Writes the selected particle indices to idx
+ * (device int32 [cap]) grouped by destination domain, domain 0 first, in
+ * ascending order within each destination, and the number per destination
+ * to counts (host int64 [nx ny nz]).  Synchronises `stream` once.  Returns
+ * TP_ERR_LIST_OVERFLOW when the total exceeds cap (counts are still filled:
+ * call again with a larger idx; cap = 0 only counts), TP_ERR_NONFINITE for a
+ * NaN or infinite position.  The count scratch grows with n (allocation).   */
+tp_status tp_halo_select(tp_halo *h, const double *pos, int64_t n, int32_t mode, int32_t self, double r_cut,
+                         int32_t *idx, int64_t cap, int64_t *counts, void *stream);
+
+/* Releases the halo (synchronises the device).  NULL is a no-op.            */
+tp_status tp_halo_free(tp_halo *h);
+
+/* Row gather for packing exchange buffers: dst[r] = src[idx[r]] for rows of
+ * `words` 32-bit words (FP64 positions: 6, FP64 masses or int64 ids: 2, FP32
+ * 3-vectors: 3); all device; m rows.  Asynchronous.                         */
+tp_status tp_gather_rows(const void *src, int32_t words, const int32_t *idx, int64_t m, void *dst, void *stream);
+
+/* Scatter-add of FP64 rows of `width` values: dst[idx[r]] += src[r] (device;
+ * FP64 atomics, so repeated indices sum in an unspecified order).  For
+ * returning the ghosts' share of the adjoint to their owners.  Asynchronous. */
+tp_status tp_scatter_add_rows(double *dst, int32_t width, const int32_t *idx, const double *src, int64_t m,
+                              void *stream);
+
 /* Leapfrog helpers for the kick-drift-kick integrator (y += a * x):
  * y: device double [n]; x: device [n], float when x_is_f32 else double.     */
 tp_status tp_axpy(double *y, const void *x, int32_t x_is_f32, double a, int64_t n,

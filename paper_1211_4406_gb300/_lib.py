@@ -79,6 +79,12 @@ SIGNATURES = {
     "tp_pm_export_mesh": ([_V, _I32, _V], C.c_int),
     "tp_pm_free": ([_V], C.c_int),
     "tp_status_string": ([C.c_int], C.c_char_p),
+    "tp_halo_create": ([_I32, _I32, _I32, C.POINTER(_V)], C.c_int),
+    "tp_halo_set_cuts": ([_V, _V, _V, _V], C.c_int),
+    "tp_halo_select": ([_V, _V, _I64, _I32, _I32, _D, _V, _I64, _V, _V], C.c_int),
+    "tp_halo_free": ([_V], C.c_int),
+    "tp_gather_rows": ([_V, _I32, _V, _I64, _V, _V], C.c_int),
+    "tp_scatter_add_rows": ([_V, _I32, _V, _V, _I64, _V], C.c_int),
 }
 
 _lib = None
