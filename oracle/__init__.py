@@ -73,6 +73,9 @@ def _load():
                                          C.c_double, _D, C.c_int]
     lib.or_list_vjp_range.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                       C.c_double, _D, _D, C.c_int]
+    lib.or_list_loss_groups.restype = C.c_double
+    lib.or_list_loss_groups.argtypes = [C.c_void_p, _I64, C.c_int64, C.c_double, C.c_double, C.c_double, _D,
+                                        C.c_int]
     lib.or_count_useful.restype = C.c_int64
     lib.or_count_useful.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
     lib.or_refresh_moments.argtypes = [C.c_void_p, _D]
@@ -266,6 +269,14 @@ class OracleTree:
         _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad),
                                   int(xi_softened))
         return grad
+
+    def list_loss_groups(self, groups, G, eps, rcut, w, xi_softened=False) -> float:
+        """sum over the given groups' particles i of w_i . a_i (list forces)."""
+        assert self.has_lists
+        g = np.ascontiguousarray(groups, dtype=np.int64)
+        w = _f64(w)
+        return float(_load().or_list_loss_groups(self._h, g.ctypes.data_as(_I64), g.size, G, eps, rcut, _dp(w),
+                                                 int(xi_softened)))
 
     def count_useful(self, eps, rcut, xi_softened=False) -> int:
         """Pairs (group particle, list entry other than itself) at a positive

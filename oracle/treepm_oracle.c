@@ -681,6 +681,34 @@ void or_list_forces(const or_tree *t, double G, double eps, double rcut, double 
     or_list_forces_range(t, 0, t->n_groups, G, eps, rcut, acc, xi_soft);
 }
 
+/* sum over the groups groups[0..ng) of sum_i w_i . a_i, a_i the list force of
+ * or_list_forces (input-order w): the part of a loss linear in the
+ * accelerations that the listed groups carry.  Central differences of a
+ * frozen tree need only the groups whose lists see the moved particle. */
+double or_list_loss_groups(const or_tree *t, const int64_t *groups, int64_t ng, double G, double eps,
+                           double rcut, const double *wv, int xi_soft)
+{
+    or_prm P = make_prm_xi(G, eps, rcut, xi_soft);
+    double total = 0.0;
+    for (int64_t q = 0; q < ng; q++) {
+        int64_t g = groups[q];
+        for (int64_t i = t->gfirst[g]; i < t->gfirst[g] + t->gcount[g]; i++) {
+            double ax = 0, ay = 0, az = 0;
+            for (int64_t e2 = t->loff[g]; e2 < t->loff[g + 1]; e2++) {
+                int64_t e = t->ent[e2];
+                if (e == i) continue;
+                double xj[3], mj;
+                entry_src(t, e, xj, &mj);
+                pair_acc(minimg(xj[0] - t->xb[0][i]), minimg(xj[1] - t->xb[1][i]),
+                         minimg(xj[2] - t->xb[2][i]), mj, &P, &ax, &ay, &az);
+            }
+            const double *w = wv + 3 * t->perm[i];
+            total += (w[0] * ax + w[1] * ay) + w[2] * az;
+        }
+    }
+    return total;
+}
+
 /* Pairs of the lists whose Eq. 2 term is not identically zero: over every
  * group, every member particle i and every list entry (particle or monopole)
  * other than i itself, count the pair when its distance r is positive and its

@@ -410,3 +410,22 @@ def test_count_useful_brute_force_with_monopoles():
             assert keep[ent < 0].all()
     assert n_nodes_entries > 0
     assert t.count_useful(eps, rc) == count
+
+
+def test_list_loss_over_groups_is_the_loss_of_their_particles():
+    """or_list_loss_groups over a set of groups equals sum w . a over those
+    groups' particles from the (pinned) list forces, and over all groups the
+    whole loss."""
+    pos, mass = inputs.clustered_box(4000, 8, 17)
+    rc, eps, G = 0.1, 2e-3, 1.3
+    t = oracle.OracleTree(pos, mass, 8, 32)
+    t.lists(rc, 0.5)
+    ex = t.export()
+    w = inputs.cotangent(4000, 5).astype(np.float64)
+    acc = t.list_forces(G, eps, rc)
+    groups = [3, 17, 0, 40]
+    rows = np.concatenate([ex.perm[ex.gfirst[g]:ex.gfirst[g] + ex.gcount[g]] for g in groups])
+    want = float(np.sum(w[rows] * acc[rows]))
+    assert abs(t.list_loss_groups(groups, G, eps, rc, w) - want) <= 1e-12 * np.abs(w[rows] * acc[rows]).sum()
+    everything = t.list_loss_groups(np.arange(ex.gfirst.size), G, eps, rc, w)
+    assert abs(everything - float(np.sum(w * acc))) <= 1e-12 * np.abs(w * acc).sum()
