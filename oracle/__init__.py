@@ -50,6 +50,11 @@ def _load():
     lib.or_g.argtypes = [C.c_double]
     lib.or_gpx.restype = C.c_double
     lib.or_gpx.argtypes = [C.c_double]
+    for name in ("or_rsqrt_seed", "or_rsqrt_refined"):
+        getattr(lib, name).restype = C.c_double
+        getattr(lib, name).argtypes = [C.c_double]
+    lib.or_rsqrt_third_order.restype = C.c_double
+    lib.or_rsqrt_third_order.argtypes = [C.c_double, C.c_double]
     lib.or_pair.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double, _D, C.c_int]
     lib.or_pair_jw.argtypes = [_D, C.c_double, _D, C.c_double, C.c_double, C.c_double, _D, C.c_int]
     lib.or_brute_force.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_double, _D, C.c_int]
@@ -98,6 +103,27 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _variant(xi_softened=False, rsqrt_refined=False) -> int:
+    """The variant bitmask of the C functions: 1 = softened cutoff argument,
+    2 = the paper's refined inverse square root for 1/s^3."""
+    return int(bool(xi_softened)) | (2 if rsqrt_refined else 0)
+
+
+def rsqrt_seed(x: float) -> float:
+    """The estimate of 1/sqrt(x) that the refinement starts from."""
+    return float(_load().or_rsqrt_seed(float(x)))
+
+
+def rsqrt_third_order(x: float, y0: float) -> float:
+    """The paper's third-order step from an estimate y0 of 1/sqrt(x)."""
+    return float(_load().or_rsqrt_third_order(float(x), float(y0)))
+
+
+def rsqrt_refined(x: float) -> float:
+    """1/sqrt(x) by the paper's refinement of rsqrt_seed(x)."""
+    return float(_load().or_rsqrt_refined(float(x)))
+
+
 def num_threads() -> int:
     return int(_load().or_num_threads())
 
@@ -118,60 +144,60 @@ def gpx(xi) -> np.ndarray | float:
     return np.array([lib.or_gpx(float(v)) for v in np.ravel(xi)]).reshape(np.shape(xi))
 
 
-def pair(d, mj, G, eps, rcut, xi_softened=False) -> np.ndarray:
+def pair(d, mj, G, eps, rcut, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     """One term of Eq. 2: acceleration from mass mj at offset d = x_j - x_i.
     xi_softened: take the cutoff argument of Eq. 3 from the softened distance
     sqrt(r^2 + eps^2) (the paper's kernel form) instead of r; every force and
     adjoint function below takes the same switch."""
     d = _f64(d)
     out = np.zeros(3)
-    _load().or_pair(_dp(d), float(mj), float(G), float(eps), float(rcut), _dp(out), int(xi_softened))
+    _load().or_pair(_dp(d), float(mj), float(G), float(eps), float(rcut), _dp(out), _variant(xi_softened, rsqrt_refined))
     return out
 
 
-def pair_jw(d, mj, w, G, eps, rcut, xi_softened=False) -> np.ndarray:
+def pair_jw(d, mj, w, G, eps, rcut, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     """G mj J(d) w for the Jacobian J of one Eq. 2 term."""
     d, w = _f64(d), _f64(w)
     out = np.zeros(3)
     _load().or_pair_jw(_dp(d), float(mj), _dp(w), float(G), float(eps), float(rcut), _dp(out),
-                       int(xi_softened))
+                       _variant(xi_softened, rsqrt_refined))
     return out
 
 
-def brute_force(pos, mass, G, eps, rcut, xi_softened=False) -> np.ndarray:
+def brute_force(pos, mass, G, eps, rcut, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     """Eq. 2 summed over all pairs (O(N^2), periodic minimum image)."""
     pos, mass = _f64(pos), _f64(mass)
     n = pos.shape[0]
     acc = np.zeros((n, 3))
-    _load().or_brute_force(n, _dp(pos), _dp(mass), G, eps, rcut, _dp(acc), int(xi_softened))
+    _load().or_brute_force(n, _dp(pos), _dp(mass), G, eps, rcut, _dp(acc), _variant(xi_softened, rsqrt_refined))
     return acc
 
 
-def brute_force_sample(pos, mass, G, eps, rcut, idx, xi_softened=False) -> np.ndarray:
+def brute_force_sample(pos, mass, G, eps, rcut, idx, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     pos, mass = _f64(pos), _f64(mass)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     acc = np.zeros((idx.size, 3))
     _load().or_brute_force_sample(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, idx.size,
-                                  idx.ctypes.data_as(_I64), _dp(acc), int(xi_softened))
+                                  idx.ctypes.data_as(_I64), _dp(acc), _variant(xi_softened, rsqrt_refined))
     return acc
 
 
-def brute_vjp(pos, mass, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
+def brute_vjp(pos, mass, G, eps, rcut, w, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     """dL/dx of L = sum_i w_i . a_i for the direct sum."""
     pos, mass, w = _f64(pos), _f64(mass), _f64(w)
     grad = np.zeros_like(pos)
     _load().or_brute_vjp(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), _dp(grad),
-                         int(xi_softened))
+                         _variant(xi_softened, rsqrt_refined))
     return grad
 
 
-def brute_vjp_sample(pos, mass, G, eps, rcut, w, idx, xi_softened=False) -> np.ndarray:
+def brute_vjp_sample(pos, mass, G, eps, rcut, w, idx, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
     """Rows idx of brute_vjp (each O(N)), for boxes too large for the full sum."""
     pos, mass, w = _f64(pos), _f64(mass), _f64(w)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     grad = np.zeros((idx.size, 3))
     _load().or_brute_vjp_sample(pos.shape[0], _dp(pos), _dp(mass), G, eps, rcut, _dp(w), idx.size,
-                                idx.ctypes.data_as(_I64), _dp(grad), int(xi_softened))
+                                idx.ctypes.data_as(_I64), _dp(grad), _variant(xi_softened, rsqrt_refined))
     return grad
 
 
@@ -240,43 +266,43 @@ class OracleTree:
         self.has_lists = True
         return n_ent
 
-    def list_forces(self, G, eps, rcut, xi_softened=False) -> np.ndarray:
+    def list_forces(self, G, eps, rcut, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
         assert self.has_lists
         acc = np.zeros((self.n, 3))
-        _load().or_list_forces(self._h, G, eps, rcut, _dp(acc), int(xi_softened))
+        _load().or_list_forces(self._h, G, eps, rcut, _dp(acc), _variant(xi_softened, rsqrt_refined))
         return acc
 
-    def list_vjp(self, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
+    def list_vjp(self, G, eps, rcut, w, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
         assert self.has_lists
         w = _f64(w)
         grad = np.zeros((self.n, 3))
-        _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad), int(xi_softened))
+        _load().or_list_vjp(self._h, G, eps, rcut, _dp(w), _dp(grad), _variant(xi_softened, rsqrt_refined))
         return grad
 
-    def list_forces_range(self, g0, g1, G, eps, rcut, xi_softened=False) -> np.ndarray:
+    def list_forces_range(self, g0, g1, G, eps, rcut, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
         """Forces of groups [g0, g1) only (other rows stay zero)."""
         assert self.has_lists
         acc = np.zeros((self.n, 3))
         _load().or_list_forces_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(acc),
-                                     int(xi_softened))
+                                     _variant(xi_softened, rsqrt_refined))
         return acc
 
-    def list_vjp_range(self, g0, g1, G, eps, rcut, w, xi_softened=False) -> np.ndarray:
+    def list_vjp_range(self, g0, g1, G, eps, rcut, w, xi_softened=False, rsqrt_refined=False) -> np.ndarray:
         """Gradient of sum over groups [g0, g1) of w_i . a_i."""
         assert self.has_lists
         w = _f64(w)
         grad = np.zeros((self.n, 3))
         _load().or_list_vjp_range(self._h, int(g0), int(g1), G, eps, rcut, _dp(w), _dp(grad),
-                                  int(xi_softened))
+                                  _variant(xi_softened, rsqrt_refined))
         return grad
 
-    def list_loss_groups(self, groups, G, eps, rcut, w, xi_softened=False) -> float:
+    def list_loss_groups(self, groups, G, eps, rcut, w, xi_softened=False, rsqrt_refined=False) -> float:
         """sum over the given groups' particles i of w_i . a_i (list forces)."""
         assert self.has_lists
         g = np.ascontiguousarray(groups, dtype=np.int64)
         w = _f64(w)
         return float(_load().or_list_loss_groups(self._h, g.ctypes.data_as(_I64), g.size, G, eps, rcut, _dp(w),
-                                                 int(xi_softened)))
+                                                 _variant(xi_softened, rsqrt_refined)))
 
     def count_useful(self, eps, rcut, xi_softened=False) -> int:
         """Pairs (group particle, list entry other than itself) at a positive
@@ -284,7 +310,7 @@ class OracleTree:
         xi_softened) is below r_cut: the evaluated pairs whose Eq. 2 term is not
         identically zero."""
         assert self.has_lists
-        return int(_load().or_count_useful(self._h, eps, rcut, int(xi_softened)))
+        return int(_load().or_count_useful(self._h, eps, rcut, int(bool(xi_softened))))
 
     def refresh(self, pos) -> None:
         """Re-take monopoles from new positions with the structure frozen."""
@@ -316,7 +342,7 @@ class OracleTree:
                     gcen=gd[:, 0:3], ghalf=gd[:, 3:6], loff=loff, ent=ent)
 
 
-def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64, xi_softened=False):
+def tree_forces(pos, mass, G, eps, rcut, theta, n_leaf=8, n_crit=64, xi_softened=False, rsqrt_refined=False):
     """Build, list and sum: the oracle's whole short-range force path."""
     t = OracleTree(pos, mass, n_leaf, n_crit)
     t.lists(rcut, theta)

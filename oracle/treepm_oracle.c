@@ -28,7 +28,9 @@
  * Readings where the paper is silent (every one is listed in the design notes):
  *   - softening: 1/|r|^3 -> 1/(r^2+eps^2)^{3/2}; the cutoff argument uses the
  *     unsoftened r; pairs with r >= r_cut or r == 0 contribute exactly 0.
- *     Every force and adjoint function also takes xi_soft: when set, the
+ *     Every force and adjoint function also takes xi_soft, a bitmask: bit 1
+ *     selects the softened cutoff argument below, bit 2 the paper's refined
+ *     inverse square root (or_rsqrt_refined) for 1/s^3.  With bit 1 set, the
  *     cutoff argument is the softened distance s = sqrt(r^2 + eps^2) instead
  *     (the paper's kernel form), and pairs with s >= r_cut contribute 0.
  *   - keys: x wrapped to [0,1), quantised to 21 bits, x bit highest in each
@@ -102,7 +104,42 @@ typedef struct {
     double G, eps, rcut, theta;
     double rc2, eps2, th2;
     int soft;                  /* cutoff argument from the softened distance */
+    int rsq;                   /* 1/s from the refined estimate (or_rsqrt_refined) */
 } or_prm;
+
+/* The paper's inverse square root (Sec. II-A): a low-accuracy estimate y0 of
+ * 1/sqrt(x) refined by one third-order step, h0 = 1 - x y0^2 and
+ * y1 = y0 (1 + h0/2 + 3 h0^2/8).  With y0 = (1 + e)/sqrt(x) the result is
+ * (1 + 5/2 e^3 + 15/8 e^4 + 3/8 e^5)/sqrt(x) exactly.                     */
+double or_rsqrt_third_order(double x, double y0)
+{
+    double h0 = 1.0 - x * (y0 * y0);
+    return y0 * ((1.0 + 0.5 * h0) + 0.375 * (h0 * h0));
+}
+
+/* The estimate the refinement starts from.  The K computer's instruction gives
+ * 8 bits; a GPU has no such instruction, and its counterpart here is the
+ * integer estimate of Lomont (2003, "Fast inverse square root"): the FP32 bit
+ * pattern of x shifted right by one and subtracted from 0x5f3759df (relative
+ * error below 3.5e-2), improved by one Newton step y (3/2 - x y^2/2) to below
+ * 1.8e-3, about the paper's 8 to 9 bits.  x > 0 and finite.                 */
+double or_rsqrt_seed(double x)
+{
+    float xf = (float)x, yf;
+    uint32_t b;
+    memcpy(&b, &xf, sizeof b);
+    b = 0x5f3759dfu - (b >> 1);
+    memcpy(&yf, &b, sizeof yf);
+    double y = (double)yf;
+    return y * (1.5 - (0.5 * x) * (y * y));
+}
+
+/* 1/sqrt(x) by the paper's refinement of the estimate above: relative error
+ * 5/2 e^3 + O(e^4) <= 1.5e-8 for |e| <= 1.8e-3.                            */
+double or_rsqrt_refined(double x)
+{
+    return or_rsqrt_third_order(x, or_rsqrt_seed(x));
+}
 
 static or_prm make_prm(double G, double eps, double rcut, double theta)
 {
@@ -110,14 +147,31 @@ static or_prm make_prm(double G, double eps, double rcut, double theta)
     p.G = G; p.eps = eps; p.rcut = rcut; p.theta = theta;
     p.rc2 = rcut * rcut; p.eps2 = eps * eps; p.th2 = theta * theta;
     p.soft = 0;
+    p.rsq = 0;
     return p;
 }
 
+/* variant: bit 1 = softened cutoff argument, bit 2 = refined inverse square
+ * root (the "xi_soft" argument of the functions below). */
 static or_prm make_prm_xi(double G, double eps, double rcut, int xi_soft)
 {
     or_prm p = make_prm(G, eps, rcut, 0.0);
-    p.soft = xi_soft != 0;
+    p.soft = (xi_soft & 1) != 0;
+    p.rsq = (xi_soft & 2) != 0;
     return p;
+}
+
+/* 1/s^3 and 1/s^2 from s^2: exact, or through the paper's refinement. */
+static inline void inv_s3(const or_prm *P, double s2, double *is3, double *is2)
+{
+    if (P->rsq) {
+        double y = or_rsqrt_refined(s2);
+        *is2 = y * y;
+        *is3 = *is2 * y;
+    } else {
+        *is3 = 1.0 / (s2 * sqrt(s2));
+        *is2 = 1.0 / s2;
+    }
 }
 
 /* One term of Eq. 2: acceleration of i due to mass mj at minimum-image offset
@@ -134,7 +188,14 @@ static inline void pair_acc(double dx, double dy, double dz, double mj,
     double c2 = P->soft ? s2 : r2;
     if (!(c2 < P->rc2)) return;
     double g = or_g(2.0 * sqrt(c2) / P->rcut);
-    double fac = P->G * mj * g / (s2 * sqrt(s2));
+    double fac;
+    if (P->rsq) {
+        double is3, is2;
+        inv_s3(P, s2, &is3, &is2);
+        fac = P->G * mj * g * is3;
+    } else {
+        fac = P->G * mj * g / (s2 * sqrt(s2));
+    }
     *ax += fac * dx;
     *ay += fac * dy;
     *az += fac * dz;
@@ -157,10 +218,18 @@ static inline void pair_jw(double dx, double dy, double dz, double mj,
     double xi = 2.0 * sqrt(c2) / P->rcut;
     double g = or_g(xi);
     double gp = or_gpx(xi);
-    double s3 = s2 * sqrt(s2);
     double k = 2.0 / P->rcut;
-    double phi = g / s3;
-    double dphi = k * k * gp / s3 - 3.0 * g / (s3 * s2);
+    double phi, dphi;
+    if (P->rsq) {
+        double is3, is2;
+        inv_s3(P, s2, &is3, &is2);
+        phi = g * is3;
+        dphi = k * k * gp * is3 - 3.0 * g * (is3 * is2);
+    } else {
+        double s3 = s2 * sqrt(s2);
+        phi = g / s3;
+        dphi = k * k * gp / s3 - 3.0 * g / (s3 * s2);
+    }
     double dw = (dx * w[0] + dy * w[1]) + dz * w[2];
     double c = P->G * mj;
     v[0] = c * (phi * w[0] + dphi * dw * dx);
