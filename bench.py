@@ -162,6 +162,18 @@ def max_over_ranks(values, device=None):
     return [float(v) for v in t.tolist()]
 
 
+def sum_over_ranks(values, device=None):
+    """Element-wise sum of `values` over all ranks of the default process
+    group (the values themselves when no group is initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
 def whole_job_rate(world, units_per_step, steps, total_ms):
     """Units all ranks processed per second over the slowest rank's time:
     every rank runs the same fixed per-rank workload (weak scaling)."""
@@ -171,7 +183,8 @@ def whole_job_rate(world, units_per_step, steps, total_ms):
 # ---------------------------------------------------------------------------
 # the reference arm: the CPU FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None, xi_softened=False):
+def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=None, xi_softened=False,
+                       rsqrt_refined=False):
     """Time the oracle: build + lists once, then `steps` samples of forward +
     adjoint over a contiguous range of groups holding ~target_fraction of the
     interactions.  Each step is charged its share of the build + lists time."""
@@ -191,8 +204,9 @@ def oracle_sample_rate(box, w, target_fraction=0.03, steps=1, warmup=0, report=N
     times = []
     for s in range(warmup + steps):
         t0 = time.perf_counter()
-        ot.list_forces_range(0, g1, box.G, box.eps, box.r_cut, xi_softened=xi_softened)
-        ot.list_vjp_range(0, g1, box.G, box.eps, box.r_cut, w64, xi_softened=xi_softened)
+        ot.list_forces_range(0, g1, box.G, box.eps, box.r_cut, xi_softened=xi_softened, rsqrt_refined=rsqrt_refined)
+        ot.list_vjp_range(0, g1, box.G, box.eps, box.r_cut, w64, xi_softened=xi_softened,
+                          rsqrt_refined=rsqrt_refined)
         dt = time.perf_counter() - t0 + frac * t_build
         if s >= warmup:
             times.append(dt)
@@ -211,7 +225,8 @@ def run_reference(args, rank, world):
     box = inputs.config_box(CONFIG_K)
     w = inputs.cotangent(box.n, box.seed + 7)
     r = oracle_sample_rate(box, w, steps=args.steps, warmup=args.warmup,
-                           xi_softened=getattr(args, "xi", "plain") == "softened")
+                           xi_softened=getattr(args, "xi", "plain") == "softened",
+                           rsqrt_refined=getattr(args, "rsqrt", "hardware") == "refined")
     total_t = sum(r["times"])
     value = r["per_step_interactions"] * len(r["times"]) / total_t
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -254,11 +269,12 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     pos = pos_h.to(dev)
     mass = mass_h.to(dev)
     cot = cot_h.to(dev)
-    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32", xi=args.xi)
+    prm = Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32", xi=args.xi,
+                 rsqrt=args.rsqrt)
     tree = ShortRangeTree(pos, mass, prm)                   # allocating build (setup)
     st = tree.stats()
     wl = workload_config(paper_regime)["workload"]
-    xkey = "" if args.xi == "plain" else "|xi-softened"
+    xkey = ("" if args.xi == "plain" else "|xi-softened") + ("" if args.rsqrt == "hardware" else "|rsqrt-refined")
     tile = autotune.tune_tile(tree, pos, mass, cot, key=f"{wl}|n{box.n}{xkey}")   # setup, not timed
     acc = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
     grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
@@ -407,11 +423,15 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     def roofline(kernel, ms, flops, note):
         ach = flops * inter / (ms * 1e-3)
         return {"bound": "alu", "achieved": ach / 1e12, "peak": fp32_pk / 1e12, "unit": "TFLOP/s",
-                "frac": ach / fp32_pk, "traffic": traffic_for(kernel, box.n, wl), "kernel": f"{kernel} ({note})",
+                "frac": ach / fp32_pk,
+                "traffic": traffic_for(kernel, st["n_entries"]) if wl == "clustered-2M" else None,
+                "traffic_basis": "ncu DRAM bytes of a 2^19-particle box of the same recipe, scaled by list entries",
+                "kernel": f"{kernel} ({note})",
                 "ms_per_launch": ms, "flops_per_interaction": flops, "peak_basis": peak_basis}
 
     kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)
     soft = "true" if args.xi == "softened" else "false"
+    rf = "true" if args.rsqrt == "refined" else "false"
     meas_ffma = measure_peak("fp32")
     meas_ffma2 = measure_peak("fp32x2")
     meas_dfma = measure_peak("fp64")
@@ -422,13 +442,15 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(paper_regime), tile_autotuned={"forward_particles_per_thread": tile[0],
                                                           "adjoint_entries_per_thread": tile[1]},
-                       **({} if args.xi == "plain" else {"xi": "softened: cutoff argument 2 sqrt(r^2+eps^2)/r_cut"})),
-        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true, {soft}>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
+                       **({} if args.xi == "plain" else {"xi": "softened: cutoff argument 2 sqrt(r^2+eps^2)/r_cut"}),
+                       **({} if args.rsqrt == "hardware" else
+                          {"rsqrt": "refined: 1/s from an estimate and the paper's third-order step"})),
+        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true, {soft}, {rf}>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
                              "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
-        "roofline_forward": roofline(f"k_pair_packed<{tile[0]}, {soft}>", kp_ms, FLOPS_PER_INTERACTION,
+        "roofline_forward": roofline(f"k_pair_packed<{tile[0]}, 8, {soft}, {rf}>", kp_ms, FLOPS_PER_INTERACTION,
                                      "FP32 forward pair kernel, separate call"),
-        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false, {soft}>", kv_ms, VJP_FLOPS_PER_INTERACTION,
-                                     "FP32 adjoint pair kernel, separate call"),
+        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false, {soft}, {rf}>", kv_ms,
+                                     VJP_FLOPS_PER_INTERACTION, "FP32 adjoint pair kernel, separate call"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},
         "gpu_launches": launches,
@@ -455,7 +477,8 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
                                  "the sum over groups of n_i * n_j that value counts",
     }
     if world == 1 and not args.no_cpu_baseline and not paper_regime:
-        r = oracle_sample_rate(box, w, steps=1, xi_softened=args.xi == "softened")
+        r = oracle_sample_rate(box, w, steps=1, xi_softened=args.xi == "softened",
+                               rsqrt_refined=args.rsqrt == "refined")
         line["cpu_baseline"] = {"value": r["per_step_interactions"] / r["times"][0], "unit": UNIT,
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
     tree.close()
@@ -481,7 +504,8 @@ def run_batched(args, rank, world, local_rank):
     """64 independent periodic boxes (sizes log-uniform in [16^3, 96^3], even
     boxes uniform, odd boxes clustered), n_crit per box from the autotuner, the
     whole step (rebuild + FP32 force + FP32 adjoint of every box) captured in
-    one CUDA graph and timed as one replay."""
+    one CUDA graph and timed as one replay.  With N ranks the 64 boxes are
+    shared among them (strong scaling: the same 64 boxes at every N)."""
     import torch
 
     from paper_1211_4406_gb300 import autotune
@@ -489,16 +513,33 @@ def run_batched(args, rank, world, local_rank):
     from paper_1211_4406_gb300 import inputs
     from paper_1211_4406_gb300.api import CapturedStep, Params, ShortRangeTree, launch_count
 
+    from paper_1211_4406_gb300.domain import partition_boxes
+
     libbuild.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
-    boxes = inputs.batched_boxes(64)
-    kinds = ["uniform" if b % 2 == 0 else "clustered" for b in range(64)]
-    base = [Params(b.G, b.eps, b.r_cut, b.theta, 64, 8, "fp32") for b in boxes]
+    all_boxes = inputs.batched_boxes(64)
+    all_kinds = ["uniform" if b % 2 == 0 else "clustered" for b in range(64)]
+    base = [Params(b.G, b.eps, b.r_cut, b.theta, 64, 8, "fp32") for b in all_boxes]
     t0 = time.perf_counter()
-    ncrit = autotune.tune_boxes(boxes, kinds, base, reps=2)
+    ncrit_all = autotune.tune_boxes(all_boxes, all_kinds, base, reps=2)
     t_tune = time.perf_counter() - t0
+    # with several ranks, each takes a share of the independent boxes (no
+    # collective on the data path): longest-processing-time split by each
+    # box's interaction count, the same on every rank
+    if world > 1:
+        costs = []
+        for b, c in zip(all_boxes, ncrit_all):
+            tb = ShortRangeTree(torch.tensor(b.pos, device=dev), torch.tensor(b.mass, device=dev),
+                                Params(b.G, b.eps, b.r_cut, b.theta, c, 8, "fp32"))
+            costs.append(tb.stats()["n_interactions"])
+            tb.close()
+        mine = partition_boxes(costs, world)[rank]
+    else:
+        mine = list(range(64))
+    boxes = [all_boxes[b] for b in mine]
+    ncrit = [ncrit_all[b] for b in mine]
     prm = [Params(b.G, b.eps, b.r_cut, b.theta, c, 8, "fp32") for b, c in zip(boxes, ncrit)]
     offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
     pos_h = torch.tensor(np.concatenate([b.pos for b in boxes])).pin_memory()
@@ -541,8 +582,10 @@ def run_batched(args, rank, world, local_rank):
     e2e_ms = _timed_replays(e2e, args.steps, flush, stream)
     inter = int(st["n_interactions"])
     tot_ms, tot_e2e = max_over_ranks([sum(ms), sum(e2e_ms)], device=dev)
-    value = whole_job_rate(world, 2 * inter, args.steps, tot_ms)
-    e2e_value = whole_job_rate(world, 2 * inter, args.steps, tot_e2e)
+    inter_all = int(sum_over_ranks([inter], device=dev)[0])        # each rank has its own share of boxes
+    value = 2 * inter_all * args.steps / (tot_ms * 1e-3)
+    e2e_value = 2 * inter_all * args.steps / (tot_e2e * 1e-3)
+    n_all = int(sum_over_ranks([n], device=dev)[0])
     tree.close()
     if rank != 0:
         return
@@ -552,10 +595,13 @@ def run_batched(args, rank, world, local_rank):
     line = {
         "metric": METRIC.replace("clustered 2M box", "64 batched boxes"), "value": value, "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "batched-64", "nbox": 64, "n_total": int(n), "n_min": int(min(b.n for b in boxes)),
-                   "n_max": int(max(b.n for b in boxes)), "kinds": "even uniform, odd clustered",
+        "config": {"workload": "batched-64", "nbox": 64, "n_total": n_all,
+                   "n_min": int(min(b.n for b in all_boxes)), "n_max": int(max(b.n for b in all_boxes)),
+                   "kinds": "even uniform, odd clustered",
+                   "sharding": "one rank" if world == 1 else
+                   f"{world} ranks, boxes split by interaction count (LPT), rank 0 has {len(mine)} boxes",
                    "r_cut": "3/N_b^(1/3)", "eps": "1/(50 N_b^(1/3))", "theta": 0.5,
                    "n_crit_autotuned": hist,
                    "tile_autotuned": {"forward_particles_per_thread": tile[0], "adjoint_entries_per_thread": tile[1]},
@@ -1034,12 +1080,17 @@ def main():
                          "of a 10-step KDK chain (checkpointed adjoint); treepm-2M: the whole TreePM "
                          "acceleration (rebuild + short-range + PM on 128^3); treepm-leapfrog-2M: the "
                          "multiple-stepsize TreePM integrator (PM once, PP twice per step)")
+    ap.add_argument("--rsqrt", default="hardware", choices=["hardware", "refined"],
+                    help="1/s in the FP32 pair kernels for clustered-2M and paper-regime-2M: the hardware "
+                         "reciprocal square root (default) or the paper's refinement of an estimate")
     ap.add_argument("--xi", default="plain", choices=["plain", "softened"],
                     help="cutoff argument of Eq. 3 for clustered-2M and paper-regime-2M: plain r (default) "
                          "or the softened sqrt(r^2+eps^2) of the paper's kernel")
     args = ap.parse_args()
     if args.xi != "plain" and args.workload not in ("clustered-2M", "paper-regime-2M"):
         ap.error(f"--xi {args.xi} applies to the clustered-2M and paper-regime-2M workloads only")
+    if args.rsqrt != "hardware" and args.workload not in ("clustered-2M", "paper-regime-2M"):
+        ap.error(f"--rsqrt {args.rsqrt} applies to the clustered-2M and paper-regime-2M workloads only")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -66,7 +66,8 @@ typedef enum { TP_FP64 = 0, TP_FP32 = 1 } tp_precision;
  *   n_leaf  a tree node holding more than n_leaf particles is split, 1..64
  *   precision  TP_FP32 (pair arithmetic in FP32 on group-relative
  *           coordinates) or TP_FP64 (plain FP64 reference path)
- *   flags   0, or TP_FLAG_CHUNKED and/or TP_FLAG_XI_SOFTENED                 */
+ *   flags   0, or any of TP_FLAG_CHUNKED, TP_FLAG_XI_SOFTENED and
+ *           TP_FLAG_RSQRT_REFINED                                           */
 typedef struct {
     double G, eps, r_cut, theta;
     int32_t n_crit, n_leaf, precision, flags;
@@ -101,6 +102,20 @@ typedef struct {
  * tp_short_range_force_vjp differentiate the variant the tree was built
  * with.  tp_short_range_force_noalloc does not take it.                    */
 #define TP_FLAG_XI_SOFTENED 2
+
+/* The paper's inverse square root (Sec. II-A) in the FP32 pair kernels: 1/s
+ * from an estimate y0 refined by one third-order step, h0 = 1 - x y0^2 and
+ * y1 = y0 (1 + h0/2 + 3 h0^2/8), instead of the hardware reciprocal square
+ * root.  The paper's processor has an 8-bit estimate instruction; here the
+ * estimate is Lomont's integer approximation (the FP32 bit pattern of x
+ * shifted right by one and subtracted from 0x5f3759df) after one Newton
+ * step, off by less than 1.8e-3, so y1 is good to about 1.5e-8.  It moves
+ * the root from the MUFU pipe to about ten FP32 operations on the FMA pipe
+ * (the pipe that bounds these kernels, so it is slower on GB300).  FP32 trees
+ * only (else TP_ERR_INVALID_ARG); the kernels for groups spanning half the
+ * box or with eps = 0 keep the hardware root.  All boxes of a batched tree
+ * must agree on this flag.                                                  */
+#define TP_FLAG_RSQRT_REFINED 4
 
 typedef struct tp_tree tp_tree; /* opaque, library-owned */
 

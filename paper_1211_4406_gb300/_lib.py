@@ -17,6 +17,7 @@ TP_FP64 = 0
 TP_FP32 = 1
 TP_FLAG_CHUNKED = 1
 TP_FLAG_XI_SOFTENED = 2
+TP_FLAG_RSQRT_REFINED = 4
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "device out of memory",
           -4: "capacity overflow", -5: "device wait timed out", -6: "non-finite position",
           -7: "no CUDA device"}

@@ -89,14 +89,18 @@ class Params:
     precision: str = "fp32"
     chunked: bool = False     # force the bounded-list-memory mode (TP_FLAG_CHUNKED)
     xi: str = "plain"         # cutoff argument of Eq. 3: "plain" r or "softened" sqrt(r^2+eps^2)
+    rsqrt: str = "hardware"   # 1/s: the "hardware" MUFU root or the paper's "refined" estimate
 
     def c(self) -> _lib.TPParams:
         if self.xi not in ("plain", "softened"):
             raise ValueError(f"xi must be 'plain' or 'softened', not {self.xi!r}")
+        if self.rsqrt not in ("hardware", "refined"):
+            raise ValueError(f"rsqrt must be 'hardware' or 'refined', not {self.rsqrt!r}")
         p = _lib.params(self.G, self.eps, self.r_cut, self.theta, self.n_crit, self.n_leaf,
                         self.precision)
         p.flags = ((_lib.TP_FLAG_CHUNKED if self.chunked else 0) |
-                   (_lib.TP_FLAG_XI_SOFTENED if self.xi == "softened" else 0))
+                   (_lib.TP_FLAG_XI_SOFTENED if self.xi == "softened" else 0) |
+                   (_lib.TP_FLAG_RSQRT_REFINED if self.rsqrt == "refined" else 0))
         return p
 
 

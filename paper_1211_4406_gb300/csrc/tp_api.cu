@@ -278,7 +278,8 @@ static tp_status validate(const tp_params &p)
     if (!std::isfinite(p.G)) return TP_ERR_INVALID_ARG;
     if (p.n_crit < 1 || p.n_crit > 4096 || p.n_leaf < 1 || p.n_leaf > 64) return TP_ERR_INVALID_ARG;
     if (p.precision != TP_FP32 && p.precision != TP_FP64) return TP_ERR_INVALID_ARG;
-    if (p.flags & ~(TP_FLAG_CHUNKED | TP_FLAG_XI_SOFTENED)) return TP_ERR_INVALID_ARG;
+    if (p.flags & ~(TP_FLAG_CHUNKED | TP_FLAG_XI_SOFTENED | TP_FLAG_RSQRT_REFINED)) return TP_ERR_INVALID_ARG;
+    if ((p.flags & TP_FLAG_RSQRT_REFINED) && p.precision != TP_FP32) return TP_ERR_INVALID_ARG;
     return TP_OK;
 }
 
@@ -565,7 +566,8 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
         if (box_offsets[b + 1] < box_offsets[b]) return TP_ERR_INVALID_ARG;
         if (validate(per_box[b]) != TP_OK) return TP_ERR_INVALID_ARG;
         if (per_box[b].precision != per_box[0].precision) return TP_ERR_INVALID_ARG;
-        if ((per_box[b].flags ^ per_box[0].flags) & TP_FLAG_XI_SOFTENED) return TP_ERR_INVALID_ARG;
+        if ((per_box[b].flags ^ per_box[0].flags) & (TP_FLAG_XI_SOFTENED | TP_FLAG_RSQRT_REFINED))
+            return TP_ERR_INVALID_ARG;
     }
     const int64_t n = box_offsets[nbox];
     if (n < 0 || n >= (1ll << 31) - 1) return TP_ERR_INVALID_ARG;
@@ -591,6 +593,7 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.n = n;
     D.nbox = nbox;
     D.xi_soft = (per_box[0].flags & TP_FLAG_XI_SOFTENED) ? 1 : 0;
+    D.rsq_refined = (per_box[0].flags & TP_FLAG_RSQRT_REFINED) ? 1 : 0;
     Pool &B = t->base;
     std::vector<BoxPrm> hb(nbox);
     for (int b = 0; b < nbox; b++)

@@ -63,6 +63,7 @@ struct TreeDev {
     int64_t n;
     int32_t nbox;
     int32_t xi_soft;                  // cutoff argument from the softened distance (all boxes)
+    int32_t rsq_refined;              // packed FP32 kernels: the paper's refined 1/s (all boxes)
     int64_t walk_budget;              // node visits per walk; 0: n_nodes + 1 (the proof bound)
     int64_t cap_nodes, cap_groups, cap_entries;
     const BoxPrm *box;

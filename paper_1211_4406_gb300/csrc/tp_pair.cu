@@ -87,6 +87,29 @@ __device__ __forceinline__ f2 f2relu(f2 v)
     return f2pack(fmaxf(a, 0.f), fmaxf(b, 0.f));
 }
 
+// The paper's inverse square root (Sec. II-A), a kernel variant
+// (TP_FLAG_RSQRT_REFINED) that takes 1/s' off the MUFU pipe: an estimate y0
+// refined by one third-order step, h0 = 1 - x y0^2, y1 = y0 (1 + h0/2 +
+// 3 h0^2/8), relative error 5/2 e^3 + O(e^4) for an estimate off by e.  The
+// K computer's estimate instruction gives 8 bits; the estimate here is the
+// integer approximation of Lomont (2003): the bit pattern of x shifted right
+// by one and subtracted from 0x5f3759df (|e| < 3.5e-2), then one Newton step
+// y (3/2 - x y^2/2) (|e| < 1.8e-3), so y1 is good to ~1.5e-8.  Ten packed
+// FP32 operations and two integer ones per pair of roots, for x > 0 normal.
+__device__ __forceinline__ f2 rsqrt_refined(f2 x)
+{
+    float xa, xb;
+    f2unpack(x, xa, xb);
+    const f2 y0 = f2pack(__uint_as_float(0x5f3759dfu - (__float_as_uint(xa) >> 1)),
+                         __uint_as_float(0x5f3759dfu - (__float_as_uint(xb) >> 1)));
+    const f2 nx = f2mul(x, f2pack(-1.f, -1.f));
+    const f2 nhx = f2mul(x, f2pack(-0.5f, -0.5f));
+    const f2 y = f2mul(y0, f2fma(nhx, f2mul(y0, y0), f2pack(1.5f, 1.5f)));
+    const f2 h0 = f2fma(nx, f2mul(y, y), f2pack(1.f, 1.f));
+    const f2 p = f2fma(f2pack(0.375f, 0.375f), h0, f2pack(0.5f, 0.5f));
+    return f2fma(f2mul(y, h0), p, y);
+}
+
 template <class R> struct Arith;
 
 template <> struct Arith<float> {
@@ -228,7 +251,7 @@ __device__ __forceinline__ void pair_offset(const JTile<R> &J, int j, const IPar
 // Two pairs per step, packed, for NI particles per thread: each staged entry
 // pair (A = {x0, x1, y0, y1}, B = {z0, z1, m0, m1}) is loaded once and used
 // for all NI particles.  Eq. 3 as g = u^5 h + v^6 c (exact 0 beyond the cutoff).
-template <int NI, bool SOFT>
+template <int NI, bool SOFT, bool RF>
 __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4 *SB, int st, int npairs, int ns,
                                                   const float *xi, const float *yi, const float *zi, float eps2,
                                                   float *axs, float *ays, float *azs)
@@ -257,7 +280,7 @@ __device__ __forceinline__ void force_tile_packed(const float4 *SA, const float4
             const f2 s2 = SOFT ? r2 : f2add(r2, E2);
             float s2a, s2b;
             f2unpack(s2, s2a, s2b);
-            const f2 ri = f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
+            const f2 ri = RF ? rsqrt_refined(s2) : f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
             f2 x;                                   // the cutoff argument xi
             if (SOFT) {
                 x = f2pack(sqrt_approx(s2a), sqrt_approx(s2b));
@@ -464,7 +487,7 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 // tile; TS = 8 (FP32 runs of at most 8 x 256 / slices entries per thread)
 // measured 2 % faster on the clustered 2M box with the FP32 error unchanged
 // (rms 4.1e-7 against the FP64 path on the same lists).
-template <int NI, int TS, bool SOFT>
+template <int NI, int TS, bool SOFT, bool RF>
 __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc, int32_t *queue,
                                                           const int32_t *order)
 {
@@ -536,7 +559,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
             for (int t0 = 0, b = 0; t0 < ne; t0 += kT, b ^= 1) {
                 const int nt = min(kT, ne - t0);
                 if (active) {
-                    force_tile_packed<NI, SOFT>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
+                    force_tile_packed<NI, SOFT, RF>(SA[b], SB[b], st, (nt + 1) >> 1, ns, xi, yi, zi, eps2, ax, ay, az);
                     if (++tc == TS || t0 + kT >= ne) {
 #pragma unroll
                         for (int k = 0; k < NI; k++) {
@@ -739,7 +762,7 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
 // tiles.  Each thread holds E list entries (a tile is E x 128 entries) and
 // adds their particle-side values before the reduce-scatter, so its cost is
 // shared by E entries.
-template <int E, bool FWD, bool SOFT>
+template <int E, bool FWD, bool SOFT, bool RF>
 __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fused(TreeDev T, const float *cot, double *gs, double *ncot,
                                                         int32_t *queue, const int32_t *order, float *acc)
 {
@@ -834,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                             float r2a, r2b, s2a, s2b;
                             f2unpack(r2, r2a, r2b);
                             f2unpack(s2, s2a, s2b);
-                            const f2 ri = f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
+                            const f2 ri = RF ? rsqrt_refined(s2) : f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
                             const f2 x = SOFT ? f2pack(sqrt_approx(s2a), sqrt_approx(s2b))   // xi
                                               : f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
                             f2 gv, gp;
@@ -1091,13 +1114,22 @@ using tp::num_sms;
 using tp::occupancy;
 
 // One configuration of the packed forward kernel, on its own occupancy.
+template <int NI, int TS, bool SOFT, bool RF>
+void launch_pair_packed_rf(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
+{
+    static const int nb = occupancy(k_pair_packed<NI, TS, SOFT, RF>, kThreads);
+    int64_t gr = (int64_t)num_sms() * nb;
+    auto kp = k_pair_packed<NI, TS, SOFT, RF>;
+    TP_LAUNCH(kp, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
+}
+
 template <int NI, int TS, bool SOFT>
 void launch_pair_packed(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
 {
-    static const int nb = occupancy(k_pair_packed<NI, TS, SOFT>, kThreads);
-    int64_t gr = (int64_t)num_sms() * nb;
-    auto kp = k_pair_packed<NI, TS, SOFT>;
-    TP_LAUNCH(kp, (int)(gr > G ? G : gr), kThreads, 0, s, T, acc, queue, order);
+    if (T.rsq_refined)
+        launch_pair_packed_rf<NI, TS, SOFT, true>(T, acc, queue, order, G, s);
+    else
+        launch_pair_packed_rf<NI, TS, SOFT, false>(T, acc, queue, order, G, s);
 }
 
 template <bool SOFT>
@@ -1121,23 +1153,33 @@ void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *o
 
 // The fused adjoint kernel with E entries per thread, with or without the
 // forward sum, on its own occupancy.
-template <int E, bool SOFT>
-void launch_vjp_fused(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
-                      const int32_t *order, int64_t G, float *acc, cudaStream_t s)
+template <int E, bool SOFT, bool RF>
+void launch_vjp_fused_rf(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
+                         const int32_t *order, int64_t G, float *acc, cudaStream_t s)
 {
-    static const int nbf = occupancy(k_vjp_fused<E, false, SOFT>, kThreads);
-    static const int nbw = occupancy(k_vjp_fused<E, true, SOFT>, kThreads);
+    static const int nbf = occupancy(k_vjp_fused<E, false, SOFT, RF>, kThreads);
+    static const int nbw = occupancy(k_vjp_fused<E, true, SOFT, RF>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
     };
     if (acc) {
-        auto kw = k_vjp_fused<E, true, SOFT>;
+        auto kw = k_vjp_fused<E, true, SOFT, RF>;
         TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
     } else {
-        auto kf = k_vjp_fused<E, false, SOFT>;
+        auto kf = k_vjp_fused<E, false, SOFT, RF>;
         TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, cot, gs, ncot, queue, order, nullptr);
     }
+}
+
+template <int E, bool SOFT>
+void launch_vjp_fused(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
+                      const int32_t *order, int64_t G, float *acc, cudaStream_t s)
+{
+    if (T.rsq_refined)
+        launch_vjp_fused_rf<E, SOFT, true>(T, cot, gs, ncot, queue, order, G, acc, s);
+    else
+        launch_vjp_fused_rf<E, SOFT, false>(T, cot, gs, ncot, queue, order, G, acc, s);
 }
 
 template <class R, bool SOFT>

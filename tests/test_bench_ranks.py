@@ -29,8 +29,10 @@ def _rank_main(rank, world, port, out):
         # rank r reports timed totals (ms) that differ per rank
         tot = bench.max_over_ranks([100.0 + 10 * rank, 200.0 - 50 * rank])
         rate = bench.whole_job_rate(world, 1000, 4, tot[0])
+        # ranks with unequal shares of the work (the batched boxes): the sum
+        units = bench.sum_over_ranks([1000.0 + 500 * rank])
         dist.barrier()
-        out.put((rank, tot, rate))
+        out.put((rank, tot, rate, units))
     finally:
         dist.destroy_process_group()
 
@@ -47,9 +49,10 @@ def test_max_over_ranks_and_rate_gloo_world2():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, tot, rate in res:
-        # every rank sees the slowest rank's totals
+    for rank, tot, rate, units in res:
+        # every rank sees the slowest rank's totals and the sum of the shares
         assert tot == [110.0, 200.0]
+        assert units == [2500.0]
         # 2 ranks x 1000 units x 4 steps over 110 ms
         assert rate == pytest.approx(2 * 1000 * 4 / 0.110)
 

@@ -13,9 +13,12 @@ nonlinear that a plain central difference at h = 1e-3 eps is off by ~1 %
 Over 10 steps the clustered box amplifies any perturbation of the state by
 ~2400x (measured on the FP64 path: its own rounding error grows from 1.9e-15
 to 4.4e-12 relative).  The FP32 path starts from its single-evaluation error
-(~2.4e-7 rms relative) and is amplified the same way (5.7e-4 rms measured), so
-the 10-step FP32 gradient is held to rms <= 2e-3 and median <= 1e-6 per
-coordinate, and the per-coordinate 1e-4 bound is checked after one step."""
+(~2.4e-7 rms relative) and is amplified the same way (6.4e-4 rms measured), so
+the 10-step FP32 gradient does not meet the per-coordinate 1e-4 bound (measured
+max 1.5e-2, rms 6.4e-4, median 2.7e-9; recorded as unmet) and is held to its
+measured level, rms <= 2e-3 and median <= 1e-6; the per-coordinate 1e-4 bound
+holds up to three steps at this size (measured max 1.3e-5, 1.5e-5 and 3.4e-5
+after one, two and three steps) and is checked there."""
 import numpy as np
 import pytest
 import torch
@@ -106,7 +109,7 @@ def test_leapfrog_gradient_fp64_against_finite_differences():
     assert np.all(np.abs(g - gref) <= 1e-8 * np.maximum(np.abs(gref), scale))
 
 
-@pytest.mark.parametrize("steps", [1, 10])
+@pytest.mark.parametrize("steps", [1, 3, 10])
 def test_leapfrog_gradient_fp32_against_oracle_adjoint(steps):
     box = inputs.config_box(4, n_override=2 ** 15)
     w = inputs.cotangent(box.n, box.seed + 7).astype(np.float64)
@@ -119,7 +122,7 @@ def test_leapfrog_gradient_fp32_against_oracle_adjoint(steps):
                                       np.zeros_like(v0), np.zeros_like(v0), w)
     scale = np.sqrt(np.mean(gref ** 2))
     e = np.abs(g - gref) / np.maximum(np.abs(gref), scale)
-    if steps == 1:
+    if steps <= 3:
         assert e.max() <= TOL, float(e.max())
     else:
         assert np.sqrt(np.mean((g - gref) ** 2)) / scale <= 2e-3
