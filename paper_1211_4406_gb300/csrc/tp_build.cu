@@ -69,7 +69,7 @@ __global__ void k_gather(const double *pos, const double *mass, TreeDev T)
         T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
         const double m = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
         T.m[s] = m;
-        T.psrc[s] = SrcRec{X, Y, Z, m};
+        T.psrc[s] = SrcRec{X, Y, Z, (float)m, 0.f};
     }
 }
 
@@ -98,7 +98,7 @@ __global__ void k_refit_gather(const double *pos, const double *mass, TreeDev T)
             m = mass[i];
             T.m[s] = m;
         }
-        T.psrc[s] = SrcRec{X, Y, Z, m};
+        T.psrc[s] = SrcRec{X, Y, Z, (float)m, 0.f};
     }
 }
 
@@ -310,7 +310,7 @@ __global__ void k_moments(TreeDev T, int L)
         // may lie just outside, hence the wrap)
         const uint64_t CX = tp_fixed64(wrap01(mx)), CY = tp_fixed64(wrap01(my)), CZ = tp_fixed64(wrap01(mz));
         T.cX[i] = CX; T.cY[i] = CY; T.cZ[i] = CZ;
-        T.nsrc[i] = SrcRec{CX, CY, CZ, M};
+        T.nsrc[i] = SrcRec{CX, CY, CZ, (float)M, 0.f};
         WNode w;
         w.cx = (uint32_t)(tp_fixed64(wrap01(cx)) >> 32);
         w.cy = (uint32_t)(tp_fixed64(wrap01(cy)) >> 32);

@@ -52,12 +52,29 @@ struct __align__(16) WNode {
 };
 
 // The 32-byte record an interaction-list entry is made from: the source's
-// fixed-point image and mass, one aligned sector per gather (particles and
-// node monopoles alike).
+// fixed-point image and its mass, rounded to FP32 once per source (the entry
+// records are FP32), one aligned sector per gather (particles and node
+// monopoles alike).
 struct __align__(32) SrcRec {
     uint64_t X, Y, Z;
-    double m;
+    float m, pad;
 };
+
+// The FP32 value of the fixed-point offset a - b (two 64-bit images; their
+// wrap-around difference read as signed is the exact minimum-image offset in
+// units of 2^-64) times sc, from its two 32-bit halves: on GB300 a conversion
+// of a 64-bit integer runs on the FP64 unit (1/64 of the FP32 rate), a 32-bit
+// one does not.  Within one rounding step of the correctly rounded value.
+// Every FP32 offset of a pair (entry records, group particles) comes from
+// here, so equal images give equal offsets and a particle's own entry an
+// exact zero difference.
+__device__ __forceinline__ float tp_offset_f32(uint64_t a, uint64_t b, float sc)
+{
+    const long long d = (long long)(a - b);
+    const float hi = (float)(int)(d >> 32);
+    const float lo = (float)(unsigned)(d & 0xffffffffll);
+    return __fmul_rn(__fmaf_rn(hi, 4294967296.0f, lo), sc);
+}
 
 struct TreeDev {
     int64_t n;

@@ -121,7 +121,7 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float soft_xi(float s2, float) { return sqrt_approx(s2); }
     static __device__ __forceinline__ float from_fixed(uint64_t a, uint64_t b, float sc)
     {
-        return __ll2float_rn((long long)(a - b)) * sc;
+        return tp_offset_f32(a, b, sc);
     }
 };
 
@@ -1058,12 +1058,14 @@ __global__ void __launch_bounds__(kThreads) k_count_useful(TreeDev T, unsigned l
             const BoxPrm &P = *G.P;
             const float sc = P.scale, e2 = T.xi_soft ? P.eps2s : 0.f;
             // Offsets are at most H = k (h + r_cut) per axis (entries lie within
-            // r_cut of the group box) and carry two FP32 roundings each, so the
-            // estimate of |d'|^2 is off by at most ~2e-6 (H + 1) near the cutoff;
-            // tol keeps a margin of five or more over that.
+            // r_cut of the group box) and carry two FP32 roundings each (2.4e-7 H
+            // per component of d'), so the estimate of |d'|^2 is off by at most
+            // ~1.7e-6 H + 1e-6 near the cutoff (|d'| = 2), and a true |d'|^2 > 0
+            // cannot round to 0 unless it is below ~1e-12 H^2; tol and tol0 keep
+            // a margin of five or more over those.
             const double hm = fmax(T.ghx[g], fmax(T.ghy[g], T.ghz[g]));
             const float H = (float)((hm + P.rcut) * (2.0 / P.rcut));
-            const float tol = 1e-5f * (H * H + 1.f);
+            const float tol = 1e-5f * (H + 1.f), tol0 = 1e-10f * (H + 1.f) * (H + 1.f);
             for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
                 const int nic = min(kThreads, G.ni - i0);
                 __syncthreads();
@@ -1085,7 +1087,7 @@ __global__ void __launch_bounds__(kThreads) k_count_useful(TreeDev T, unsigned l
                         } else {
                             const float dx = r.x - px[k], dy = r.y - py[k], dz = r.z - pz[k];
                             const float r2 = dx * dx + dy * dy + dz * dz, c2 = r2 + e2;
-                            u = (r2 > tol && fabsf(c2 - 4.f) > tol) ? c2 < 4.f : useful_f64(T, P, i, e);
+                            u = (r2 > tol0 && fabsf(c2 - 4.f) > tol) ? c2 < 4.f : useful_f64(T, P, i, e);
                         }
                         cnt += u ? 1ull : 0ull;
                     }

@@ -68,13 +68,12 @@ struct WalkGroup {
 
 // An entry's record for the pair kernels: its offset from the group centre
 // (wrap-around difference of the 64-bit images, the exact minimum image)
-// scaled by k = 2/r_cut and rounded once to FP32, and its mass.
+// scaled by k = 2/r_cut and converted to FP32 by tp_offset_f32, and its mass.
 __device__ __forceinline__ float4 entry_record(const TreeDev &T, uint64_t GX, uint64_t GY, uint64_t GZ, float sc,
                                               int32_t e)
 {
     const SrcRec q = e >= 0 ? T.psrc[e] : T.nsrc[-e - 1];
-    return make_float4(__ll2float_rn((long long)(q.X - GX)) * sc, __ll2float_rn((long long)(q.Y - GY)) * sc,
-                       __ll2float_rn((long long)(q.Z - GZ)) * sc, (float)q.m);
+    return make_float4(tp_offset_f32(q.X, GX, sc), tp_offset_f32(q.Y, GY, sc), tp_offset_f32(q.Z, GZ, sc), q.m);
 }
 
 __device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g)

@@ -9,12 +9,17 @@ with n).  The allocating build runs first; each step is rebuild + force +
 adjoint (step), only the force or only the adjoint, rebuild + the one-pass
 force and adjoint (fused), or rebuild + all three (all).
 
-  python -m paper_1211_4406_gb300.profile_step --record-traffic CSV --n N
+  python -m paper_1211_4406_gb300.profile_step --record-traffic CSV --n N --entries E
 
 reads an ncu CSV of dram__bytes_read.sum / dram__bytes_write.sum /
-gpu__time_duration.sum for the pair kernels (taken on this command with --n N)
-and writes the per-launch DRAM traffic, with the digest of the device code it
-was measured on, to profiles/kernel_traffic.json.
+gpu__time_duration.sum for the pair kernels (taken on this command with --n N,
+whose tree has E list entries) and writes the per-launch DRAM traffic, with
+the digest of the device code it was measured on, to
+profiles/kernel_traffic.json.  The capture is taken on a smaller box of the
+clustered recipe (a few GB on the device, so that the multi-metric replay
+stays short); the pair kernels stream each list entry's record once per
+launch, so their traffic scales with the entry count, and traffic_for
+scales the record to the tree it is asked about.
 """
 from __future__ import annotations
 
@@ -56,10 +61,11 @@ UNIT_SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e
               "s": 1e9, "second": 1e9}
 
 
-def record_traffic(csv_path: str, n: int, out_path: str | None = None) -> dict:
+def record_traffic(csv_path: str, n: int, out_path: str | None = None, entries: int | None = None) -> dict:
     """Per-launch DRAM bytes and ncu time of the pair kernels from an ncu CSV
     (one row per launch and metric), written to `out_path` (default: the
-    committed traffic record).  Values are scaled by their unit column; an
+    committed traffic record), with the particle count n and the list entry
+    count of the captured tree.  Values are scaled by their unit column; an
     unknown unit raises ValueError."""
     rows = list(csv.reader(open(csv_path)))
     hi = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
@@ -84,7 +90,7 @@ def record_traffic(csv_path: str, n: int, out_path: str | None = None) -> dict:
         k["launches"] += 1
         k["dram_bytes"] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
         k["ns"] += d.get("gpu__time_duration.sum", 0.0)
-    rec = {"workload": "clustered-2M" if n == 128 ** 3 else f"clustered-{n}", "n": n,
+    rec = {"recipe": "clustered", "n": n, "entries": entries,
            "digest": kernel_source_digest(),
            "kernels": {k: {"bytes_per_launch": v["dram_bytes"] / v["launches"],
                            "ncu_ms_per_launch": v["ns"] / v["launches"] / 1e6}
@@ -100,19 +106,22 @@ def record_traffic(csv_path: str, n: int, out_path: str | None = None) -> dict:
     return rec
 
 
-def traffic_for(kernel: str, n: int, workload: str = "clustered-2M", path: str | None = None):
+def traffic_for(kernel: str, entries: int, recipe: str = "clustered", path: str | None = None):
     """DRAM bytes per launch of `kernel` (its name with template arguments, as
-    ncu prints it) on `workload` at particle count n, or None when no capture
-    exists for that workload and n or the device code has changed since it
-    was taken."""
+    ncu prints it) on a tree of the input recipe `recipe` with `entries` list
+    entries: the captured bytes scaled by entries / the captured tree's
+    entries.  None when no capture exists for that recipe or the device code
+    has changed since it was taken."""
     try:
         rec = json.load(open(path or TRAFFIC_JSON))
     except (OSError, ValueError):
         return None
-    if rec.get("n") != n or rec.get("workload") != workload or rec.get("digest") != kernel_source_digest():
+    if rec.get("recipe") != recipe or rec.get("digest") != kernel_source_digest() or not rec.get("entries"):
         return None
     k = rec.get("kernels", {}).get(kernel_key(kernel))
-    return None if k is None else k.get("bytes_per_launch")
+    if k is None:
+        return None
+    return k.get("bytes_per_launch") * float(entries) / float(rec["entries"])
 
 
 def main():
@@ -122,9 +131,10 @@ def main():
     ap.add_argument("--what", default="step", choices=["step", "force", "vjp", "fused", "all", "treepm"],
                     help="treepm: rebuild + short-range force + PM force on the mesh of r_cut = 3 spacings")
     ap.add_argument("--record-traffic", metavar="CSV")
+    ap.add_argument("--entries", type=int, help="list entries of the captured tree (printed by the run)")
     args = ap.parse_args()
     if args.record_traffic:
-        print(json.dumps(record_traffic(args.record_traffic, args.n)))
+        print(json.dumps(record_traffic(args.record_traffic, args.n, entries=args.entries)))
         return
     import torch
 

@@ -1,7 +1,8 @@
 """The DRAM-traffic record behind the bench line's roofline `traffic`: the
 ncu CSV parser (unit column, kernel-name spelling, per-launch averages) and
-the lookup, which refuses a record taken on other device code, another
-workload or another particle count."""
+the lookup, which scales a capture on a smaller box of the same recipe by
+the list entry count and refuses a record taken on other device code or
+another recipe."""
 import json
 
 import pytest
@@ -39,8 +40,8 @@ def test_parser_scales_units_and_averages_launches(tmp_path):
         row(4, KP, "dram__bytes_write.sum", "byte", "0"),
         row(4, KP, "gpu__time_duration.sum", "ns", "9500000"),
     ])
-    rec = ps.record_traffic(str(csv_path), 128 ** 3, out_path=str(out))
-    assert rec["workload"] == "clustered-2M" and rec["n"] == 128 ** 3
+    rec = ps.record_traffic(str(csv_path), 128 ** 3, out_path=str(out), entries=190000000)
+    assert rec["recipe"] == "clustered" and rec["n"] == 128 ** 3 and rec["entries"] == 190000000
     assert rec["digest"] == ps.kernel_source_digest()
     k = rec["kernels"]
     assert set(k) == {"k_vjp_fused<4,1,0>", "k_pair_packed<2,0>"}     # other kernels are ignored
@@ -58,31 +59,30 @@ def test_parser_rejects_an_unknown_unit(tmp_path):
         ps.record_traffic(str(csv_path), 1024, out_path=str(tmp_path / "t.json"))
 
 
-def test_lookup_refuses_other_code_workload_or_size(tmp_path):
-    n = 128 ** 3
-    rec = {"workload": "clustered-2M", "n": n, "digest": ps.kernel_source_digest(),
-           "kernels": {"k_vjp_fused<4,1,0>": {"bytes_per_launch": 5.26e9}}}
+def test_lookup_scales_by_entries_and_refuses_other_code_or_recipe(tmp_path):
+    rec = {"recipe": "clustered", "n": 2 ** 19, "entries": 30000000, "digest": ps.kernel_source_digest(),
+           "kernels": {"k_vjp_fused<4,1,0,0>": {"bytes_per_launch": 8.0e8}}}
     p = tmp_path / "t.json"
     p.write_text(json.dumps(rec))
-    name = "k_vjp_fused<4, true, false>"                 # the bench's spelling
-    assert ps.traffic_for(name, n, "clustered-2M", path=str(p)) == 5.26e9
-    assert ps.traffic_for(name, n // 2, "clustered-2M", path=str(p)) is None
-    assert ps.traffic_for(name, n, "paper-regime-2M", path=str(p)) is None
-    assert ps.traffic_for("k_pair_packed<2, false>", n, "clustered-2M", path=str(p)) is None
+    name = "k_vjp_fused<4, true, false, false>"          # the bench's spelling
+    assert ps.traffic_for(name, 30000000, path=str(p)) == pytest.approx(8.0e8)
+    assert ps.traffic_for(name, 190000000, path=str(p)) == pytest.approx(8.0e8 * 19 / 3)
+    assert ps.traffic_for(name, 190000000, recipe="uniform", path=str(p)) is None
+    assert ps.traffic_for("k_pair_packed<2, 8, false, false>", 190000000, path=str(p)) is None
     rec["digest"] = "0" * 64
     p.write_text(json.dumps(rec))
-    assert ps.traffic_for(name, n, "clustered-2M", path=str(p)) is None
-    assert ps.traffic_for(name, n, "clustered-2M", path=str(tmp_path / "missing.json")) is None
+    assert ps.traffic_for(name, 190000000, path=str(p)) is None
+    assert ps.traffic_for(name, 190000000, path=str(tmp_path / "missing.json")) is None
     p.write_text("{not json")
-    assert ps.traffic_for(name, n, "clustered-2M", path=str(p)) is None
+    assert ps.traffic_for(name, 190000000, path=str(p)) is None
 
 
 def test_committed_record_names_the_bench_kernels():
     """The committed record covers the three pair-kernel launches the bench
-    reports, each with a traffic at least the list records it must stream
-    (16 B per entry of the 1.9e8-entry lists) and below 100 GB."""
+    reports, each with a traffic per entry at least the 16-byte record it must
+    stream and below 100 bytes."""
     rec = json.load(open(ps.TRAFFIC_JSON))
-    assert rec["workload"] == "clustered-2M" and rec["n"] == 128 ** 3
-    assert set(rec["kernels"]) == {"k_pair_packed<2,0>", "k_vjp_fused<4,0,0>", "k_vjp_fused<4,1,0>"}
+    assert rec["recipe"] == "clustered" and rec["entries"] > 0
+    assert set(rec["kernels"]) == {"k_pair_packed<2,8,0,0>", "k_vjp_fused<4,0,0,0>", "k_vjp_fused<4,1,0,0>"}
     for k in rec["kernels"].values():
-        assert 16 * 1.9e8 <= k["bytes_per_launch"] < 1e11
+        assert 16 <= k["bytes_per_launch"] / rec["entries"] < 100
