@@ -62,10 +62,11 @@ CONFIG_K = 2
 def workload_config(paper_regime: bool = False):
     if paper_regime:
         return {"workload": "paper-regime-2M", "n": 128 ** 3, "halos": 2000, "r_cut": "7.5/128",
-                "eps": "1/6400", "theta": 0.5, "n_crit": 128, "n_leaf": 8, "seed": 14408,
+                "eps": "1/6400", "theta": 0.5, "n_crit": 192, "n_leaf": 8, "seed": 14408,
                 "l2": "flushed (256 MiB write) before every timed step",
-                "why": "the paper's list shapes (Table I: <N_i> ~ 115, <N_j> ~ 2300; r_cut = 7.5 mean "
-                       "spacings as in its 4096^3 PM mesh for 10240^3 particles)"}
+                "why": "the paper's group size (Table I: <N_i> ~ 115) and r_cut = 7.5 mean spacings (its "
+                       "4096^3 PM mesh for 10240^3 particles); its <N_j> ~ 2300 is not reached: a group box "
+                       "of ~115 particles is wider than r_cut, so no monopole lies wholly inside r_cut"}
     return {"workload": "clustered-2M", "n": 128 ** 3, "halos": 2000, "r_cut": "3/128",
             "eps": "1/6400", "theta": 0.5, "n_crit": 64, "n_leaf": 8, "seed": 14408,
             "l2": "flushed (256 MiB write) before every timed step"}
@@ -73,12 +74,12 @@ def workload_config(paper_regime: bool = False):
 
 def bench_box(paper_regime: bool = False):
     """The clustered 2M box; in the paper's regime with r_cut = 7.5/128 and
-    n_crit = 128 instead of 3/128 and 64."""
+    n_crit = 192 (<N_i> = 109, Table I: ~115) instead of 3/128 and 64."""
     from paper_1211_4406_gb300 import inputs
     box = inputs.config_box(CONFIG_K)
     if paper_regime:
         box.r_cut = 7.5 / 128
-        box.n_crit = 128
+        box.n_crit = 192
     return box
 
 
@@ -476,13 +477,159 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
         "useful_fraction_basis": "pairs with a non-zero Eq. 2 term (0 < r < r_cut, decided in FP64) among "
                                  "the sum over groups of n_i * n_j that value counts",
     }
+    tree.close()
+    if not paper_regime and args.xi == "plain" and args.rsqrt == "hardware" and not args.no_sub_records:
+        # the other configurations, each measured briefly after the timed
+        # region above with its own clock sample and kernel count
+        subs = {}
+        for name, fn in (("uniform-32k", sub_uniform_32k), ("batched-64", sub_batched_64),
+                         ("clustered-134M", sub_clustered_134m)):
+            if name == "clustered-134M" and args.no_c5:
+                continue
+            try:
+                subs[name] = fn(dev, stream, flush, local_rank)
+            except Exception as e:              # a sub-record never voids the main line
+                subs[name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.synchronize()
+        line["sub_records"] = subs
     if world == 1 and not args.no_cpu_baseline and not paper_regime:
         r = oracle_sample_rate(box, w, steps=1, xi_softened=args.xi == "softened",
                                rsqrt_refined=args.rsqrt == "refined")
         line["cpu_baseline"] = {"value": r["per_step_interactions"] / r["times"][0], "unit": UNIT,
                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
-    tree.close()
     print(json.dumps(line), flush=True)
+
+
+def _sampled(clock_gpu, fn):
+    """fn() with nvidia-smi sampling around it: (fn's result, clock summary)."""
+    clocks = ClockSampler(clock_gpu)
+    clocks.start()
+    clocks.mark()
+    try:
+        out = fn()
+    finally:
+        clk = clocks.stop()
+    return out, clk
+
+
+def sub_uniform_32k(dev, stream, flush, local_rank, steps=10, warmup=3):
+    """C1: the plain FP64 path on the uniform 32^3 box, rebuild + force +
+    adjoint per step (device-timed, L2 flushed), with the FP32 step beside it."""
+    import torch
+
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count
+    box = inputs.config_box(1)
+    pos, mass = torch.tensor(box.pos, device=dev), torch.tensor(box.mass, device=dev)
+    cot64 = torch.tensor(inputs.cotangent(box.n, box.seed + 7), device=dev).double()
+    out = {"config": "N = 32^3 uniform, r_cut = 3/32, eps = 1/1600, theta = 0.5, n_crit = 64"}
+    for prec, adt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        tree = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, prec))
+        acc = torch.empty((box.n, 3), dtype=adt, device=dev)
+        grad = torch.empty((box.n, 3), dtype=torch.float64, device=dev)
+        cot = cot64.to(adt)
+
+        def step():
+            tree.rebuild(pos, mass)
+            tree.force(acc)
+            tree.vjp(cot, grad)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        l0 = launch_count()
+        ms, clk = _sampled(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0,
+                           lambda: _timed_replays(step, steps, flush, stream))
+        inter = int(tree.stats()["n_interactions"])
+        if tree.status() != 0:
+            raise RuntimeError(f"{prec} tree status {tree.status()}")
+        tree.close()
+        m = sum(ms) / len(ms)
+        out[prec] = {"ms_per_step": m, "interactions_per_s": 2 * inter / (m * 1e-3),
+                     "gpu_launches_per_step": (launch_count() - l0) // steps, "clocks": clk}
+        out["n_interactions"] = inter
+    out["fp32_over_fp64_step_speedup"] = out["fp64"]["ms_per_step"] / out["fp32"]["ms_per_step"]
+    return out
+
+
+def sub_batched_64(dev, stream, flush, local_rank, steps=5, warmup=3):
+    """C3: the 64 batched boxes (autotuned n_crit and tile), rebuild plus
+    forces and adjoint of every box as one CUDA-graph replay."""
+    import torch
+
+    from paper_1211_4406_gb300 import autotune, inputs
+    from paper_1211_4406_gb300.api import CapturedStep, Params, ShortRangeTree, launch_count
+    t0 = time.perf_counter()
+    boxes = inputs.batched_boxes(64)
+    kinds = ["uniform" if b % 2 == 0 else "clustered" for b in range(64)]
+    base = [Params(b.G, b.eps, b.r_cut, b.theta, 64, 8, "fp32") for b in boxes]
+    ncrit = autotune.tune_boxes(boxes, kinds, base, reps=2)
+    prm = [Params(b.G, b.eps, b.r_cut, b.theta, c, 8, "fp32") for b, c in zip(boxes, ncrit)]
+    offs = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
+    pos = torch.tensor(np.concatenate([b.pos for b in boxes]), device=dev)
+    mass = torch.tensor(np.concatenate([b.mass for b in boxes]), device=dev)
+    cot = torch.tensor(np.concatenate([inputs.cotangent(b.n, b.seed + 7) for b in boxes]), device=dev)
+    tree = ShortRangeTree(pos, mass, prm, box_offsets=offs.tolist())
+    tile = autotune.tune_tile(tree, pos, mass, cot, key=f"batched-64|n{tree.n}")
+    acc = torch.empty((tree.n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((tree.n, 3), dtype=torch.float64, device=dev)
+    l0 = launch_count()
+    step = CapturedStep(tree, pos, mass, cot, acc, grad)
+    per_replay = (launch_count() - l0) // 2
+    setup = time.perf_counter() - t0
+    for _ in range(warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    ms, clk = _sampled(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0,
+                       lambda: _timed_replays(step.replay, steps, flush, stream))
+    st = tree.stats()
+    if tree.status() != 0:
+        raise RuntimeError("batched tree status")
+    tree.close()
+    m = sum(ms) / len(ms)
+    return {"config": "64 boxes, N_b log-uniform in [16^3, 96^3], even uniform, odd clustered, "
+                      "r_cut = 3/N_b^(1/3), theta = 0.5, one CUDA-graph replay per step",
+            "n_total": int(tree.n), "n_interactions": int(st["n_interactions"]),
+            "ms_per_step": m, "interactions_per_s": 2 * st["n_interactions"] / (m * 1e-3),
+            "useful_fraction": st["n_useful"] / max(1, st["n_interactions"]),
+            "tile_autotuned": list(tile), "gpu_launches_per_step": per_replay, "setup_s": setup, "clocks": clk}
+
+
+def sub_clustered_134m(dev, stream, flush, local_rank, steps=1, warmup=1):
+    """C5: the 512^3 clustered box (chunked lists), rebuild plus forces and
+    adjoint in one pass per step."""
+    import torch
+
+    from paper_1211_4406_gb300 import inputs
+    from paper_1211_4406_gb300.api import Params, ShortRangeTree, launch_count
+    t0 = time.perf_counter()
+    box = inputs.config_box(5)
+    t_gen = time.perf_counter() - t0
+    n = box.n
+    pos, mass = torch.from_numpy(box.pos).to(dev), torch.from_numpy(box.mass).to(dev)
+    cot = torch.from_numpy(inputs.cotangent(n, box.seed + 7)).to(dev)
+    tree = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf, "fp32"))
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((n, 3), dtype=torch.float64, device=dev)
+
+    def step():
+        tree.rebuild(pos, mass)
+        tree.force_vjp(cot, acc, grad)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    ms, clk = _sampled(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0,
+                       lambda: _timed_replays(step, steps, flush, stream))
+    launches = (launch_count() - l0) // steps
+    st = tree.stats()
+    if tree.status() != 0:
+        raise RuntimeError("134M tree status")
+    tree.close()
+    m = sum(ms) / len(ms)
+    return {"config": "N = 512^3 clustered (10^5 halos), r_cut = 3/512, eps = 1/25600, theta = 0.5, chunked lists",
+            "n_interactions": int(st["n_interactions"]), "n_windows": int(st["n_windows"]),
+            "ms_per_step": m, "interactions_per_s": 2 * st["n_interactions"] / (m * 1e-3),
+            "gpu_launches_per_step": launches, "generate_inputs_s": t_gen, "clocks": clk}
 
 
 def _timed_replays(fn, steps, flush, stream):
@@ -1071,6 +1218,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="leave out the default line's brief measurements of the other configurations")
+    ap.add_argument("--no-c5", action="store_true",
+                    help="leave the 512^3 box out of the default line's sub-records (its inputs take ~40 s to draw)")
     ap.add_argument("--workload", default="clustered-2M", choices=list(WORKLOADS),
                     help="clustered-2M (the default line); batched-64: 64 independent boxes, "
                          "autotuned n_crit, the whole step as one CUDA-graph replay; uniform-32k: "

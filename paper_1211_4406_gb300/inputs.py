@@ -46,6 +46,31 @@ def _nfw_mu(s: np.ndarray) -> np.ndarray:
     return np.log1p(s) - s / (1.0 + s)
 
 
+def _bisect_mu(uu: np.ndarray, conc: float) -> np.ndarray:
+    lo = np.zeros_like(uu)
+    hi = np.full_like(uu, conc)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = _nfw_mu(mid) < uu
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+def _nfw_radius(uu: np.ndarray, conc: float) -> np.ndarray:
+    """s in [0, conc] with mu(s) = uu by 60 bisection steps (element by
+    element, so large inputs are split into chunks that run on several host
+    threads with the same result)."""
+    chunk = 1 << 22
+    if uu.size <= 2 * chunk:
+        return _bisect_mu(uu, conc)
+    import concurrent.futures as cf
+    import os
+    parts = [uu[i:i + chunk] for i in range(0, uu.size, chunk)]
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        return np.concatenate(list(ex.map(lambda p: _bisect_mu(p, conc), parts)))
+
+
 def clustered_box(n: int, n_halo: int, seed: int, frac: float = 0.7,
                   m_lo: float = 1.0, m_hi: float = 1000.0, slope: float = 1.9,
                   conc: float = 10.0) -> tuple[np.ndarray, np.ndarray]:
@@ -72,14 +97,7 @@ def clustered_box(n: int, n_halo: int, seed: int, frac: float = 0.7,
     r200 = (3.0 * m_frac / (800.0 * math.pi)) ** (1.0 / 3.0)
     rs = r200 / conc
     uu = rng.random(halo_of.size) * _nfw_mu(np.array(conc))
-    lo = np.zeros_like(uu)
-    hi = np.full_like(uu, conc)
-    for _ in range(60):
-        mid = 0.5 * (lo + hi)
-        below = _nfw_mu(mid) < uu
-        lo = np.where(below, mid, lo)
-        hi = np.where(below, hi, mid)
-    s = 0.5 * (lo + hi)
+    s = _nfw_radius(uu, conc)
     rad = s * rs[halo_of]
     dirs = rng.standard_normal((halo_of.size, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
