@@ -160,7 +160,7 @@ struct tp_tree {
     int64_t h_nodes = 0, h_groups = 0, h_items = 0, h_pad = 0, h_entries = 0;
     // chunked mode: windows [first group, group count) with lists of bounded size
     bool chunked = false, force_chunked = false, windows_stale = true;
-    std::vector<int64_t> win_first, win_count;
+    std::vector<int64_t> win_first, win_count, win_xitems;
     int64_t *d_wsz = nullptr;         // [kMaxWindows] device copies of the window sizes
     int64_t *d_etot = nullptr;        // entries summed over the windows
     // tile shapes of the FP32 pair kernels (tp_tree_set_tile)
@@ -221,11 +221,13 @@ static bool alloc_groups(tp_tree *t, int64_t cap)
     D.gpad = P.get<int32_t>(c);
     D.icnt = P.get<int32_t>(c);
     D.ioff = P.get<int64_t>(c);
-    t->lpt_key = P.get<uint64_t>(c);
-    t->lpt_key2 = P.get<uint64_t>(c);
-    t->order = reinterpret_cast<int32_t *>(P.get<uint32_t>(c));
-    t->lpt_val2 = P.get<uint32_t>(c);
-    t->lpt_tmp = P.get<char>(tp::radix_tmp_bytes(cap));
+    // work items: the groups' first chunks and up to cap_xitems further ones
+    const size_t cw = c + (size_t)D.cap_xitems;
+    t->lpt_key = P.get<uint64_t>(cw);
+    t->lpt_key2 = P.get<uint64_t>(cw);
+    t->order = reinterpret_cast<int32_t *>(P.get<uint32_t>(cw));
+    t->lpt_val2 = P.get<uint32_t>(cw);
+    t->lpt_tmp = P.get<char>(tp::radix_tmp_bytes((int64_t)cw));
     return P.ok;
 }
 
@@ -316,9 +318,10 @@ constexpr int64_t kWindowSlots = 1ll << 29;  // padded-slot budget of one window
 constexpr double kSlotBytes = 4.0 + 4.0 + 16.0;   // per padded slot: slot, entry id, entry record
 constexpr int kMaxWindows = 1 << 16;
 
-static TreeDev window_view(const TreeDev &D, int64_t g0, int64_t ng, int64_t *d_ng)
+static TreeDev window_view(const TreeDev &D, int64_t g0, int64_t ng, int64_t *d_ng, int64_t nx)
 {
     TreeDev V = D;
+    V.cap_xitems = nx < D.cap_xitems ? nx : D.cap_xitems;   // the window's further chunks
     V.gfirst += g0; V.gcount += g0; V.gbox += g0;
     V.gcx += g0; V.gcy += g0; V.gcz += g0; V.ghx += g0; V.ghy += g0; V.ghz += g0;
     V.gux += g0; V.guy += g0; V.guz += g0; V.ghux += g0; V.ghuy += g0; V.ghuz += g0;
@@ -342,28 +345,32 @@ static tp_status plan_windows(tp_tree *t, cudaStream_t s, int64_t slot_budget, i
     if (e == TP_OK) e = cuda_status(cudaStreamSynchronize(s));
     if (e != TP_OK) return e;
     if (G > D.cap_groups) G = D.cap_groups;
-    std::vector<int32_t> ic((size_t)(G > 0 ? G : 1)), gp((size_t)(G > 0 ? G : 1));
+    std::vector<int32_t> ic((size_t)(G > 0 ? G : 1)), gp((size_t)(G > 0 ? G : 1)), gc((size_t)(G > 0 ? G : 1));
     if (G > 0) {
         e = cuda_status(cudaMemcpy(ic.data(), D.icnt, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
         if (e == TP_OK) e = cuda_status(cudaMemcpy(gp.data(), D.gpad, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
+        if (e == TP_OK) e = cuda_status(cudaMemcpy(gc.data(), D.gcount, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
         if (e != TP_OK) return e;
     }
     t->win_first.clear();
     t->win_count.clear();
-    int64_t g0 = 0, slots = 0, items = 0, ms = 0, mi = 0;
+    t->win_xitems.clear();
+    int64_t g0 = 0, slots = 0, items = 0, xitems = 0, ms = 0, mi = 0;
     for (int64_t g = 0; g <= G; g++) {
         const bool close = g == G || (g > g0 && (slots + gp[g] > slot_budget || items + ic[g] > item_budget));
         if (close && g > g0) {
             t->win_first.push_back(g0);
             t->win_count.push_back(g - g0);
+            t->win_xitems.push_back(xitems);
             ms = slots > ms ? slots : ms;
             mi = items > mi ? items : mi;
             g0 = g;
-            slots = items = 0;
+            slots = items = xitems = 0;
         }
         if (g < G) {
             slots += gp[g];
             items += ic[g];
+            if (gc[g] > kWorkChunk) xitems += (gc[g] - 1) / kWorkChunk;   // chunks after the first
         }
     }
     if ((int64_t)t->win_count.size() > kMaxWindows) return TP_ERR_LIST_OVERFLOW;
@@ -415,7 +422,7 @@ static tp_status for_each_window(tp_tree *t, cudaStream_t s, F body)
     }
     reset_list_stats(t, s);
     for (size_t w = 0; w < t->win_count.size(); w++) {
-        TreeDev V = window_view(t->D, t->win_first[w], t->win_count[w], t->d_wsz + w);
+        TreeDev V = window_view(t->D, t->win_first[w], t->win_count[w], t->d_wsz + w, t->win_xitems[w]);
         walk_window(t, V, s);
         body(V);
     }
@@ -617,6 +624,10 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     D.n_pad = B.get<int64_t>(1);
     D.n_ambig = B.get<unsigned long long>(1);
     D.n_general = B.get<unsigned long long>(1);
+    // every further chunk of a group holds kWorkChunk particles of its own
+    D.cap_xitems = n / kWorkChunk + 1;
+    D.xitem = B.get<int2>((size_t)D.cap_xitems);
+    D.n_xitems = B.get<int64_t>(1);
     D.status = B.get<int32_t>(1);
     t->queue = B.get<int32_t>(4);
     t->gs = B.get<double>(3 * nn);

@@ -133,8 +133,18 @@ struct TreeDev {
     int64_t *n_entries;               // device scalar
     unsigned long long *n_ambig;      // device scalar
     unsigned long long *n_general;    // device scalar: groups the general FP32 pair kernels take
+    // work items of the pair kernels beyond each group's first kWorkChunk
+    // particles: {group, chunk} of the further chunks of larger groups
+    int64_t cap_xitems;
+    int2 *xitem;                      // [cap_xitems]
+    int64_t *n_xitems;                // device scalar
     int32_t *status;                  // first latched error
 };
+
+// Particles per work item of the pair kernels: a group of more particles is
+// taken as several items (its chunks of kWorkChunk), so that no single item
+// outlasts the others in the persistent queue.
+constexpr int kWorkChunk = 128;
 
 __device__ __forceinline__ void tp_latch(int32_t *status, int32_t code)
 {

@@ -186,6 +186,41 @@ __device__ __forceinline__ Group load_group(const TreeDev &T, int64_t g)
     return G;
 }
 
+// The number of work items: with an LPT order, every group's first chunk and
+// the further chunks of larger groups (k_lpt_keys); without one, the groups.
+__device__ __forceinline__ int64_t work_count(const TreeDev &T, const int32_t *order)
+{
+    const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    if (!order) return G;
+    const int64_t x = *T.n_xitems;
+    return G + (x < T.cap_xitems ? x : T.cap_xitems);
+}
+
+// Work item `item`: with an LPT order the group's particles narrowed to the
+// item's chunk of at most kWorkChunk (order values below cap_groups are the
+// groups' first chunks, the others index the table of further chunks);
+// without one, group `item` whole.  (One inlined load_group on both paths:
+// an early return with a second copy made the packed forward kernel's
+// register allocation and schedule worse, 1.7 % on the clustered 2M box.)
+__device__ __forceinline__ Group load_work(const TreeDev &T, const int32_t *order, int64_t item)
+{
+    int64_t g = item;
+    int i0 = 0;
+    if (order) {
+        const int64_t v = order[item];
+        g = v;
+        if (v >= T.cap_groups) {
+            const int2 x = T.xitem[v - T.cap_groups];
+            g = x.x;
+            i0 = x.y * kWorkChunk;
+        }
+    }
+    Group G = load_group(T, g);
+    G.first += i0;
+    G.ni = order ? min(kWorkChunk, G.ni - i0) : G.ni;
+    return G;
+}
+
 // Shared-memory j tile: group-relative scaled offsets, or for groups that
 // span half the box the raw 64-bit images (their pair differences are taken
 // in integers, which is the exact minimum image).
@@ -409,12 +444,11 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
     __shared__ double red[3][kThreads];
     __shared__ int s_item;
     if (sizeof(R) == 4 && *T.n_general == 0) return;     // every group went to the packed kernel
-    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int64_t W_n = work_count(T, order);
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
-    for (int64_t item = next_item<QUEUE>(queue, -1, &s_item); item < G_n;
+    for (int64_t item = next_item<QUEUE>(queue, -1, &s_item); item < W_n;
          item = next_item<QUEUE>(queue, item, &s_item)) {
-        const int64_t g = order ? order[item] : item;
-        const Group G = load_group(T, g);
+        const Group G = load_work(T, order, item);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
         if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_pair_packed takes these
         for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
@@ -472,9 +506,11 @@ __global__ void __launch_bounds__(kThreads) k_pair(TreeDev T, R *acc, int32_t *q
 
 // The FP32 forward kernel for ordinary groups with eps > 0: packed pair math
 // fed by the entry records.  Each of the 128 threads holds NI particles of
-// the group and takes a slice of the entry pairs of every tile (256 entries):
-// the group's particle columns (NI particles each) and the slices make a grid
-// of columns x floor(128 / columns) threads, and the threads left over idle.
+// the work item (a group, or a chunk of at most kWorkChunk particles of a
+// larger one) and takes a slice of the entry pairs of every tile (256
+// entries): the item's particle columns (NI particles each) and the slices
+// make a grid of columns x floor(128 / columns) threads, and the threads left
+// over idle.
 // Tiles are double buffered in shared memory:
 // while tile t is computed from one buffer, each thread stores its entry pair
 // of tile t+1 (loaded one tile earlier into registers) into the other buffer
@@ -495,13 +531,12 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
     __shared__ float4 SA[2][NT], SB[2][NT];
     __shared__ double red[3 * NI][NT];
     __shared__ int s_item;
-    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int64_t W_n = work_count(T, order);
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const float4 pad = make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
-    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < W_n;
          item = next_item<true>(queue, item, &s_item)) {
-        const int64_t g = order ? order[item] : item;
-        const Group G = load_group(T, g);
+        const Group G = load_work(T, order, item);
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
         const int ne = bad ? 0 : G.ne;
@@ -641,13 +676,12 @@ __global__ void __launch_bounds__(kThreads) k_vjp(TreeDev T, const R *cot, doubl
     __shared__ R part[kThreads / 32][4][kThreads];   // per-warp i-side sums of one tile
     __shared__ int s_item;
     if (sizeof(R) == 4 && *T.n_general == 0) return;     // every group went to the packed kernel
-    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int64_t W_n = work_count(T, order);
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < W_n;
          item = next_item<true>(queue, item, &s_item)) {
-        const int64_t g = order ? order[item] : item;
-        const Group G = load_group(T, g);
+        const Group G = load_work(T, order, item);
         const R sc = scale_of<R>(*G.P), eps2 = eps2_of<R>(*G.P);
         if (sizeof(R) == 4 && !G.wrap && eps2 > R(0)) continue;   // k_vjp_fused takes these
         const int ne = bad ? 0 : G.ne;
@@ -775,17 +809,16 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
     __shared__ float4 IA[kThreads / 2], IB[kThreads / 2], IC[kThreads / 2];
     __shared__ float part[kWarps][NQ][kThreads];
     __shared__ int s_item;
-    const int64_t G_n = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
+    const int64_t W_n = work_count(T, order);
     const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // after the reduce-scatter below, lane holds the sum of value vidx:
     // value 8P + 2q + h (16 values) or 16P + 2q + h (32 values, FWD)
     const int vidx = FWD ? lane : (lane >> 1) & 15;
     const int vP = FWD ? vidx >> 4 : vidx >> 3, vq = FWD ? (vidx >> 1) & 7 : (vidx >> 1) & 3, vh = vidx & 1;
-    for (int64_t item = next_item<true>(queue, -1, &s_item); item < G_n;
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < W_n;
          item = next_item<true>(queue, item, &s_item)) {
-        const int64_t g = order ? order[item] : item;
-        const Group G = load_group(T, g);
+        const Group G = load_work(T, order, item);
         const float sc = G.P->scale, eps2 = G.P->eps2s;
         if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
         const int ne = bad ? 0 : G.ne;
@@ -835,6 +868,7 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                     vx[u] = vy[u] = vz[u] = f2pack(0.f, 0.f);
                 }
                 const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
+                const bool wfull = t0 + (E - 1) * kThreads + warp * 32 + 31 < ne;
                 for (int pp = 0; pp < npe; pp += 2) {
                     float v[NV];
 #pragma unroll
@@ -848,9 +882,7 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                         // padding pair of an odd count of particle pairs, and the
                         // entry slots past the end of the list
                         const bool live = P == 0 || pp + 1 < npr;
-#pragma unroll
-                        for (int u = 0; u < E; u++) {
-                            if (!live || t0 + u * kThreads + warp * 32 >= ne) break;
+                        auto term = [&](int u) {
                             const f2 dx = f2sub(XJ[u], a.x), dy = f2sub(YJ[u], a.y), dz = f2sub(ZJ[u], b.x);
                             const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
                             const f2 s2 = f2add(r2, E2);
@@ -880,6 +912,18 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
                                 sfx = f2fma(alpha, dx, sfx);
                                 sfy = f2fma(alpha, dy, sfy);
                                 sfz = f2fma(alpha, dz, sfz);
+                            }
+                        };
+                        // every slot of this warp holds an entry (all tiles but
+                        // the last): no branch between the E independent terms
+                        if (live && wfull) {
+#pragma unroll
+                            for (int u = 0; u < E; u++) term(u);
+                        } else if (live) {
+#pragma unroll
+                            for (int u = 0; u < E; u++) {
+                                if (t0 + u * kThreads + warp * 32 >= ne) break;
+                                term(u);
                             }
                         }
                         constexpr int B0 = FWD ? 16 : 8;

@@ -91,9 +91,20 @@ __device__ __forceinline__ WalkGroup load_walk_group(const TreeDev &T, int64_t g
 enum { kPrune = 0, kAccept = 1, kOpen = 2 };
 
 // The decision at node nd (w = its walk record) for group W; namb counts the
-// decisions that needed the exact FP64 test.
+// decisions that needed the exact FP64 test.  allin reports, for an opened
+// node, that its box lies wholly within r_cut of the group box for certain:
+// the largest box-to-box distance on the integer grid is below the lower
+// threshold.  Every particle of the node lies in its tight box [lo, hi], and
+// the per-axis centre and half-width taken from it in FP64 cover that box to
+// within an ulp, so each particle's point-to-box gap is at most that distance
+// plus ~1e-15; the grid distance is within 3 sqrt(3) units of 2^-32 of the
+// distance from the FP64 centres and half-widths (three truncations per
+// axis), and the lower threshold lies TP_FILTER_SLACK = 8 units inside r_cut.
+// The reference test of every such particle (FP64 gap < r_cut) therefore
+// keeps it, and the walk may take the particles of an opened leaf with allin
+// set without testing them.
 __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W, int32_t nd, const WNode &w,
-                                           int &namb)
+                                           int &namb, bool &allin)
 {
     const uint64_t T_lo = W.P->T_lo, T_hi = W.P->T_hi;
     const uint32_t ax = absdiff32(w.cx, W.gx), ay = absdiff32(w.cy, W.gy), az = absdiff32(w.cz, W.gz);
@@ -102,6 +113,7 @@ __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W,
     const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
     bool exact = false;
     double gap2d = 0.0, far2d = 0.0;
+    allin = false;
     if (gap2 >= T_hi) return kPrune;
     if (gap2 >= T_lo) {
         exact = true;
@@ -110,11 +122,12 @@ __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W,
                             T.gcy[W.g], T.gcz[W.g], T.ghx[W.g], T.ghy[W.g], T.ghz[W.g], &far2d);
         if (gap2d >= W.P->rc2) return kPrune;
     }
+    const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
+    const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
+    allin = !exact && far2 < T_lo;
     const bool overlap = w.first < W.g1 && W.g0 < w.first + w.count;
     if (overlap) return kOpen;
     if (!exact) {
-        const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
-        const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
         const int A = far2 < T_lo ? 1 : (far2 >= T_hi ? 0 : -1);
         const int B = gap2 >= W.P->TB_hi[w.level] ? 1 : (gap2 < W.P->TB_lo[w.level] ? 0 : -1);
         if (A == 0 || B == 0) return kOpen;
@@ -159,7 +172,8 @@ __device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start,
         }
         const WNode w = T.wn[nd];
         int namb = 0;
-        const int d = decide_node(T, W, nd, w, namb);
+        bool allin;
+        const int d = decide_node(T, W, nd, w, namb, allin);
         ambig += namb;
         if (d == kPrune) {
             nd = w.skip;
@@ -280,7 +294,8 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
             } else {                                   // one node decision
                 const WNode w = T.wn[nd];
                 int namb = 0;
-                const int d = decide_node(T, W, nd, w, namb);
+                bool allin;
+                const int d = decide_node(T, W, nd, w, namb, allin);
                 ambig += namb;
                 if (d == kPrune) {
                     nd = w.skip;
@@ -288,7 +303,12 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
                     if (cnt < bound) out[cnt] = -(nd + 1);
                     cnt++;
                     nd = w.skip;
-                } else if (w.child < 0) {              // an opened leaf: its particles below
+                } else if (w.child < 0 && allin) {     // an opened leaf wholly within r_cut: every particle
+                    for (int32_t k = 0; k < w.count; k++)
+                        if (cnt + k < bound) out[cnt + k] = w.first + k;
+                    cnt += w.count;
+                    nd = w.skip;
+                } else if (w.child < 0) {              // an opened leaf: its particles tested below
                     pcur = w.first;
                     pend = w.first + w.count;
                     nd = w.skip;
@@ -426,21 +446,44 @@ __global__ void k_refit_records(TreeDev T)
     }
 }
 
-// LPT keys for the persistent work queue: groups in descending order of their
-// pair count n_i * n_j (ties by group index, the sort is stable).
+// The sort key of a work item of pair count c: the upper 16 bits of the FP32
+// value of c (exponent and 7 mantissa bits; monotone in c), complemented, so
+// that a two-pass sort puts the items in descending order of c to within 1 %,
+// which is all the queue's balance needs.  Keys lie in [0x3000, 0x7fff];
+// padding takes 0x8000 (unused groups) or 0xffff (unused extra slots).
+__device__ __forceinline__ uint64_t lpt_key(uint64_t c)
+{
+    return (uint64_t)(0x7fffu - (__float_as_uint((float)c) >> 16));
+}
+
+// LPT keys for the persistent work queue: work items in descending order of
+// their pair count n_i * n_j (ties by slot, the sort is stable).  A group's
+// first kWorkChunk particles are the item in its own slot g; each further
+// chunk of a larger group takes a slot past cap_groups and a {group, chunk}
+// entry of the table T.xitem (slots handed out by an atomic counter: the
+// order of equal keys there varies, the items' results do not).  The extra
+// slots beyond the counter keep the padding key their memset gave them.
 __global__ void k_lpt_keys(TreeDev T, uint64_t *key, uint32_t *val)
 {
     const int64_t G = *T.n_groups < T.cap_groups ? *T.n_groups : T.cap_groups;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < T.cap_groups;
          g += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t cost = 0;
-        if (g < G) {
-            cost = (uint64_t)T.gcount[g] * (uint64_t)T.lcnt[g];
-            if (cost > 0xffffffffull) cost = 0xffffffffull;
-        }
-        key[g] = g < G ? 0xffffffffull - cost : 0xffffffffull + 1;   // padding sorts last
+        const int32_t ni = g < G ? T.gcount[g] : 0;
+        const uint64_t cost = g < G ? (uint64_t)(ni < kWorkChunk ? ni : kWorkChunk) * (uint64_t)T.lcnt[g] : 0;
+        key[g] = g < G ? lpt_key(cost) : 0x8000ull;                   // padding sorts last
         val[g] = (uint32_t)g;
         if (g < G) {
+            for (int c = 1; c * kWorkChunk < ni; c++) {
+                const unsigned long long k = atomicAdd(reinterpret_cast<unsigned long long *>(T.n_xitems), 1ull);
+                if ((int64_t)k >= T.cap_xitems) {               // cannot happen: cap_xitems >= n / kWorkChunk
+                    tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
+                    break;
+                }
+                const int32_t nc = ni - c * kWorkChunk < kWorkChunk ? ni - c * kWorkChunk : kWorkChunk;
+                key[T.cap_groups + k] = lpt_key((uint64_t)nc * (uint64_t)T.lcnt[g]);
+                val[T.cap_groups + k] = (uint32_t)(T.cap_groups + k);
+                T.xitem[k] = make_int2((int)g, c);
+            }
             // groups whose pairs the packed FP32 kernels leave to the general ones:
             // offsets that may need the minimum image per pair, or eps = 0
             const BoxPrm &P = T.box[T.gbox[g]];
@@ -538,14 +581,17 @@ void walk_write(TreeDev &T, cudaStream_t s)
     TP_LAUNCH(k_compact, grid_for(T.cap_items, 256), 256, 0, s, T);
 }
 
-// order[] = groups by descending cost; key/val/key2/val2 hold cap_groups each.
+// order[] = work items by descending cost; key/val/key2/val2 hold
+// cap_groups + cap_xitems each.
 void lpt_order(TreeDev &T, uint64_t *key, uint32_t *val, uint64_t *key2, uint32_t *val2,
                void *radix_tmp, cudaStream_t s)
 {
     if (T.cap_groups <= 0) return;
     cudaMemsetAsync(T.n_general, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(T.n_xitems, 0, sizeof(int64_t), s);
+    if (T.cap_xitems > 0) cudaMemsetAsync(key + T.cap_groups, 0xff, sizeof(uint64_t) * (size_t)T.cap_xitems, s);
     TP_LAUNCH(k_lpt_keys, grid_for(T.cap_groups, 256), 256, 0, s, T, key, val);
-    radix_sort(key, val, key2, val2, T.cap_groups, 40, nullptr, 1, radix_tmp, s);
+    radix_sort(key, val, key2, val2, T.cap_groups + T.cap_xitems, 16, nullptr, 1, radix_tmp, s);
 }
 
 void list_stats(TreeDev &T, unsigned long long *inter, int32_t *max_nj, cudaStream_t s)
