@@ -197,7 +197,7 @@ static bool alloc_nodes(tp_tree *t, int64_t cap)
     D.nsrc = P.get<SrcRec>(c);
     D.wn = P.get<WNode>(c);
     t->nch = P.get<uint32_t>(c);
-    t->nofs = P.get<uint32_t>(c);
+    t->nofs = P.get<uint32_t>(c > 1024 ? c : 1024);   // also the topology passes' block sums (608 blocks)
     t->cbnd = P.get<int32_t>(7 * c);
     t->ncot = P.get<double>(3 * c);
     return P.ok;

@@ -12,6 +12,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kLevelGrid = 152 * 4;   // fixed grid: node counts live on the device
+static_assert(kLevelGrid <= 1024, "the block-sum scratch of the topology passes holds 1024 sums");
 
 __device__ __forceinline__ double wrap01(double x)
 {
@@ -162,78 +163,149 @@ __device__ __forceinline__ int child_bounds(const TreeDev &T, int32_t i, int L, 
     return k;
 }
 
-// a4 (count): number of non-empty children of every node of level L; their
-// inner bounds b[1..7] are kept for the write pass.
-__global__ void k_split_count(TreeDev T, int L, uint32_t *nch, int32_t *cb)
+// The contiguous chunk [c0, c1) of a level's nl nodes taken by this block of
+// the level grid.  The count and write passes cut every level the same way,
+// so that the write pass forms the prefix of the child counts from the count
+// pass's block sums (no separate scan).
+__device__ __forceinline__ void level_chunk(int64_t nl, int64_t &c0, int64_t &c1)
 {
+    const int64_t chunk = (nl + gridDim.x - 1) / gridDim.x;
+    c0 = (int64_t)blockIdx.x * chunk;
+    c1 = c0 + chunk < nl ? c0 + chunk : nl;
+    if (c0 > nl) c0 = nl;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// a4 (count): number of non-empty children of every node of level L (their
+// inner bounds b[1..7] are kept for the write pass), and the sum over this
+// block's chunk of the level in part[blockIdx.x].
+__global__ void __launch_bounds__(kBlock) k_split_count(TreeDev T, int L, uint32_t *nch, int32_t *cb,
+                                                        uint32_t *part)
+{
+    __shared__ uint32_t ws[kBlock / 32];
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c0, c1;
+    level_chunk(nl, c0, c1);
+    uint32_t sum = 0;
+    for (int64_t t = c0 + threadIdx.x; t < c1; t += blockDim.x) {
         int32_t b[9];
         const int k = child_bounds(T, (int32_t)(s0 + t), L, b);
         nch[t] = (uint32_t)k;
+        sum += (uint32_t)k;
         if (k > 0)
             for (int o = 1; o < 8; o++) cb[7 * t + o - 1] = b[o];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kBlock / 32; w++) tot += ws[w];
+        part[blockIdx.x] = tot;
+    }
 }
 
-// a4 (write): children of level-L nodes at lstart[L+1] + scan offset, in
-// octant order; skip pointers make the breadth-first array walkable depth
-// first without a stack (next sibling, else the parent's skip).  Level L+1
-// starts right after level L; a level that would pass cap_nodes is dropped
-// whole (status TP_ERR_LIST_OVERFLOW).  Every thread derives the start and
-// the kept count itself; block 0 stores them.  Its zeroing of an overflowing
-// count may race with other blocks' reads, and either value they see gives
-// nnext = 0.
-__global__ void k_split_write(TreeDev T, int L, const uint32_t *nch, const uint32_t *ofs, const int32_t *cb)
+// The children of level-L node i (t-th of its level) at c0 onwards, in octant
+// order; skip pointers make the breadth-first array walkable depth first
+// without a stack (next sibling, else the parent's skip).
+__device__ __forceinline__ void write_children(TreeDev &T, int L, int32_t i, int64_t t, int k, int64_t base,
+                                               int64_t end, const int32_t *cb)
 {
+    if (k == 0 || base + k > end) {     // a leaf, or truncated by an overflow
+        T.child[i] = -1;
+        T.nchild[i] = 0;
+        return;
+    }
+    int32_t b[9];
+    b[0] = T.first[i];
+    b[8] = b[0] + T.count[i];
+    for (int o = 1; o < 8; o++) b[o] = cb[7 * t + o - 1];
+    int j = 0;
+    for (int o = 0; o < 8; o++) {
+        if (b[o + 1] <= b[o]) continue;
+        const int32_t c = (int32_t)(base + j);
+        T.first[c] = b[o];
+        T.count[c] = b[o + 1] - b[o];
+        T.level[c] = (uint8_t)(L + 1);
+        T.parent[c] = i;
+        T.nbx[c] = T.nbx[i];
+        T.child[c] = -1;
+        T.nchild[c] = 0;
+        T.skip[c] = (j == k - 1) ? T.skip[i] : c + 1;
+        j++;
+    }
+    T.child[i] = (int32_t)base;
+    T.nchild[i] = k;
+}
+
+// a4 (write): children of level-L nodes at lstart[L+1] + their exclusive
+// prefix of child counts: the block sums of the chunks before this block's
+// (part, from the count pass) plus a scan within the chunk.  Level L+1 starts
+// right after level L; a level that would pass cap_nodes is dropped whole
+// (status TP_ERR_LIST_OVERFLOW).  Every block derives the level's total
+// itself; block 0 stores the next level's start and count and the node count.
+__global__ void __launch_bounds__(kBlock) k_split_write(TreeDev T, int L, const uint32_t *nch,
+                                                        const uint32_t *part, const int32_t *cb)
+{
+    constexpr int nw = kBlock / 32;
+    __shared__ uint32_t warp_tot[nw], s_red[2][nw];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
-    const int64_t base0 = s0 + nl, counted = T.lcount[L + 1];
-    const bool overflow = base0 + counted > T.cap_nodes;
-    const int64_t nnext = overflow ? 0 : counted;
+    uint32_t before_blk = 0, total = 0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
+        const uint32_t v = part[j];
+        total += v;
+        if (j < (int)blockIdx.x) before_blk += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        before_blk += __shfl_xor_sync(0xffffffffu, before_blk, o);
+    }
+    if (lane == 0) { s_red[0][warp] = total; s_red[1][warp] = before_blk; }
+    __syncthreads();
+    total = before_blk = 0;
+    for (int w = 0; w < nw; w++) { total += s_red[0][w]; before_blk += s_red[1][w]; }
+    const int64_t base0 = s0 + nl;
+    const bool overflow = base0 + (int64_t)total > T.cap_nodes;
+    const int64_t nnext = overflow ? 0 : (int64_t)total;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         T.lstart[L + 1] = base0;
-        if (overflow) {
-            tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
-            T.lcount[L + 1] = 0;
-        }
+        T.lcount[L + 1] = nnext;
+        if (overflow) tp_latch(T.status, TP_ERR_LIST_OVERFLOW);
         *T.n_nodes = base0 + nnext;
     }
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = (int32_t)(s0 + t);
-        if (nch[t] == 0 || nnext == 0) {
-            T.child[i] = -1;
-            T.nchild[i] = 0;
-            continue;
+    int64_t c0, c1;
+    level_chunk(nl, c0, c1);
+    uint32_t carry = before_blk;
+    for (int64_t tb = c0; tb < c1; tb += blockDim.x) {
+        const int64_t t = tb + threadIdx.x;
+        const uint32_t v = t < c1 ? nch[t] : 0u;
+        const uint32_t inc = warp_incl_scan_u32(v);
+        if (lane == 31) warp_tot[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t w = lane < nw ? warp_tot[lane] : 0u;
+            const uint32_t wi = warp_incl_scan_u32(w);
+            if (lane < nw) warp_tot[lane] = wi;
         }
-        int32_t b[9];
-        b[0] = T.first[i];
-        b[8] = b[0] + T.count[i];
-        for (int o = 1; o < 8; o++) b[o] = cb[7 * t + o - 1];
-        const int k = (int)nch[t];
-        const int64_t base = base0 + ofs[t];
-        if (base + k > base0 + nnext) {   // truncated by an overflow
-            T.child[i] = -1;
-            T.nchild[i] = 0;
-            continue;
-        }
-        int j = 0;
-        for (int o = 0; o < 8; o++) {
-            if (b[o + 1] <= b[o]) continue;
-            const int32_t c = (int32_t)(base + j);
-            T.first[c] = b[o];
-            T.count[c] = b[o + 1] - b[o];
-            T.level[c] = (uint8_t)(L + 1);
-            T.parent[c] = i;
-            T.nbx[c] = T.nbx[i];
-            T.child[c] = -1;
-            T.nchild[c] = 0;
-            T.skip[c] = (j == k - 1) ? T.skip[i] : c + 1;
-            j++;
-        }
-        T.child[i] = (int32_t)base;
-        T.nchild[i] = k;
+        __syncthreads();
+        const uint32_t pre = carry + (warp == 0 ? 0u : warp_tot[warp - 1]) + inc - v;
+        if (t < c1)
+            write_children(T, L, (int32_t)(s0 + t), t, nnext == 0 ? 0 : (int)v, base0 + pre, base0 + nnext, cb);
+        carry += warp_tot[nw - 1];
+        __syncthreads();
     }
 }
 
@@ -438,14 +510,14 @@ void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, u
     TP_LAUNCH(k_gather, grid_for(T.n, kBlock), kBlock, 0, s, pos, mass, T);
 }
 
-// Topology and monopoles.  nch/ofs: scratch of cap_nodes u32 each.
+// Topology and monopoles.  nch: scratch of cap_nodes u32; ofs: at least
+// kLevelGrid u32 (the count pass's block sums).
 void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s)
 {
     TP_LAUNCH(k_init_roots, (T.nbox + 127) / 128, 128, 0, s, T);
-    for (int L = 0; L < TP_MAX_LEVEL; L++) {
-        TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch, cb);
-        scan_u32(nch, ofs, 0, T.lcount + L, T.lcount + L + 1, scan_tmp, s);
-        TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, ofs, cb);
+    for (int L = 0; L < TP_MAX_LEVEL; L++) {       // ofs holds the count pass's block sums
+        TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch, cb, ofs);
+        TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, (const uint32_t *)ofs, cb);
     }
     build_moments(T, s);
 }
