@@ -31,6 +31,16 @@ __device__ __forceinline__ uint32_t absdiff32(uint32_t a, uint32_t b)
 
 __device__ __forceinline__ double dminimg(double t) { return __dsub_rn(t, rint(t)); }
 
+// v^2 for a grid gap v < 2^32, as one 32 x 32 -> 64-bit multiply (a 64-bit
+// product would take several).  Every gap the walk squares is at most 2^31
+// (wrap-around differences of 32-bit coordinates, less the half-widths), so
+// a sum of three squares stays below 2^64.
+__device__ __forceinline__ uint64_t sq32(uint64_t v)
+{
+    const uint32_t u = (uint32_t)v;
+    return (uint64_t)u * u;
+}
+
 // Reference FP64 box distances: per axis t = |minimg(a - c)|, s = h + hg,
 // gap = max(0, t - s), far = t + s; sums (x^2 + y^2) + z^2.
 __device__ __forceinline__ double exact_dist2(double ax, double ay, double az, double hx, double hy,
@@ -110,7 +120,7 @@ __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W,
     const uint32_t ax = absdiff32(w.cx, W.gx), ay = absdiff32(w.cy, W.gy), az = absdiff32(w.cz, W.gz);
     const uint64_t sx = (uint64_t)w.hx + W.hx, sy = (uint64_t)w.hy + W.hy, sz = (uint64_t)w.hz + W.hz;
     const uint64_t dx = ax > sx ? ax - sx : 0, dy = ay > sy ? ay - sy : 0, dz = az > sz ? az - sz : 0;
-    const uint64_t gap2 = dx * dx + dy * dy + dz * dz;
+    const uint64_t gap2 = sq32(dx) + sq32(dy) + sq32(dz);
     bool exact = false;
     double gap2d = 0.0, far2d = 0.0;
     allin = false;
@@ -123,7 +133,7 @@ __device__ __forceinline__ int decide_node(const TreeDev &T, const WalkGroup &W,
         if (gap2d >= W.P->rc2) return kPrune;
     }
     const uint64_t fx = ax + sx, fy = ay + sy, fz = az + sz;
-    const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : fx * fx + fy * fy + fz * fz;
+    const uint64_t far2 = ((fx | fy | fz) >> 31) ? ~0ull : sq32(fx) + sq32(fy) + sq32(fz);
     allin = !exact && far2 < T_lo;
     const bool overlap = w.first < W.g1 && W.g0 < w.first + w.count;
     if (overlap) return kOpen;
@@ -146,7 +156,7 @@ __device__ __forceinline__ bool keep_particle(const TreeDev &T, const WalkGroup 
     const uint4 q = T.P32[p];
     const uint32_t qx = absdiff32(q.x, W.gx), qy = absdiff32(q.y, W.gy), qz = absdiff32(q.z, W.gz);
     const uint64_t ex = qx > W.hx ? qx - W.hx : 0, ey = qy > W.hy ? qy - W.hy : 0, ez = qz > W.hz ? qz - W.hz : 0;
-    const uint64_t p2 = ex * ex + ey * ey + ez * ez;
+    const uint64_t p2 = sq32(ex) + sq32(ey) + sq32(ez);
     if (p2 >= W.P->T_hi) return false;
     if (p2 < W.P->T_lo) return true;
     namb++;
