@@ -220,6 +220,9 @@ static bool alloc_groups(tp_tree *t, int64_t cap)
     D.lcnt = P.get<int32_t>(c);
     D.gpad = P.get<int32_t>(c);
     D.icnt = P.get<int32_t>(c);
+    D.kscr = (int32_t)(kTopScratchTotal / (int64_t)(c > 0 ? c : 1) < kTopScratch
+                           ? kTopScratchTotal / (int64_t)(c > 0 ? c : 1) : kTopScratch);
+    D.iscr = P.get<int32_t>(c * (size_t)D.kscr);
     D.ioff = P.get<int64_t>(c);
     // work items: the groups' first chunks and up to cap_xitems further ones
     const size_t cw = c + (size_t)D.cap_xitems;
@@ -327,6 +330,7 @@ static TreeDev window_view(const TreeDev &D, int64_t g0, int64_t ng, int64_t *d_
     V.gux += g0; V.guy += g0; V.guz += g0; V.ghux += g0; V.ghuy += g0; V.ghuz += g0;
     V.gX += g0; V.gY += g0; V.gZ += g0;
     V.gpad += g0; V.loff += g0; V.lcnt += g0; V.icnt += g0; V.ioff += g0;
+    V.iscr += g0 * D.kscr;
     V.n_groups = d_ng;
     V.cap_groups = ng;
     return V;

@@ -115,6 +115,8 @@ struct TreeDev {
     // walk items: subtree tasks and top-level monopoles, group-major, DFS order
     int64_t cap_items;
     int32_t *icnt;                    // [cap_groups] items per group
+    int32_t *iscr;                    // [cap_groups x kscr] each group's first items (count pass)
+    int32_t kscr;                     // items kept per group in iscr
     int64_t *ioff;                    // [cap_groups] first item of each group
     int64_t *n_items;                 // device scalar
     int32_t *item, *igrp, *icnt2;     // [cap_items] item, its group, its entry count
@@ -145,6 +147,12 @@ struct TreeDev {
 // taken as several items (its chunks of kWorkChunk), so that no single item
 // outlasts the others in the persistent queue.
 constexpr int kWorkChunk = 128;
+
+// Items of a group's top walk kept by the count pass, so that the write pass
+// copies them instead of walking again (groups with more walk again): up to
+// kTopScratch per group, within kTopScratchTotal items for the whole tree.
+constexpr int kTopScratch = 1024;
+constexpr int64_t kTopScratchTotal = 1ll << 28;
 
 __device__ __forceinline__ void tp_latch(int32_t *status, int32_t code)
 {

@@ -204,7 +204,9 @@ __device__ int32_t walk_top(const TreeDev &T, const WalkGroup &W, int32_t start,
     return cnt;
 }
 
-// Top walk of every group: item counts (WRITE = false) or items (WRITE = true).
+// Top walk of every group: item counts, and the first kscr items in the
+// group's scratch (WRITE = false); or the items at their offsets (WRITE =
+// true), copied from the scratch when it holds them all, else walked again.
 template <bool WRITE>
 __global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
 {
@@ -213,17 +215,22 @@ __global__ void __launch_bounds__(kBlock) k_walk_top(TreeDev T, int32_t split)
     unsigned long long ambig = 0;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const WalkGroup W = load_walk_group(T, g);
         if (!WRITE) {
+            const WalkGroup W = load_walk_group(T, g);
             int64_t slots = 0;
-            T.icnt[g] = walk_top(T, W, T.gbox[g], split, nullptr, 0, ambig, &slots);
+            T.icnt[g] = walk_top(T, W, T.gbox[g], split, T.iscr + g * T.kscr, T.kscr, ambig, &slots);
             T.gpad[g] = slots < 0x7fffffff ? (int32_t)slots : 0x7fffffff;
         } else {
             const int64_t o = T.ioff[g];
             const int64_t n = T.icnt[g];
             if (o + n > T.cap_items) continue;
-            const int32_t c = walk_top(T, W, T.gbox[g], split, T.item + o, n, ambig);
-            for (int64_t k = 0; k < c && k < n; k++) T.igrp[o + k] = (int32_t)g;
+            if (n <= T.kscr) {                      // the count pass kept them all
+                const int32_t *src = T.iscr + g * T.kscr;
+                for (int64_t k = 0; k < n; k++) T.item[o + k] = src[k];
+            } else {
+                walk_top(T, load_walk_group(T, g), T.gbox[g], split, T.item + o, n, ambig);
+            }
+            for (int64_t k = 0; k < n; k++) T.igrp[o + k] = (int32_t)g;
         }
     }
     if (!WRITE && ambig) atomicAdd(T.n_ambig, ambig);
