@@ -22,6 +22,7 @@
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int32_t kBigTask = 256;   // particles of a walk task taken in the first sweep
 
 __device__ __forceinline__ uint32_t absdiff32(uint32_t a, uint32_t b)
 {
@@ -278,9 +279,15 @@ __global__ void __launch_bounds__(kBlock) k_walk_task(TreeDev T, unsigned long l
             if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(nm));
             base = __shfl_sync(full, base, leader);
             if (it < 0 && !exhausted) {
+                // two sweeps over the items: tasks of more than kBigTask
+                // particles first, then the rest, so that no long task starts
+                // near the end of the launch
                 const int64_t cand = (int64_t)base + __popc(nm & below);
-                if (cand < NI) {
-                    it = cand;
+                const int64_t c = cand < NI ? cand : cand - NI;
+                if (cand < 2 * NI && (cand < NI) != (T.ibound[c] > kBigTask)) {
+                    // this sweep leaves the item to the other one
+                } else if (cand < 2 * NI) {
+                    it = c;
                     const int32_t v = T.item[it];
                     out = T.pent + T.ibpos[it];
                     if (v < 0) {                       // an accepted monopole
