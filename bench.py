@@ -433,6 +433,12 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
     kp_ms, kv_ms, kw_ms = mean(k_pair_ms), mean(k_vjp_ms), mean(k_fused_ms)
     soft = "true" if args.xi == "softened" else "false"
     rf = "true" if args.rsqrt == "refined" else "false"
+    # the adjoint kernels of the tuned shape: E entries per thread; at E = 8 the
+    # entry-packed kernel (four pairs of entries per thread) in the one pass and
+    # four entries per thread for the adjoint alone
+    adj_kernel = (lambda fwd: f"k_vjp_epack<4, {fwd}, {soft}, {rf}>" if fwd == "true" else
+                  f"k_vjp_fused<4, {fwd}, {soft}, {rf}>") if tile[1] == 8 else \
+        (lambda fwd: f"k_vjp_fused<{tile[1]}, {fwd}, {soft}, {rf}>")
     meas_ffma = measure_peak("fp32")
     meas_ffma2 = measure_peak("fp32x2")
     meas_dfma = measure_peak("fp64")
@@ -446,11 +452,11 @@ def run_ours(args, rank, world, local_rank, paper_regime=False):
                        **({} if args.xi == "plain" else {"xi": "softened: cutoff argument 2 sqrt(r^2+eps^2)/r_cut"}),
                        **({} if args.rsqrt == "hardware" else
                           {"rsqrt": "refined: 1/s from an estimate and the paper's third-order step"})),
-        "roofline": roofline(f"k_vjp_fused<{tile[1]}, true, {soft}, {rf}>", kw_ms, FUSED_FLOPS_PER_INTERACTION,
+        "roofline": roofline(adj_kernel("true"), kw_ms, FUSED_FLOPS_PER_INTERACTION,
                              "one pass: forward (Eq. 2 x Eq. 3) and adjoint; the largest share of the step"),
         "roofline_forward": roofline(f"k_pair_packed<{tile[0]}, 8, {soft}, {rf}>", kp_ms, FLOPS_PER_INTERACTION,
                                      "FP32 forward pair kernel, separate call"),
-        "roofline_adjoint": roofline(f"k_vjp_fused<{tile[1]}, false, {soft}, {rf}>", kv_ms,
+        "roofline_adjoint": roofline(adj_kernel("false"), kv_ms,
                                      VJP_FLOPS_PER_INTERACTION, "FP32 adjoint pair kernel, separate call"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": tot_e2e / args.steps},

@@ -235,7 +235,9 @@ tp_status tp_tree_free(tp_tree *t);
 
 /* Tile shape of the FP32 pair kernels, a tuning knob with no counterpart in
  * the paper: group particles per thread of the forward kernel (1, 2 or 4) and
- * list entries per thread of the adjoint kernel (2 or 4); 2 and 4 by default.
+ * list entries per thread of the adjoint kernel (2 or 4; or 8, held as four
+ * pairs of entries in the f32x2 operations of the forces-and-adjoint pass,
+ * with 4 for the adjoint alone); 2 and 4 by default.
  * Applies to later force / vjp calls on t (not to calls already enqueued).
  * Results agree to rounding (the per-particle sums are taken in a different
  * order).  TP_ERR_INVALID_ARG for other values.                              */

@@ -112,7 +112,7 @@ def tune_boxes(boxes, kinds, base_params, cache_path: str | None = None, candida
 
 
 def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cache_path: str | None = None,
-              fwd_choices=(2, 1, 4), adj_choices=(4, 2), reps: int = 3) -> tuple[int, int]:
+              fwd_choices=(2, 1, 4), adj_choices=(4, 2, 8), reps: int = 3) -> tuple[int, int]:
     """Tile shape of `tree` (set on it and returned): group particles per
     thread of the forward kernel, timed on the force call, and list entries
     per thread of the adjoint kernel, timed on the one-pass forces + adjoint

@@ -941,7 +941,7 @@ tp_status tp_tree_set_walk_budget(tp_tree *t, int64_t budget)
 tp_status tp_tree_set_tile(tp_tree *t, int32_t fwd_particles, int32_t adj_entries)
 {
     if (!t || (fwd_particles != 1 && fwd_particles != 2 && fwd_particles != 4) ||
-        (adj_entries != 2 && adj_entries != 4))
+        (adj_entries != 2 && adj_entries != 4 && adj_entries != 8))
         return TP_ERR_INVALID_ARG;
     t->fwd_particles = fwd_particles;
     t->adj_entries = adj_entries;

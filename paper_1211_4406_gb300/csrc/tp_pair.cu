@@ -1000,6 +1000,209 @@ __global__ void __launch_bounds__(kThreads, E >= 4 ? 4 : (FWD ? 5 : 6)) k_vjp_fu
     }
 }
 
+// The same adjoint (with FWD, the forward sum too) with two list entries,
+// not two particles, in each f32x2 operation.  Each thread holds EP pairs of
+// entries (2 EP entries: a tile is 2 EP x 128), and the work item's particles
+// are staged in shared memory with every value duplicated, {x, x, y, y},
+// {z, z, wx, wx}, {wy, wy, wz, wz}, so that a particle enters both halves of
+// a pair without a move.  The entry side v sums in registers per pair (its
+// halves are two entries).  The particle side sums over the thread's pairs
+// in packed form, then over the two halves, and the warp reduce-scatters 16
+// values per step: two particles' 7 quantities (FWD) or four particles' 4.
+// One reduce-scatter thus serves 2 EP entries of a thread instead of E, which
+// halves its shuffles, selects and adds per interaction at EP = 4, in about
+// the registers of k_vjp_fused<4>: a pair's offsets hold two entries rather
+// than one entry twice.
+template <int EP, bool FWD, bool SOFT, bool RF>
+__global__ void __launch_bounds__(kThreads, 4) k_vjp_epack(TreeDev T, const float *cot, double *gs, double *ncot,
+                                                           int32_t *queue, const int32_t *order, float *acc)
+{
+    constexpr int kWarps = kThreads / 32;
+    constexpr unsigned kFull = 0xffffffffu;
+    constexpr int NQ = FWD ? 7 : 4;          // A, B (3), with FWD also F (3)
+    constexpr int NP = FWD ? 2 : 4;          // particles per reduce-scatter
+    constexpr int kSlot = FWD ? 8 : 4;       // values per particle in it (FWD: one padding)
+    constexpr int kRow = 2 * kThreads;       // entries of one pair slot across the CTA
+    __shared__ ulonglong2 IA[kThreads], IB[kThreads], IC[kThreads];
+    __shared__ float part[kWarps][NQ][kThreads];
+    __shared__ int s_item;
+    const int64_t W_n = work_count(T, order);
+    const bool bad = *T.status == TP_ERR_LIST_OVERFLOW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // after the reduce-scatter, lanes 2m and 2m+1 hold value m = kSlot P + q
+    const int vidx = (lane >> 1) & 15;
+    const int vP = vidx / kSlot, vq = vidx % kSlot;
+    for (int64_t item = next_item<true>(queue, -1, &s_item); item < W_n;
+         item = next_item<true>(queue, item, &s_item)) {
+        const Group G = load_work(T, order, item);
+        const float sc = G.P->scale, eps2 = G.P->eps2s;
+        if (G.wrap || !(eps2 > 0.f)) continue;              // the general kernel takes these
+        const int ne = bad ? 0 : G.ne;
+        for (int i0 = 0; i0 < G.ni; i0 += kThreads) {
+            const int nic = min(kThreads, G.ni - i0);
+            const int npad = (nic + NP - 1) / NP * NP;      // particles rounded up to the step
+            __syncthreads();
+            if (threadIdx.x < npad) {
+                float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, wx = 0.f, wy = 0.f, wz = 0.f;   // pad: far, no weight
+                if (threadIdx.x < nic) {
+                    const int32_t p = G.first + i0 + threadIdx.x;
+                    const int64_t o = T.perm[p];
+                    x = Arith<float>::from_fixed(T.X[p], G.X, sc);
+                    y = Arith<float>::from_fixed(T.Y[p], G.Y, sc);
+                    z = Arith<float>::from_fixed(T.Z[p], G.Z, sc);
+                    wx = cot[3 * o]; wy = cot[3 * o + 1]; wz = cot[3 * o + 2];
+                }
+                IA[threadIdx.x] = make_ulonglong2(f2pack(x, x), f2pack(y, y));
+                IB[threadIdx.x] = make_ulonglong2(f2pack(z, z), f2pack(wx, wx));
+                IC[threadIdx.x] = make_ulonglong2(f2pack(wy, wy), f2pack(wz, wz));
+            }
+            float sh[NQ], sl[NQ];                           // compensated FP32 sums across tiles
+#pragma unroll
+            for (int q = 0; q < NQ; q++) sh[q] = sl[q] = 0.f;
+            __syncthreads();
+            for (int t0 = 0; t0 < ne; t0 += EP * kRow) {
+                f2 XJ[EP], YJ[EP], ZJ[EP], MJ[EP], vx[EP], vy[EP], vz[EP];
+#pragma unroll
+                for (int u = 0; u < EP; u++) {
+                    const int q = t0 + u * kRow + 2 * (int)threadIdx.x;
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 r0 = q < ne ? T.rec[G.e0 + q] : z4;
+                    const float4 r1 = q + 1 < ne ? T.rec[G.e0 + q + 1] : z4;
+                    XJ[u] = f2pack(r0.x, r1.x); YJ[u] = f2pack(r0.y, r1.y); ZJ[u] = f2pack(r0.z, r1.z);
+                    MJ[u] = f2pack(r0.w, r1.w);                 // 0 for an empty slot
+                    vx[u] = vy[u] = vz[u] = f2pack(0.f, 0.f);
+                }
+                const f2 E2 = f2pack(eps2, eps2), M3 = f2pack(-3.f, -3.f);
+                const bool wfull = t0 + (EP - 1) * kRow + 64 * warp + 63 < ne;
+                for (int k0 = 0; k0 < npad; k0 += NP) {
+                    float v[16];
+#pragma unroll
+                    for (int P = 0; P < NP; P++) {
+                        const ulonglong2 a = IA[k0 + P], b = IB[k0 + P], c = IC[k0 + P];
+                        const f2 X = a.x, Y = a.y, Z = b.x, WX = b.y, WY = c.x, WZ = c.y;
+                        f2 sa = f2pack(0.f, 0.f), sbx = sa, sby = sa, sbz = sa, sfx = sa, sfy = sa, sfz = sa;
+                        auto term = [&](int u) {
+                            const f2 dx = f2sub(XJ[u], X), dy = f2sub(YJ[u], Y), dz = f2sub(ZJ[u], Z);
+                            const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+                            const f2 s2 = f2add(r2, E2);
+                            float r2a, r2b, s2a, s2b, ma, mb;
+                            f2unpack(r2, r2a, r2b);
+                            f2unpack(s2, s2a, s2b);
+                            f2unpack(MJ[u], ma, mb);
+                            const f2 ri = RF ? rsqrt_refined(s2) : f2pack(rsqrt_approx(s2a), rsqrt_approx(s2b));
+                            const f2 x = SOFT ? f2pack(sqrt_approx(s2a), sqrt_approx(s2b))   // xi
+                                              : f2pack(sqrt_approx(r2a), sqrt_approx(r2b));
+                            f2 gv, gp;
+                            g_gpx_packed(x, gv, gp);
+                            const f2 ri2 = f2mul(ri, ri);
+                            // m_j / s'^3, zero for the particle itself (and coincident pairs)
+                            const f2 mr3 = f2mul(f2pack(r2a > 0.f ? ma : 0.f, r2b > 0.f ? mb : 0.f), f2mul(ri2, ri));
+                            const f2 dw = f2fma(dz, WZ, f2fma(dy, WY, f2mul(dx, WX)));
+                            const f2 alpha = f2mul(gv, mr3);                       // m phi
+                            const f2 beta = f2mul(f2mul(f2fma(gv, f2mul(M3, ri2), gp), mr3), dw);   // m psi (d.w)
+                            vx[u] = f2fma(beta, dx, f2fma(alpha, WX, vx[u]));
+                            vy[u] = f2fma(beta, dy, f2fma(alpha, WY, vy[u]));
+                            vz[u] = f2fma(beta, dz, f2fma(alpha, WZ, vz[u]));
+                            sa = f2add(sa, alpha);
+                            sbx = f2fma(beta, dx, sbx);
+                            sby = f2fma(beta, dy, sby);
+                            sbz = f2fma(beta, dz, sbz);
+                            if (FWD) {
+                                sfx = f2fma(alpha, dx, sfx);
+                                sfy = f2fma(alpha, dy, sfy);
+                                sfz = f2fma(alpha, dz, sfz);
+                            }
+                        };
+                        // warp-uniform skips of terms that would be exact zeros: padding
+                        // particles, and pair slots of this warp past the list's end
+                        if (k0 + P < nic) {
+                            if (wfull) {
+#pragma unroll
+                                for (int u = 0; u < EP; u++) term(u);
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < EP; u++) {
+                                    if (t0 + u * kRow + 64 * warp >= ne) break;
+                                    term(u);
+                                }
+                            }
+                        }
+                        float l, h;
+                        f2unpack(sa, l, h); v[kSlot * P + 0] = l + h;
+                        f2unpack(sbx, l, h); v[kSlot * P + 1] = l + h;
+                        f2unpack(sby, l, h); v[kSlot * P + 2] = l + h;
+                        f2unpack(sbz, l, h); v[kSlot * P + 3] = l + h;
+                        if (FWD) {
+                            f2unpack(sfx, l, h); v[kSlot * P + 4] = l + h;
+                            f2unpack(sfy, l, h); v[kSlot * P + 5] = l + h;
+                            f2unpack(sfz, l, h); v[kSlot * P + 6] = l + h;
+                            v[kSlot * P + 7] = 0.f;
+                        }
+                    }
+                    // reduce-scatter of the 16 values over the warp's 32 lanes
+#pragma unroll
+                    for (int lvl = 0; lvl < 4; lvl++) {
+                        const int off = 16 >> lvl, half = 8 >> lvl;
+                        const bool upper = (lane & off) != 0;
+#pragma unroll
+                        for (int kk = 0; kk < half; kk++) {
+                            const float send = upper ? v[kk] : v[kk + half];
+                            const float keep = upper ? v[kk + half] : v[kk];
+                            v[kk] = keep + __shfl_xor_sync(kFull, send, off);
+                        }
+                    }
+                    v[0] += __shfl_xor_sync(kFull, v[0], 1);
+                    if ((lane & 1) == 0 && vq < NQ) part[warp][vq][k0 + vP] = v[0];
+                }
+#pragma unroll
+                for (int u = 0; u < EP; u++) {
+                    const int q = t0 + u * kRow + 2 * (int)threadIdx.x;
+                    float l, h;
+                    if (q < ne) {
+                        const int32_t e = T.ent[G.e0 + q];
+                        double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
+                        f2unpack(vx[u], l, h); atomicAdd(dst, (double)l);
+                        f2unpack(vy[u], l, h); atomicAdd(dst + 1, (double)l);
+                        f2unpack(vz[u], l, h); atomicAdd(dst + 2, (double)l);
+                    }
+                    if (q + 1 < ne) {
+                        const int32_t e = T.ent[G.e0 + q + 1];
+                        double *dst = e >= 0 ? gs + 3 * (int64_t)e : ncot + 3 * (int64_t)(-e - 1);
+                        f2unpack(vx[u], l, h); atomicAdd(dst, (double)h);
+                        f2unpack(vy[u], l, h); atomicAdd(dst + 1, (double)h);
+                        f2unpack(vz[u], l, h); atomicAdd(dst + 2, (double)h);
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x < nic) {
+#pragma unroll
+                    for (int k = 0; k < NQ; k++) {
+                        float t = 0.f;
+#pragma unroll
+                        for (int w = 0; w < kWarps; w++) t += part[w][k][threadIdx.x];
+                        two_sum_add(sh[k], sl[k], t);
+                    }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x < nic) {
+                const int32_t p = G.first + i0 + threadIdx.x;
+                const int64_t o = T.perm[p];
+                const double sA = (double)sh[0] + (double)sl[0];
+                atomicAdd(gs + 3 * (int64_t)p, -(sA * (double)cot[3 * o] + ((double)sh[1] + (double)sl[1])));
+                atomicAdd(gs + 3 * (int64_t)p + 1, -(sA * (double)cot[3 * o + 1] + ((double)sh[2] + (double)sl[2])));
+                atomicAdd(gs + 3 * (int64_t)p + 2, -(sA * (double)cot[3 * o + 2] + ((double)sh[3] + (double)sl[3])));
+                if (FWD) {
+                    const double gk2 = G.P->gk2;
+#pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        acc[3 * o + c] = (float)(gk2 * ((double)sh[4 + c] + (double)sl[4 + c]));
+                }
+            }
+        }
+    }
+}
+
 // Node cotangents reach member particles through the centre of mass:
 // P_a = P_parent(a) + c_a / M_a, taken level by level from the roots down (in
 // place of c_a), so each node's sum runs root..node in that order; then
@@ -1198,22 +1401,34 @@ void pair_forward_f32_t(TreeDev &T, float *acc, int32_t *queue, const int32_t *o
 }
 
 // The fused adjoint kernel with E entries per thread, with or without the
-// forward sum, on its own occupancy.
+// forward sum, on its own occupancy.  E = 8 takes the entry-packed kernel
+// (four pairs of entries per thread) for the forces and adjoint in one pass,
+// and four entries per thread for the adjoint alone, whose four particle-side
+// quantities gain less from the packing than the one pass's seven (measured:
+// one pass 16.67 -> 16.47 ms on the clustered 2M box and 25.3 -> 23.1 ms in
+// the paper regime; the adjoint alone 14.5 -> 15.4 and 20.0 -> 22.7 ms).
 template <int E, bool SOFT, bool RF>
 void launch_vjp_fused_rf(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue,
                          const int32_t *order, int64_t G, float *acc, cudaStream_t s)
 {
-    static const int nbf = occupancy(k_vjp_fused<E, false, SOFT, RF>, kThreads);
-    static const int nbw = occupancy(k_vjp_fused<E, true, SOFT, RF>, kThreads);
     auto grid_of = [&](int per_sm) {
         int64_t gr = (int64_t)num_sms() * per_sm;
         return (int)(gr > G ? G : gr);
     };
+    if (E == 8 && acc) {
+        static const int nbw = occupancy(k_vjp_epack<4, true, SOFT, RF>, kThreads);
+        auto kw = k_vjp_epack<4, true, SOFT, RF>;
+        TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
+        return;
+    }
+    constexpr int EF = E == 8 ? 4 : E;
+    static const int nbf = occupancy(k_vjp_fused<EF, false, SOFT, RF>, kThreads);
+    static const int nbw = occupancy(k_vjp_fused<EF, true, SOFT, RF>, kThreads);
     if (acc) {
-        auto kw = k_vjp_fused<E, true, SOFT, RF>;
+        auto kw = k_vjp_fused<EF, true, SOFT, RF>;
         TP_LAUNCH(kw, grid_of(nbw), kThreads, 0, s, T, cot, gs, ncot, queue, order, acc);
     } else {
-        auto kf = k_vjp_fused<E, false, SOFT, RF>;
+        auto kf = k_vjp_fused<EF, false, SOFT, RF>;
         TP_LAUNCH(kf, grid_of(nbf), kThreads, 0, s, T, cot, gs, ncot, queue, order, nullptr);
     }
 }
@@ -1242,6 +1457,8 @@ void vjp_pairs_t(TreeDev &T, const R *cot, double *gs, double *ncot, int32_t *qu
         if (ev0) record_timing_event(ev0, s);
         if (adj_entries == 2)
             launch_vjp_fused<2, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
+        else if (adj_entries == 8)
+            launch_vjp_fused<8, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
         else
             launch_vjp_fused<4, SOFT>(T, (const float *)cot, gs, ncot, queue + 1, order, G, acc, s);
         if (ev1) record_timing_event(ev1, s);

@@ -34,7 +34,7 @@ from . import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "kernel_traffic.json")
-TRAFFIC_KERNELS = ("k_pair_packed", "k_vjp_fused")
+TRAFFIC_KERNELS = ("k_pair_packed", "k_vjp_fused", "k_vjp_epack")
 
 
 def kernel_key(name: str) -> str:

@@ -74,7 +74,7 @@ def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
         t.close()
 
 
-@pytest.mark.parametrize("tile", [(1, 2), (1, 4), (2, 2), (2, 4), (4, 4)])
+@pytest.mark.parametrize("tile", [(1, 2), (1, 4), (2, 2), (2, 4), (4, 4), (2, 8)])
 def test_every_tile_shape(tile):
     """Each tile shape (forward particles per thread, adjoint entries per
     thread) meets the oracle bounds, for the separate and the one-pass calls."""
