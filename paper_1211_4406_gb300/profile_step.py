@@ -1,7 +1,7 @@
 """Run the hot path once or a few times on a synthetic clustered box, for
 profilers (ncu launch lists and single-kernel captures).
 
-  python -m paper_1211_4406_gb300.profile_step [--n N] [--steps K] [--what step|force|vjp|fused|all]
+  python -m paper_1211_4406_gb300.profile_step [--n N] [--steps K] [--what step|force|vjp|fused|all] [--tile F,A]
 
 --n 2097152 is the benchmark workload (128^3 particles, 2000 NFW halos,
 r_cut = 3/128); smaller n keeps the recipe (halo count, r_cut and eps scale
@@ -96,8 +96,8 @@ def record_traffic(csv_path: str, n: int, out_path: str | None = None, entries: 
                            "ncu_ms_per_launch": v["ns"] / v["launches"] / 1e6}
                        for k, v in out.items()},
            "command": ("ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                       "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused\" -c 3 --csv --log-file "
-                       f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1 --what all")}
+                       "--clock-control none -k regex:\"k_pair_packed|k_vjp_fused|k_vjp_epack\" -c 3 --csv --log-file "
+                       f"<csv> python -m paper_1211_4406_gb300.profile_step --n {n} --steps 1 --what all --tile 2,8")}
     out_path = out_path or TRAFFIC_JSON
     os.makedirs(os.path.dirname(out_path), exist_ok=True)
     with open(out_path, "w") as f:
@@ -132,6 +132,8 @@ def main():
                     help="treepm: rebuild + short-range force + PM force on the mesh of r_cut = 3 spacings")
     ap.add_argument("--record-traffic", metavar="CSV")
     ap.add_argument("--entries", type=int, help="list entries of the captured tree (printed by the run)")
+    ap.add_argument("--tile", default="2,8", help="forward particles and adjoint entries per thread "
+                    "(tp_tree_set_tile; 2,8 is the shape the autotuner picks for the clustered recipe)")
     args = ap.parse_args()
     if args.record_traffic:
         print(json.dumps(record_traffic(args.record_traffic, args.n, entries=args.entries)))
@@ -146,6 +148,7 @@ def main():
     cot = torch.tensor(inputs.cotangent(box.n, box.seed + 7), device="cuda")
     t = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit,
                                          box.n_leaf, "fp32"))
+    t.set_tile(*(int(v) for v in args.tile.split(",")))
     acc = torch.empty((box.n, 3), dtype=torch.float32, device="cuda")
     grad = torch.empty((box.n, 3), dtype=torch.float64, device="cuda")
     pm = PMSolver(int(round(3.0 / box.r_cut)), box.r_cut, box.G) if args.what == "treepm" else None

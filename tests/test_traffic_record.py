@@ -83,6 +83,6 @@ def test_committed_record_names_the_bench_kernels():
     stream and below 100 bytes."""
     rec = json.load(open(ps.TRAFFIC_JSON))
     assert rec["recipe"] == "clustered" and rec["entries"] > 0
-    assert set(rec["kernels"]) == {"k_pair_packed<2,8,0,0>", "k_vjp_fused<4,0,0,0>", "k_vjp_fused<4,1,0,0>"}
+    assert set(rec["kernels"]) == {"k_pair_packed<2,8,0,0>", "k_vjp_fused<4,0,0,0>", "k_vjp_epack<4,1,0,0>"}
     for k in rec["kernels"].values():
         assert 16 <= k["bytes_per_launch"] / rec["entries"] < 100
