@@ -229,7 +229,8 @@ class ShortRangeTree:
     # -- tuning and kernel timing ----------------------------------------------
     def set_tile(self, fwd_particles: int = 2, adj_entries: int = 4) -> None:
         """Particles per thread of the forward pair kernel (1, 2, 4) and list
-        entries per thread of the adjoint kernel (2, 4)."""
+        entries per thread of the adjoint kernel (2, 4; or 8, held as four
+        pairs of entries in the one-pass kernel, 4 for the adjoint alone)."""
         _lib.check(_lib.load().tp_tree_set_tile(self.handle, int(fwd_particles), int(adj_entries)),
                    "tp_tree_set_tile")
         self.tile = (int(fwd_particles), int(adj_entries))
