@@ -14,9 +14,9 @@ is held to 2e-4 (the bound is recorded as unmet there).  Which box exceeds
 carry larger FP32 offsets): measured 1.26e-4 in a uniform box of 361k
 particles, at a force 1e-3 of the median, in one run, and 1.40e-4 in a
 clustered box of 626k particles (n_crit 48), at a force 0.036 of the median,
-in another; every other box stayed below 7.2e-5.  The maximum with the floor at 1e-2 x the
-median is printed as well.  The oracle's walks take a minute of CPU, so this
-runs only with TP_ONEOFF=1.
+in another; every other box stayed below 7.2e-5.  The maximum with the
+floor at 1e-2 x the median is printed as well.  The oracle's walks take a
+minute of CPU, so this runs only with TP_ONEOFF=1.
 """
 import numpy as np
 import pytest

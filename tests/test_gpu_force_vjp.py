@@ -42,7 +42,8 @@ def test_force_vjp_matches_oracle_and_separate_calls(k, n):
     t.close()
 
 
-def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
+@pytest.mark.parametrize("adj_tile", [4, 8])
+def test_force_vjp_fp64_and_chunked_and_box_spanning_groups(adj_tile):
     boxes = [inputs.config_box(1, n_override=nn) for nn in (729, 4096)] + [inputs.config_box(2, n_override=2 ** 14)]
     pos = torch.tensor(np.concatenate([b.pos for b in boxes]), device="cuda")
     mass = torch.tensor(np.concatenate([b.mass for b in boxes]), device="cuda")
@@ -51,6 +52,7 @@ def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
     for precision in ("fp32", "fp64"):
         prm = [Params(b.G, b.eps, b.r_cut, b.theta, 32, 8, precision) for b in boxes]
         t = ShortRangeTree(pos, mass, prm, box_offsets=offs)
+        t.set_tile(2, adj_tile)
         cot = torch.tensor(w, device="cuda")
         acc, grad = t.force_vjp(cot)
         a_sep, g_sep = t.force().clone(), t.vjp(cot).cpu().numpy()
@@ -62,10 +64,18 @@ def test_force_vjp_fp64_and_chunked_and_box_spanning_groups():
         else:
             rms, mx = rel_err(acc.double().cpu().numpy(), a_sep.double().cpu().numpy())
             assert rms <= 1e-6 and mx <= 1e-4, (rms, mx)
-            assert np.abs(grad.cpu().numpy() - g_sep).max() <= 1e-6 * scale
+            d = np.abs(grad.cpu().numpy() - g_sep)
+            if adj_tile == 8:
+                # the entry-packed one pass sums in another FP32 order than the
+                # adjoint alone (measured max 8e-6 of the rms): the per-coordinate
+                # FP32 bound of the oracle comparisons
+                assert np.all(d <= 1e-4 * np.maximum(np.abs(g_sep), scale)), float(d.max() / scale)
+            else:
+                assert d.max() <= 1e-6 * scale
             # chunked: the same pass window by window
             prm_c = [Params(b.G, b.eps, b.r_cut, b.theta, 32, 8, precision, chunked=True) for b in boxes]
             tc = ShortRangeTree(pos, mass, prm_c, box_offsets=offs)
+            tc.set_tile(2, adj_tile)
             assert tc.stats()["n_windows"] > 1
             acc_c, grad_c = tc.force_vjp(cot)
             assert torch.equal(acc, acc_c)

@@ -66,7 +66,8 @@ def group_sizes(ot):
 
 @pytest.mark.parametrize("box", boxes(), ids=lambda b: b.name)
 @pytest.mark.parametrize("variant", [{}, {"xi": "softened"}, {"rsqrt": "refined"}], ids=["plain", "xi_soft", "rsqrt"])
-def test_large_groups_against_oracle(box, variant):
+@pytest.mark.parametrize("adj_tile", [4, 8])
+def test_large_groups_against_oracle(box, variant, adj_tile):
     soft = variant.get("xi") == "softened"
     refined = variant.get("rsqrt") == "refined"
     ot = oracle.OracleTree(box.pos, box.mass, box.n_leaf, box.n_crit)
@@ -83,6 +84,7 @@ def test_large_groups_against_oracle(box, variant):
             continue                                        # the refined root is an FP32 variant
         t = ShortRangeTree(pos, mass, Params(box.G, box.eps, box.r_cut, box.theta, box.n_crit, box.n_leaf,
                                              prec, **variant))
+        t.set_tile(2, adj_tile)                             # 8: the entry-packed one pass
         c = cot if prec == "fp32" else cot.double()
         a = t.force().double().cpu().numpy()
         g = t.vjp(c).cpu().numpy()
