@@ -112,7 +112,7 @@ def tune_boxes(boxes, kinds, base_params, cache_path: str | None = None, candida
 
 
 def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cache_path: str | None = None,
-              fwd_choices=(2, 1, 4), adj_choices=(4, 2, 8), reps: int = 3) -> tuple[int, int]:
+              fwd_choices=(2, 1, 4), adj_choices=(4, 2, 8), reps: int = 5) -> tuple[int, int]:
     """Tile shape of `tree` (set on it and returned): group particles per
     thread of the forward kernel, timed on the force call, and list entries
     per thread of the adjoint kernel, timed on the one-pass forces + adjoint
@@ -129,27 +129,26 @@ def tune_tile(tree: ShortRangeTree, pos, mass, cot, key: str | None = None, cach
     grad = torch.empty((tree.n, 3), dtype=torch.float64, device=pos.device)
     tree.rebuild(pos, mass)
 
-    def median_ms(fn):
-        ts = []
+    def medians_ms(choices, set_choice, fn):
+        """Median event time of fn for every choice, the choices interleaved
+        round by round (one untimed round first), so that a drift of the
+        clocks or of the caches over the tuning does not favour one."""
+        ts = {c: [] for c in choices}
         for r in range(reps + 1):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            b.synchronize()
-            if r:
-                ts.append(a.elapsed_time(b))
-        ts.sort()
-        return ts[len(ts) // 2]
+            for c in choices:
+                set_choice(c)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                if r:
+                    ts[c].append(a.elapsed_time(b))
+        return {c: sorted(v)[len(v) // 2] for c, v in ts.items()}
 
-    fwd_ms, adj_ms = {}, {}
-    for f in fwd_choices:
-        tree.set_tile(f, adj_choices[0])
-        fwd_ms[f] = median_ms(lambda: tree.force(acc))
+    fwd_ms = medians_ms(fwd_choices, lambda f: tree.set_tile(f, adj_choices[0]), lambda: tree.force(acc))
     best_f = min(fwd_ms, key=fwd_ms.get)
-    for e in adj_choices:
-        tree.set_tile(best_f, e)
-        adj_ms[e] = median_ms(lambda: tree.force_vjp(cot, acc, grad))
+    adj_ms = medians_ms(adj_choices, lambda e: tree.set_tile(best_f, e), lambda: tree.force_vjp(cot, acc, grad))
     best = (best_f, min(adj_ms, key=adj_ms.get))
     tree.set_tile(*best)
     if ck:

@@ -463,7 +463,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(D.n_general, 0xff, sizeof(unsigned long long), s);   // counted again by the LPT pass
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
-    if (D.n > 0) {                            // the refit reference: this build's sorted positions
+    if (D.n > 0) {                            // the refit reference: the sorted positions of the latest tree build
         cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(D.ry, D.y, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(D.rz, D.z, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
