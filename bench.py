@@ -13,9 +13,11 @@ r_cut = 3/128, eps = 1/6400, theta = 0.5, n_crit = 64.
 Prints one JSON line.  value = short-range interactions per second, counting
 each (i, list entry) pair of the forward pass and of the adjoint pass once
 (interactions = sum over groups of n_i * n_j, the paper's count).  With N > 1
-every rank runs an independent replica (the path does not shard one box), so
-scaling is weak and value sums the ranks' interactions over the slowest rank's
-time.  --impl reference times the CPU FP64 oracle on a bounded sample.
+every rank runs an independent replica of the box, so scaling is weak and
+value sums the ranks' interactions over the slowest rank's time; the batched
+workload (--workload batched-64) shares its 64 boxes among the ranks instead,
+and domain.DomainShortRange splits one box over ranks (tested on gloo ranks).
+--impl reference times the CPU FP64 oracle on a bounded sample.
 """
 from __future__ import annotations
 
