@@ -21,7 +21,10 @@
  *     current device; pointers marked "host" are ordinary host memory.
  *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
  *     stream).  Work is enqueued on it; calls return without waiting unless
- *     stated otherwise.
+ *     stated otherwise.  A tree also owns a second (non-blocking) stream on
+ *     which the builds run the steps that do not depend on each other; it
+ *     forks from and joins back into `stream` by events within each call, so
+ *     the work stays ordered on `stream` and captures into one graph.
  *   - Positions are FP64 [n][3] row-major (x,y,z per particle), any finite
  *     value (they are wrapped into [0,1)).  Masses are FP64 [n] >= 0, or NULL
  *     for equal masses 1/n.

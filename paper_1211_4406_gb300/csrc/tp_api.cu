@@ -130,6 +130,10 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
+// Events of the side stream: after the gather, after the topology, after the
+// monopoles, before and after the LPT order.
+enum { kEvGather, kEvTopology, kEvMoments, kEvLists, kEvOrder, kSideEvents };
+
 struct tp_tree {
     int64_t n = 0;
     int32_t nbox = 0;
@@ -168,7 +172,26 @@ struct tp_tree {
     // kernel timing: events around the main forward / adjoint kernel launches
     bool ktiming = false, kf_rec = false, kv_rec = false;
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // a second stream for the build steps that do not depend on each other
+    // (fork/join by events, so the calls stay ordered on the caller's stream
+    // and capture into one graph): kSideEvents events, see side_fork/side_join
+    cudaStream_t side = nullptr;
+    cudaEvent_t sev[kSideEvents] = {};
 };
+
+// The side stream starts after everything issued on s so far.
+static void side_fork(tp_tree *t, cudaStream_t s, int ev)
+{
+    cudaEventRecord(t->sev[ev], s);
+    cudaStreamWaitEvent(t->side, t->sev[ev], 0);
+}
+
+// s continues after everything issued on the side stream so far.
+static void side_join(tp_tree *t, cudaStream_t s, int ev)
+{
+    cudaEventRecord(t->sev[ev], t->side);
+    cudaStreamWaitEvent(s, t->sev[ev], 0);
+}
 
 static tp_status cuda_status(cudaError_t e)
 {
@@ -391,6 +414,17 @@ static tp_status plan_windows(tp_tree *t, cudaStream_t s, int64_t slot_budget, i
 
 __global__ void k_add_entries(TreeDev V, int64_t *tot) { *tot += *V.n_entries; }
 
+// The lists and their records (k_compact), and beside them on the side
+// stream the LPT order of the work items, which needs only the list counts.
+static void write_and_order(tp_tree *t, TreeDev &V, cudaStream_t s)
+{
+    side_fork(t, s, kEvLists);
+    tp::lpt_order(V, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
+                  t->lpt_tmp, t->side);
+    tp::walk_write(V, s);
+    side_join(t, s, kEvOrder);
+}
+
 // The walk of one window: items, tasks, lists and records, LPT order; list
 // statistics accumulate into the tree's counters.
 static void walk_window(tp_tree *t, TreeDev &V, cudaStream_t s)
@@ -401,9 +435,7 @@ static void walk_window(tp_tree *t, TreeDev &V, cudaStream_t s)
     TP_LAUNCH(k_check_pad, 1, 1, 0, s, V);
     tp::walk_expand(V, reinterpret_cast<unsigned long long *>(t->queue + 2), t->scan_tmp, s);
     TP_LAUNCH(k_check_entries, 1, 1, 0, s, V);
-    tp::walk_write(V, s);
-    tp::lpt_order(V, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
-                  t->lpt_tmp, s);
+    write_and_order(t, V, s);
     tp::list_stats(V, t->d_inter, t->d_maxnj, s);
     TP_LAUNCH(k_add_entries, 1, 1, 0, s, V, t->d_etot);
 }
@@ -463,13 +495,23 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     cudaMemsetAsync(D.n_ambig, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(D.n_general, 0xff, sizeof(unsigned long long), s);   // counted again by the LPT pass
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
-    if (D.n > 0) {                            // the refit reference: the sorted positions of the latest tree build
-        cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(D.ry, D.y, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(D.rz, D.z, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, s);
+    // Side stream: the refit reference (the sorted positions of the latest
+    // tree build), then the monopoles once the topology is final; the
+    // groups go on beside them on s, and the walk waits for both.
+    side_fork(t, s, kEvGather);
+    if (D.n > 0) {
+        cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, t->side);
+        cudaMemcpyAsync(D.ry, D.y, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, t->side);
+        cudaMemcpyAsync(D.rz, D.z, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, t->side);
     }
+    bool moments = false;
     for (int attempt = 0;; attempt++) {
         tp::build_topology(D, t->nch, t->nofs, t->cbnd, t->scan_tmp, s);
+        if (!sync) {                          // no host check can send the topology round again
+            side_fork(t, s, kEvTopology);
+            tp::build_moments(D, t->side);
+            moments = true;
+        }
         tp::build_group_starts(D, t->flag, t->gofs, t->scan_tmp, s);
         if (!sync) break;
         int32_t st = 0;
@@ -490,8 +532,13 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
         }
         break;
     }
+    if (!moments) {
+        side_fork(t, s, kEvTopology);
+        tp::build_moments(D, t->side);
+    }
     TP_LAUNCH(k_clamp_groups, 1, 1, 0, s, D);
     tp::build_groups(D, t->flag, t->gofs, s);
+    side_join(t, s, kEvMoments);
     construction.end();
     NvtxRange traversal("tree traversal");
     // walk: top items per group, then subtree tasks, then the entries
@@ -559,9 +606,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
         }
     }
     TP_LAUNCH(k_check_entries, 1, 1, 0, s, D);
-    tp::walk_write(D, s);
-    tp::lpt_order(D, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
-                  t->lpt_tmp, s);
+    write_and_order(t, D, s);
     return TP_OK;
 }
 
@@ -599,6 +644,12 @@ tp_status tp_build_tree_batched(const double *pos, const double *mass, const int
     for (int b = 0; b < nbox; b++)
         if (per_box[b].flags & TP_FLAG_CHUNKED) t->force_chunked = true;
     t->last = s;
+    bool side_ok = cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &e : t->sev) side_ok = side_ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!side_ok) {
+        tp_tree_free(t);
+        return TP_ERR_CUDA;
+    }
     TreeDev &D = t->D;
     std::memset(&D, 0, sizeof(D));
     D.n = n;
@@ -989,8 +1040,12 @@ tp_status tp_tree_free(tp_tree *t)
     if (!t) return TP_OK;
     if (t->last) cudaStreamSynchronize(t->last);
     else cudaDeviceSynchronize();
+    if (t->side) cudaStreamSynchronize(t->side);   // a build that stopped early may not have joined it
     for (auto &e : t->kev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : t->sev)
+        if (e) cudaEventDestroy(e);
+    if (t->side) cudaStreamDestroy(t->side);
     t->lists.release();
     t->pad.release();
     t->items.release();

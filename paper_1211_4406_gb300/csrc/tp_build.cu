@@ -13,11 +13,40 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kLevelGrid = 152 * 4;   // fixed grid: node counts live on the device
 static_assert(kLevelGrid <= 1024, "the block-sum scratch of the topology passes holds 1024 sums");
+constexpr int kMomBatch = 4;          // particles or children loaded together by k_moments
 
+// x in [+0, 1): read as unsigned integers, the bits of such doubles (and of
+// no others) lie below those of 1.0.
+__device__ __forceinline__ bool unit_interval(double x)
+{
+    return (uint64_t)__double_as_longlong(x) < 0x3ff0000000000000ull;
+}
+
+// x - floor(x), with 1 -> 0 where the difference rounds up to 1.  For x in
+// [+0, 1) floor(x) = +0 and the difference is x itself, which the common case
+// returns without an FP64 operation (GB300 issues those at a small fraction
+// of its integer rate).
 __device__ __forceinline__ double wrap01(double x)
 {
+    if (unit_interval(x)) return x;
     double w = __dsub_rn(x, floor(x));
     return w >= 1.0 ? 0.0 : w;
+}
+
+// tp_fixed64 (x 2^64 truncated to 64 bits) from the IEEE-754 fields when x is
+// in [+0, 1): a normal x is m 2^(e - 1075) with the 53-bit significand m and
+// biased exponent e <= 1022, so x 2^64 = m 2^(e - 1011), a left shift of at
+// most 11 bits or a right shift that truncates; subnormals and shifts of 64
+// bits or more give 0.  Other x take the FP64 conversion.
+__device__ __forceinline__ uint64_t fixed64(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    if (b >= 0x3ff0000000000000ull) return tp_fixed64(x);
+    const int e = (int)(b >> 52);
+    if (e == 0) return 0ull;
+    const uint64_t m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const int sh = e - 1011;
+    return sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ull);
 }
 
 // 21 bits -> every third bit of 63 (bit b lands on 3b).
@@ -34,6 +63,8 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v)
 
 __device__ __forceinline__ uint32_t quantise(double w)
 {
+    // floor(w 2^21) = floor(floor(w 2^64) / 2^43) for w in [0, 1), below 2^21
+    if (unit_interval(w)) return (uint32_t)(fixed64(w) >> 43);
     double q = floor(w * 2097152.0);
     if (q > 2097151.0) q = 2097151.0;
     if (q < 0.0) q = 0.0;
@@ -65,7 +96,7 @@ __global__ void k_gather(const double *pos, const double *mass, TreeDev T)
         const int64_t i = T.perm[s];
         const double x = wrap01(pos[3 * i]), y = wrap01(pos[3 * i + 1]), z = wrap01(pos[3 * i + 2]);
         T.x[s] = x; T.y[s] = y; T.z[s] = z;
-        const uint64_t X = tp_fixed64(x), Y = tp_fixed64(y), Z = tp_fixed64(z);
+        const uint64_t X = fixed64(x), Y = fixed64(y), Z = fixed64(z);
         T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
         T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
         const double m = mass ? mass[i] : T.box[tp_box_of(T.box_off, T.nbox, i)].inv_n;
@@ -91,7 +122,7 @@ __global__ void k_refit_gather(const double *pos, const double *mass, TreeDev T)
             x[c] = __dadd_rn(r[c], __dsub_rn(d, rint(d)));
         }
         T.x[s] = x[0]; T.y[s] = x[1]; T.z[s] = x[2];
-        const uint64_t X = tp_fixed64(wrap01(x[0])), Y = tp_fixed64(wrap01(x[1])), Z = tp_fixed64(wrap01(x[2]));
+        const uint64_t X = fixed64(wrap01(x[0])), Y = fixed64(wrap01(x[1])), Z = fixed64(wrap01(x[2]));
         T.X[s] = X; T.Y[s] = Y; T.Z[s] = Z;
         T.P32[s] = make_uint4((uint32_t)(X >> 32), (uint32_t)(Y >> 32), (uint32_t)(Z >> 32), 0u);
         double m = T.m[s];
@@ -328,7 +359,7 @@ __device__ __forceinline__ double ord_value(uint64_t k)
 // a5: monopoles bottom-up in canonical order (leaf: particles in key order;
 // internal: children in octant order), tight boxes, fixed-point images and
 // the walk record.
-__global__ void k_moments(TreeDev T, int L)
+__global__ void __launch_bounds__(kBlock, 4) k_moments(TreeDev T, int L)
 {
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
@@ -337,29 +368,54 @@ __global__ void k_moments(TreeDev T, int L)
         double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
         uint64_t klx = ~0ull, kly = ~0ull, klz = ~0ull, khx = 0ull, khy = 0ull, khz = 0ull;
         const int32_t nc = T.nchild[i];
+        // Loads four particles (children) at a time, so that their latencies
+        // overlap; an index past the end repeats the last one, which leaves the
+        // min/max unchanged, and the sums take only the real ones, in order.
+        auto minmax = [&](uint64_t ax, uint64_t ay, uint64_t az, uint64_t bx, uint64_t by, uint64_t bz) {
+            klx = ax < klx ? ax : klx; kly = ay < kly ? ay : kly; klz = az < klz ? az : klz;
+            khx = bx > khx ? bx : khx; khy = by > khy ? by : khy; khz = bz > khz ? bz : khz;
+        };
         if (nc == 0) {
             const int32_t f = T.first[i], e = f + T.count[i];
-            for (int32_t p = f; p < e; p++) {
-                const double mp = T.m[p], xp = T.x[p], yp = T.y[p], zp = T.z[p];
-                M = __dadd_rn(M, mp);
-                Sx = __dadd_rn(Sx, __dmul_rn(mp, xp));
-                Sy = __dadd_rn(Sy, __dmul_rn(mp, yp));
-                Sz = __dadd_rn(Sz, __dmul_rn(mp, zp));
-                const uint64_t kx = ord_key(xp), ky = ord_key(yp), kz = ord_key(zp);
-                klx = kx < klx ? kx : klx; kly = ky < kly ? ky : kly; klz = kz < klz ? kz : klz;
-                khx = kx > khx ? kx : khx; khy = ky > khy ? ky : khy; khz = kz > khz ? kz : khz;
+            for (int32_t p0 = f; p0 < e; p0 += kMomBatch) {
+                double mp[kMomBatch], xp[kMomBatch], yp[kMomBatch], zp[kMomBatch];
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    const int32_t p = p0 + k < e ? p0 + k : e - 1;
+                    mp[k] = T.m[p]; xp[k] = T.x[p]; yp[k] = T.y[p]; zp[k] = T.z[p];
+                }
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    const uint64_t kx = ord_key(xp[k]), ky = ord_key(yp[k]), kz = ord_key(zp[k]);
+                    minmax(kx, ky, kz, kx, ky, kz);
+                    if (p0 + k < e) {
+                        M = __dadd_rn(M, mp[k]);
+                        Sx = __dadd_rn(Sx, __dmul_rn(mp[k], xp[k]));
+                        Sy = __dadd_rn(Sy, __dmul_rn(mp[k], yp[k]));
+                        Sz = __dadd_rn(Sz, __dmul_rn(mp[k], zp[k]));
+                    }
+                }
             }
         } else {
-            const int32_t c0 = T.child[i];
-            for (int32_t c = c0; c < c0 + nc; c++) {
-                M = __dadd_rn(M, T.M[c]);
-                Sx = __dadd_rn(Sx, T.Sx[c]);
-                Sy = __dadd_rn(Sy, T.Sy[c]);
-                Sz = __dadd_rn(Sz, T.Sz[c]);
-                const uint64_t ax = ord_key(T.lox[c]), ay = ord_key(T.loy[c]), az = ord_key(T.loz[c]);
-                const uint64_t bx = ord_key(T.hix[c]), by = ord_key(T.hiy[c]), bz = ord_key(T.hiz[c]);
-                klx = ax < klx ? ax : klx; kly = ay < kly ? ay : kly; klz = az < klz ? az : klz;
-                khx = bx > khx ? bx : khx; khy = by > khy ? by : khy; khz = bz > khz ? bz : khz;
+            const int32_t c0 = T.child[i], c1 = c0 + nc;
+            for (int32_t b0 = c0; b0 < c1; b0 += kMomBatch) {
+                double cm[kMomBatch], cx[kMomBatch], cy[kMomBatch], cz[kMomBatch];
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    const int32_t c = b0 + k < c1 ? b0 + k : c1 - 1;
+                    cm[k] = T.M[c]; cx[k] = T.Sx[c]; cy[k] = T.Sy[c]; cz[k] = T.Sz[c];
+                    minmax(ord_key(T.lox[c]), ord_key(T.loy[c]), ord_key(T.loz[c]), ord_key(T.hix[c]),
+                           ord_key(T.hiy[c]), ord_key(T.hiz[c]));
+                }
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    if (b0 + k < c1) {
+                        M = __dadd_rn(M, cm[k]);
+                        Sx = __dadd_rn(Sx, cx[k]);
+                        Sy = __dadd_rn(Sy, cy[k]);
+                        Sz = __dadd_rn(Sz, cz[k]);
+                    }
+                }
             }
         }
         double lx = ord_value(klx), ly = ord_value(kly), lz = ord_value(klz);
@@ -380,16 +436,16 @@ __global__ void k_moments(TreeDev T, int L)
         T.comx[i] = mx; T.comy[i] = my; T.comz[i] = mz;
         // images of the centres (in [0,1) after a build; after a refit they
         // may lie just outside, hence the wrap)
-        const uint64_t CX = tp_fixed64(wrap01(mx)), CY = tp_fixed64(wrap01(my)), CZ = tp_fixed64(wrap01(mz));
+        const uint64_t CX = fixed64(wrap01(mx)), CY = fixed64(wrap01(my)), CZ = fixed64(wrap01(mz));
         T.cX[i] = CX; T.cY[i] = CY; T.cZ[i] = CZ;
         T.nsrc[i] = SrcRec{CX, CY, CZ, (float)M, 0.f};
         WNode w;
-        w.cx = (uint32_t)(tp_fixed64(wrap01(cx)) >> 32);
-        w.cy = (uint32_t)(tp_fixed64(wrap01(cy)) >> 32);
-        w.cz = (uint32_t)(tp_fixed64(wrap01(cz)) >> 32);
-        w.hx = (uint32_t)(tp_fixed64(fx) >> 32);
-        w.hy = (uint32_t)(tp_fixed64(fy) >> 32);
-        w.hz = (uint32_t)(tp_fixed64(fz) >> 32);
+        w.cx = (uint32_t)(fixed64(wrap01(cx)) >> 32);
+        w.cy = (uint32_t)(fixed64(wrap01(cy)) >> 32);
+        w.cz = (uint32_t)(fixed64(wrap01(cz)) >> 32);
+        w.hx = (uint32_t)(fixed64(fx) >> 32);
+        w.hy = (uint32_t)(fixed64(fy) >> 32);
+        w.hz = (uint32_t)(fixed64(fz) >> 32);
         w.child = nc ? T.child[i] : -1;
         w.skip = T.skip[i];
         w.first = T.first[i];
@@ -477,22 +533,18 @@ __global__ void k_group_bbox(TreeDev T)
                 lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
                 hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
             }
-        if (lane == 0) {
-            T.gcount[g] = e - f;
-            double c[3], h[3];
-            for (int k = 0; k < 3; k++) {
-                const double l = __longlong_as_double(lo[k]), u = __longlong_as_double(hi[k]);
-                c[k] = __dmul_rn(__dadd_rn(l, u), 0.5);
-                h[k] = __dmul_rn(__dsub_rn(u, l), 0.5);
-            }
-            T.gcx[g] = c[0]; T.gcy[g] = c[1]; T.gcz[g] = c[2];
-            T.ghx[g] = h[0]; T.ghy[g] = h[1]; T.ghz[g] = h[2];
-            const uint64_t X = tp_fixed64(c[0]), Y = tp_fixed64(c[1]), Z = tp_fixed64(c[2]);
-            T.gX[g] = X; T.gY[g] = Y; T.gZ[g] = Z;
-            T.gux[g] = (uint32_t)(X >> 32); T.guy[g] = (uint32_t)(Y >> 32); T.guz[g] = (uint32_t)(Z >> 32);
-            T.ghux[g] = (uint32_t)(tp_fixed64(h[0]) >> 32);
-            T.ghuy[g] = (uint32_t)(tp_fixed64(h[1]) >> 32);
-            T.ghuz[g] = (uint32_t)(tp_fixed64(h[2]) >> 32);
+        if (lane == 0) T.gcount[g] = e - f;
+        if (lane < 3) {                    // one axis per lane: three FP64 chains side by side
+            const unsigned long long lk = lane == 0 ? lo[0] : (lane == 1 ? lo[1] : lo[2]);
+            const unsigned long long hk = lane == 0 ? hi[0] : (lane == 1 ? hi[1] : hi[2]);
+            const double l = __longlong_as_double(lk), u = __longlong_as_double(hk);
+            const double c = __dmul_rn(__dadd_rn(l, u), 0.5), h = __dmul_rn(__dsub_rn(u, l), 0.5);
+            const uint64_t X = fixed64(c);
+            (lane == 0 ? T.gcx : (lane == 1 ? T.gcy : T.gcz))[g] = c;
+            (lane == 0 ? T.ghx : (lane == 1 ? T.ghy : T.ghz))[g] = h;
+            (lane == 0 ? T.gX : (lane == 1 ? T.gY : T.gZ))[g] = X;
+            (lane == 0 ? T.gux : (lane == 1 ? T.guy : T.guz))[g] = (uint32_t)(X >> 32);
+            (lane == 0 ? T.ghux : (lane == 1 ? T.ghuy : T.ghuz))[g] = (uint32_t)(fixed64(h) >> 32);
         }
     }
 }
@@ -510,7 +562,7 @@ void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, u
     TP_LAUNCH(k_gather, grid_for(T.n, kBlock), kBlock, 0, s, pos, mass, T);
 }
 
-// Topology and monopoles.  nch: scratch of cap_nodes u32; ofs: at least
+// Topology (the monopoles follow in build_moments).  nch: scratch of cap_nodes u32; ofs: at least
 // kLevelGrid u32 (the count pass's block sums).
 void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s)
 {
@@ -519,7 +571,6 @@ void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void 
         TP_LAUNCH(k_split_count, kLevelGrid, kBlock, 0, s, T, L, nch, cb, ofs);
         TP_LAUNCH(k_split_write, kLevelGrid, kBlock, 0, s, T, L, nch, (const uint32_t *)ofs, cb);
     }
-    build_moments(T, s);
 }
 
 // Monopoles of every node, bottom-up by level.

@@ -103,7 +103,8 @@ void scan_impl(const Tin *in, Tout *out, int64_t n_host, const int64_t *d_n, int
 
 // ------------------------------------------------------------------------
 // Radix sort: 8-bit digits, tiles of 4096 items, per-warp stable ranking with
-// __match_any_sync, prefix over (digit, tile) by the device-wide scan.
+// __match_any_sync, prefix over (digit, tile) by the device-wide scan, and
+// stores staged through shared memory in output order.
 // ------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t radix_digit(uint64_t key, uint32_t val, int shift, int mode,
                                                 const int64_t *box_off, int32_t nbox)
@@ -128,18 +129,31 @@ k_radix_hist(const uint64_t *key, const uint32_t *val, int64_t n, int shift, int
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
 }
 
+// The scatter ranks the tile's items stably by digit (per warp with
+// __match_any_sync, then across warps), stages them in shared memory in that
+// order, and writes each digit's run of the tile with consecutive threads on
+// consecutive addresses, so that the stores coalesce instead of landing in up
+// to 32 digit buckets per warp instruction.
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const uint64_t *key, const uint32_t *val, uint64_t *key2, uint32_t *val2,
                 int64_t n, int shift, int mode, const int64_t *box_off, int32_t nbox,
                 const uint32_t *offsets, int64_t nblocks)
 {
-    __shared__ uint32_t whist[kRadixWarps][256];
-    __shared__ uint32_t gofs[256];
+    union Stage {
+        uint32_t whist[kRadixWarps][256];   // per-warp digit counts, then their prefix over warps
+        uint64_t key[kRadixTile];           // the tile's keys in output order, then
+        uint32_t val[kRadixTile];           // its values
+    };
+    __shared__ Stage S;
+    __shared__ uint8_t sdig[kRadixTile];
+    __shared__ uint32_t gofs[256], tstart[256], wsum[kRadixWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) whist[d >> 8][d & 255] = 0;
+    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) S.whist[d >> 8][d & 255] = 0;
     gofs[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)warp * (32 * kRadixItems);
+    const int64_t tile0 = (int64_t)blockIdx.x * kRadixTile;
+    const int ntile = n - tile0 < kRadixTile ? (int)(n - tile0) : kRadixTile;
+    const int64_t base = tile0 + (int64_t)warp * (32 * kRadixItems);
     const unsigned lt = (1u << lane) - 1u;
     uint64_t k[kRadixItems];
     uint32_t v[kRadixItems], dg[kRadixItems], rk[kRadixItems];
@@ -152,30 +166,58 @@ k_radix_scatter(const uint64_t *key, const uint32_t *val, uint64_t *key2, uint32
         const uint32_t d = ok ? radix_digit(k[r], v[r], shift, mode, box_off, nbox) : 256u;
         dg[r] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = d < 256u ? whist[warp][d] : 0u;
+        const uint32_t before = d < 256u ? S.whist[warp][d] : 0u;
         __syncwarp();
-        if (d < 256u && (peers & lt) == 0u) whist[warp][d] = before + __popc(peers);
+        if (d < 256u && (peers & lt) == 0u) S.whist[warp][d] = before + __popc(peers);
         __syncwarp();
         rk[r] = before + __popc(peers & lt);
     }
     __syncthreads();
     {
+        // digit d: prefix over the warps, then the tile's exclusive scan over digits
         const int d = threadIdx.x;
         uint32_t run = 0;
         for (int w = 0; w < kRadixWarps; w++) {
-            const uint32_t c = whist[w][d];
-            whist[w][d] = run;
+            const uint32_t c = S.whist[w][d];
+            S.whist[w][d] = run;
             run += c;
         }
+        uint32_t inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; w++) before += wsum[w];
+        tstart[d] = before + inc - run;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kRadixItems; r++) {
+    for (int r = 0; r < kRadixItems; r++)          // position in the tile's output order
+        if (dg[r] < 256u) rk[r] += tstart[dg[r]] + S.whist[warp][dg[r]];
+    __syncthreads();                               // the counts are read: the stage takes the keys
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++)
         if (dg[r] < 256u) {
-            const uint32_t pos = gofs[dg[r]] + whist[warp][dg[r]] + rk[r];
-            key2[pos] = k[r];
-            val2[pos] = v[r];
+            S.key[rk[r]] = k[r];
+            sdig[rk[r]] = (uint8_t)dg[r];
         }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntile; i += kRadixThreads) {
+        const uint32_t d = sdig[i];
+        key2[gofs[d] + (uint32_t)i - tstart[d]] = S.key[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++)
+        if (dg[r] < 256u) S.val[rk[r]] = v[r];
+    __syncthreads();
+    for (int i = threadIdx.x; i < ntile; i += kRadixThreads) {
+        const uint32_t d = sdig[i];
+        val2[gofs[d] + (uint32_t)i - tstart[d]] = S.val[i];
     }
 }
 

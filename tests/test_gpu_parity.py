@@ -74,6 +74,20 @@ def small_boxes():
     out.append(inputs.Box("wrap", pos, mass, 1.0, 1e-3, 0.15, 0.5))
     pos, mass = inputs.clustered_box(6000, 30, 77)
     out.append(inputs.Box("clustered6k", pos, mass, 1.3, 5e-4, 0.08, 0.5, n_crit=32, n_leaf=4))
+    # coordinates at the edges of the integer fast paths of the wrap, the
+    # 64-bit images and the 21-bit key digits: zeros of both signs,
+    # subnormals, powers of two around 2^-64 and 2^-43, values just below 1
+    # and just below 0 (whose wrap rounds to 1 and becomes 0), 1, and values
+    # outside [0, 1)
+    pos, mass = inputs.uniform_box(600, 11)
+    edge = np.array([0.0, -0.0, 5e-324, 2.0 ** -1022, 2.0 ** -1000, 2.0 ** -70, 2.0 ** -65, 2.0 ** -64,
+                     2.0 ** -63, 3 * 2.0 ** -64, 2.0 ** -44, 2.0 ** -43, 2.0 ** -21, 0.5, 1 - 2.0 ** -53,
+                     1 - 2.0 ** -43, 1 - 2.0 ** -21, 1.0, -2.0 ** -60, -2.0 ** -53, -0.5, 2 - 2.0 ** -52, 3.0,
+                     -1e-300, 7.25])
+    for c in range(3):
+        pos[c * edge.size:(c + 1) * edge.size, c] = edge
+        pos[3 * edge.size:4 * edge.size, c] = np.roll(edge, c)
+    out.append(inputs.Box("edges", pos, mass, 1.0, 1e-3, 0.15, 0.5))
     return out
 
 
