@@ -26,7 +26,7 @@ void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32
                    int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries);
 void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int32_t *queue,
                    const int32_t *order, int64_t G, cudaStream_t s);
-void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s);
+void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, int32_t *leaf_of, cudaStream_t s);
 void force_vjp_pairs_f32(TreeDev &T, float *acc, const float *cot, double *gs, double *ncot, int32_t *queue,
                          const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
                          int adj_entries);
@@ -37,10 +37,11 @@ void count_useful(TreeDev &T, unsigned long long *useful, cudaStream_t s);
 void pair_forward_f32(TreeDev &T, float *acc, int32_t *queue, const int32_t *order, int64_t G,
                       cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int fwd_particles);
 void pair_forward_f64(TreeDev &T, double *acc, int64_t G, cudaStream_t s);
-void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries);
-void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s);
+void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *leaf_of,
+             int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+             int adj_entries);
+void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *leaf_of,
+             int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s);
 }  // namespace tp
 
 static std::atomic<long long> g_launches{0};
@@ -178,6 +179,10 @@ struct tp_tree {
     cudaStream_t side = nullptr;
     cudaEvent_t sev[kSideEvents] = {};
 };
+
+// Scratch of n int32 for the adjoint's epilogue (each particle's leaf): the
+// group-start flags, which only a build uses.
+static int32_t *leaf_scratch(tp_tree *t) { return reinterpret_cast<int32_t *>(t->flag); }
 
 // The side stream starts after everything issued on s so far.
 static void side_fork(tp_tree *t, cudaStream_t s, int ev)
@@ -802,17 +807,19 @@ tp_status tp_short_range_vjp(tp_tree *t, const void *cot, double *grad, void *st
                 tp::vjp_pairs_f64(V, (const double *)cot, t->gs, t->ncot, t->queue, t->order, V.cap_groups, s);
         });
         if (e != TP_OK) return e;
-        tp::vjp_end(t->D, grad, t->gs, t->ncot, s);
+        tp::vjp_end(t->D, grad, t->gs, t->ncot, leaf_scratch(t), s);
         return cuda_status(cudaGetLastError());
     }
     if (t->precision == TP_FP32)
     {
-        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s,
-                    t->ktiming ? t->kev[2] : nullptr, t->ktiming ? t->kev[3] : nullptr, t->adj_entries);
+        tp::vjp_f32(t->D, (const float *)cot, grad, t->gs, t->ncot, leaf_scratch(t), t->queue, t->order,
+                    t->D.cap_groups, s, t->ktiming ? t->kev[2] : nullptr, t->ktiming ? t->kev[3] : nullptr,
+                    t->adj_entries);
         t->kv_rec = t->ktiming && t->D.cap_groups > 0;
     }
     else
-        tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, t->queue, t->order, t->D.cap_groups, s);
+        tp::vjp_f64(t->D, (const double *)cot, grad, t->gs, t->ncot, leaf_scratch(t), t->queue, t->order,
+                    t->D.cap_groups, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -845,7 +852,7 @@ tp_status tp_short_range_force_vjp(tp_tree *t, void *acc, const void *cot, doubl
                                 t->ktiming ? t->kev[3] : nullptr, t->adj_entries);
         t->kv_rec = t->ktiming && t->D.cap_groups > 0;
     }
-    tp::vjp_end(t->D, grad, t->gs, t->ncot, s);
+    tp::vjp_end(t->D, grad, t->gs, t->ncot, leaf_scratch(t), s);
     return cuda_status(cudaGetLastError());
 }
 

@@ -13,7 +13,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kLevelGrid = 152 * 4;   // fixed grid: node counts live on the device
 static_assert(kLevelGrid <= 1024, "the block-sum scratch of the topology passes holds 1024 sums");
-constexpr int kMomBatch = 4;          // particles or children loaded together by k_moments
+constexpr int kMomBatch = 2;          // particles or children loaded together by k_moments
 
 // x in [+0, 1): read as unsigned integers, the bits of such doubles (and of
 // no others) lie below those of 1.0.

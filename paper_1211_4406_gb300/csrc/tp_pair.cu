@@ -1203,65 +1203,72 @@ __global__ void __launch_bounds__(kThreads, 4) k_vjp_epack(TreeDev T, const floa
     }
 }
 
-// Node cotangents reach member particles through the centre of mass:
-// P_a = P_parent(a) + c_a / M_a, taken level by level from the roots down (in
-// place of c_a), so each node's sum runs root..node in that order; then
-// grad_p += m_p P_leaf(p).  Then key order -> input order.
-__global__ void k_pushdown_level(TreeDev T, double *ncot, int L)
+// Node cotangents reach member particles through the centre of mass: with
+// q_a = c_a / M_a (taken as c_a times 1/M_a; 0 for an empty node) and
+// P_a = P_parent(a) + q_a from the roots down, P at a leaf is the sum of q
+// over its ancestors in root-to-leaf order, and grad_p += m_p P_leaf(p).
+// k_node_quot turns every node's c into q in place; k_leaf_sum forms each
+// leaf's P from its chain of parents (at most TP_NLEVELS nodes), stores it in
+// the leaf's own slot (no other chain reads a leaf) and records the leaf of
+// each of its particles; k_unsort_grad then adds m_p P per particle and
+// writes the gradient in input order, with the box's factor G k^3, which the
+// pair kernels leave out of their sums so that its FP64 multiply is taken
+// once per particle here instead of once per entry and tile.
+__global__ void k_node_quot(TreeDev T, double *ncot)
 {
-    const int64_t s0 = T.lstart[L], nl = T.lcount[L];
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nl;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = s0 + k;
-        if (a >= T.cap_nodes) break;
-        double px = 0.0, py = 0.0, pz = 0.0;
-        const int32_t par = T.parent[a];
-        if (par >= 0) {
-            px = ncot[3 * (int64_t)par];
-            py = ncot[3 * (int64_t)par + 1];
-            pz = ncot[3 * (int64_t)par + 2];
-        }
+    const int64_t nn = *T.n_nodes < T.cap_nodes ? *T.n_nodes : T.cap_nodes;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nn;
+         a += (int64_t)gridDim.x * blockDim.x) {
         const double M = T.M[a];
-        if (M > 0.0) {
-            px += ncot[3 * a] / M;
-            py += ncot[3 * a + 1] / M;
-            pz += ncot[3 * a + 2] / M;
-        }
-        ncot[3 * a] = px;
-        ncot[3 * a + 1] = py;
-        ncot[3 * a + 2] = pz;
+        const double r = M > 0.0 ? 1.0 / M : 0.0;
+        ncot[3 * a] *= r;
+        ncot[3 * a + 1] *= r;
+        ncot[3 * a + 2] *= r;
     }
 }
 
-__global__ void k_pushdown_leaves(TreeDev T, double *gs, const double *P)
+__global__ void k_leaf_sum(TreeDev T, double *q, int32_t *leaf_of)
 {
     const int64_t nn = *T.n_nodes < T.cap_nodes ? *T.n_nodes : T.cap_nodes;
+    if (*T.status == TP_ERR_LIST_OVERFLOW) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (T.nchild[i] != 0 || T.count[i] == 0) continue;
-        const double Px = P[3 * i], Py = P[3 * i + 1], Pz = P[3 * i + 2];
-        for (int32_t p = T.first[i]; p < T.first[i] + T.count[i]; p++) {
-            const double mp = T.m[p];
-            gs[3 * (int64_t)p] += mp * Px;
-            gs[3 * (int64_t)p + 1] += mp * Py;
-            gs[3 * (int64_t)p + 2] += mp * Pz;
+        int32_t chain[TP_NLEVELS];
+        int d = 0;
+        for (int32_t a = (int32_t)i; a >= 0 && d < TP_NLEVELS; a = T.parent[a]) chain[d++] = a;
+        double Px = 0.0, Py = 0.0, Pz = 0.0;
+        for (int k = d - 1; k >= 0; k--) {
+            const int64_t a = chain[k];
+            Px += q[3 * a];
+            Py += q[3 * a + 1];
+            Pz += q[3 * a + 2];
         }
+        q[3 * i] = Px;
+        q[3 * i + 1] = Py;
+        q[3 * i + 2] = Pz;
+        const int32_t f = T.first[i], e = f + T.count[i];
+        for (int32_t p = f; p < e; p++) leaf_of[p] = (int32_t)i;
     }
 }
 
-// The pair kernels sum the adjoint without the factor G k^3 (k = 2/r_cut),
-// which is the same for every term of a box, so that its FP64 multiply is
-// taken once per particle here instead of once per entry and tile.
-__global__ void k_unsort3(TreeDev T, const double *gs, double *grad)
+__global__ void k_unsort_grad(TreeDev T, const double *gs, const double *P, const int32_t *leaf_of, double *grad)
 {
+    // after an overflow the leaves may not cover every particle: zeros, as the pair sums are
+    const bool zero = *T.status == TP_ERR_LIST_OVERFLOW;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < T.n;
          s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = T.perm[s];
-        const BoxPrm &P = T.box[T.nbox > 1 ? tp_box_of(T.box_off, T.nbox, o) : 0];
-        const double gk3 = P.gk2 * (2.0 / P.rcut);
-        grad[3 * o] = gk3 * gs[3 * s];
-        grad[3 * o + 1] = gk3 * gs[3 * s + 1];
-        grad[3 * o + 2] = gk3 * gs[3 * s + 2];
+        if (zero) {
+            grad[3 * o] = grad[3 * o + 1] = grad[3 * o + 2] = 0.0;
+            continue;
+        }
+        const int64_t L = leaf_of[s];
+        const BoxPrm &B = T.box[T.nbox > 1 ? tp_box_of(T.box_off, T.nbox, o) : 0];
+        const double gk3 = B.gk2 * (2.0 / B.rcut), mp = T.m[s];
+        grad[3 * o] = gk3 * (gs[3 * s] + mp * P[3 * L]);
+        grad[3 * o + 1] = gk3 * (gs[3 * s + 1] + mp * P[3 * L + 1]);
+        grad[3 * o + 2] = gk3 * (gs[3 * s + 2] + mp * P[3 * L + 2]);
     }
 }
 
@@ -1541,11 +1548,13 @@ void vjp_begin(TreeDev &T, double *gs, double *ncot, cudaStream_t s)
     cudaMemsetAsync(ncot, 0, sizeof(double) * 3 * (size_t)T.cap_nodes, s);
 }
 
-void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, cudaStream_t s)
+// leaf_of: scratch of n int32.
+void vjp_end(TreeDev &T, double *grad, double *gs, double *ncot, int32_t *leaf_of, cudaStream_t s)
 {
-    for (int L = 0; L < TP_NLEVELS; L++) TP_LAUNCH(k_pushdown_level, 152 * 2, 256, 0, s, T, ncot, L);
-    TP_LAUNCH(k_pushdown_leaves, 152 * 4, 256, 0, s, T, gs, ncot);
-    TP_LAUNCH(k_unsort3, grid_for(T.n, 256), 256, 0, s, T, gs, grad);
+    if (T.n == 0) return;
+    TP_LAUNCH(k_node_quot, grid_for(T.cap_nodes, 256), 256, 0, s, T, ncot);
+    TP_LAUNCH(k_leaf_sum, grid_for(T.cap_nodes, 128), 128, 0, s, T, ncot, leaf_of);
+    TP_LAUNCH(k_unsort_grad, grid_for(T.n, 256), 256, 0, s, T, gs, ncot, leaf_of, grad);
 }
 
 void vjp_pairs_f32(TreeDev &T, const float *cot, double *gs, double *ncot, int32_t *queue, const int32_t *order,
@@ -1583,20 +1592,21 @@ void vjp_pairs_f64(TreeDev &T, const double *cot, double *gs, double *ncot, int3
     vjp_pairs<double>(T, cot, gs, ncot, queue, order, G, s, nullptr, nullptr);
 }
 
-void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, int adj_entries)
+void vjp_f32(TreeDev &T, const float *cot, double *grad, double *gs, double *ncot, int32_t *leaf_of,
+             int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+             int adj_entries)
 {
     vjp_begin(T, gs, ncot, s);
     vjp_pairs<float>(T, cot, gs, ncot, queue, order, G, s, ev0, ev1, nullptr, adj_entries);
-    vjp_end(T, grad, gs, ncot, s);
+    vjp_end(T, grad, gs, ncot, leaf_of, s);
 }
 
-void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *queue,
-             const int32_t *order, int64_t G, cudaStream_t s)
+void vjp_f64(TreeDev &T, const double *cot, double *grad, double *gs, double *ncot, int32_t *leaf_of,
+             int32_t *queue, const int32_t *order, int64_t G, cudaStream_t s)
 {
     vjp_begin(T, gs, ncot, s);
     vjp_pairs<double>(T, cot, gs, ncot, queue, order, G, s, nullptr, nullptr);
-    vjp_end(T, grad, gs, ncot, s);
+    vjp_end(T, grad, gs, ncot, leaf_of, s);
 }
 
 }  // namespace tp

@@ -121,10 +121,15 @@ k_radix_hist(const uint64_t *key, const uint32_t *val, int64_t n, int shift, int
     hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    uint32_t d[kRadixItems];               // all loads first, so that they are in flight together
+#pragma unroll
     for (int r = 0; r < kRadixItems; r++) {
         const int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
-        if (i < n) atomicAdd(&hist[radix_digit(key[i], val[i], shift, mode, box_off, nbox)], 1u);
+        d[r] = i < n ? radix_digit(key[i], mode ? val[i] : 0u, shift, mode, box_off, nbox) : 256u;
     }
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++)
+        if (d[r] < 256u) atomicAdd(&hist[d[r]], 1u);
     __syncthreads();
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
 }
@@ -158,11 +163,15 @@ k_radix_scatter(const uint64_t *key, const uint32_t *val, uint64_t *key2, uint32
     uint64_t k[kRadixItems];
     uint32_t v[kRadixItems], dg[kRadixItems], rk[kRadixItems];
 #pragma unroll
-    for (int r = 0; r < kRadixItems; r++) {
+    for (int r = 0; r < kRadixItems; r++) {     // all loads first, so that they are in flight together
         const int64_t i = base + r * 32 + lane;
         const bool ok = i < n;
         k[r] = ok ? key[i] : 0ull;
         v[r] = ok ? val[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRadixItems; r++) {
+        const bool ok = base + r * 32 + lane < n;
         const uint32_t d = ok ? radix_digit(k[r], v[r], shift, mode, box_off, nbox) : 256u;
         dg[r] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
