@@ -14,6 +14,8 @@ namespace tp {
 void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, uint64_t *key2,
                             uint32_t *perm2, void *radix_tmp, cudaStream_t s);
 void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s);
+void build_boxes(TreeDev &T, cudaStream_t s);
+void build_masses(TreeDev &T, cudaStream_t s);
 void build_group_starts(TreeDev &T, uint32_t *flag, uint32_t *gofs, void *scan_tmp, cudaStream_t s);
 void build_groups(TreeDev &T, const uint32_t *flag, const uint32_t *gofs, cudaStream_t s);
 void walk_top_count(TreeDev &T, int32_t split, void *scan_tmp, cudaStream_t s);
@@ -132,8 +134,8 @@ bool is_device_ptr(const void *p)
 }  // namespace
 
 // Events of the side stream: after the gather, after the topology, after the
-// monopoles, before and after the LPT order.
-enum { kEvGather, kEvTopology, kEvMoments, kEvLists, kEvOrder, kSideEvents };
+// node boxes, after the monopoles, before and after the LPT order.
+enum { kEvGather, kEvTopology, kEvBoxes, kEvMasses, kEvLists, kEvOrder, kSideEvents };
 
 struct tp_tree {
     int64_t n = 0;
@@ -419,10 +421,25 @@ static tp_status plan_windows(tp_tree *t, cudaStream_t s, int64_t slot_budget, i
 
 __global__ void k_add_entries(TreeDev V, int64_t *tot) { *tot += *V.n_entries; }
 
-// The lists and their records (k_compact), and beside them on the side
-// stream the LPT order of the work items, which needs only the list counts.
+// Node boxes and walk records, then the monopoles, on the side stream once
+// the topology issued on s is final: the walk waits for the boxes only
+// (kEvBoxes), the compaction and every later use for the monopoles
+// (kEvMasses), which thus run beside the walk.
+static void fork_moments(tp_tree *t, cudaStream_t s)
+{
+    side_fork(t, s, kEvTopology);
+    tp::build_boxes(t->D, t->side);
+    cudaEventRecord(t->sev[kEvBoxes], t->side);
+    tp::build_masses(t->D, t->side);
+    cudaEventRecord(t->sev[kEvMasses], t->side);
+}
+
+// The lists and their records (k_compact, which reads the monopoles' source
+// records), and beside them on the side stream the LPT order of the work
+// items, which needs only the list counts.
 static void write_and_order(tp_tree *t, TreeDev &V, cudaStream_t s)
 {
+    cudaStreamWaitEvent(s, t->sev[kEvMasses], 0);
     side_fork(t, s, kEvLists);
     tp::lpt_order(V, t->lpt_key, reinterpret_cast<uint32_t *>(t->order), t->lpt_key2, t->lpt_val2,
                   t->lpt_tmp, t->side);
@@ -501,8 +518,8 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     cudaMemsetAsync(D.n_general, 0xff, sizeof(unsigned long long), s);   // counted again by the LPT pass
     tp::build_keys_sort_gather(D, pos, mass, t->key2, t->perm2, t->radix_tmp, s);
     // Side stream: the refit reference (the sorted positions of the latest
-    // tree build), then the monopoles once the topology is final; the
-    // groups go on beside them on s, and the walk waits for both.
+    // tree build), then the boxes and monopoles once the topology is final
+    // (fork_moments); the groups go on beside them on s.
     side_fork(t, s, kEvGather);
     if (D.n > 0) {
         cudaMemcpyAsync(D.rx, D.x, sizeof(double) * (size_t)D.n, cudaMemcpyDeviceToDevice, t->side);
@@ -513,8 +530,7 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
     for (int attempt = 0;; attempt++) {
         tp::build_topology(D, t->nch, t->nofs, t->cbnd, t->scan_tmp, s);
         if (!sync) {                          // no host check can send the topology round again
-            side_fork(t, s, kEvTopology);
-            tp::build_moments(D, t->side);
+            fork_moments(t, s);
             moments = true;
         }
         tp::build_group_starts(D, t->flag, t->gofs, t->scan_tmp, s);
@@ -537,18 +553,16 @@ static tp_status run_build(tp_tree *t, const double *pos, const double *mass, cu
         }
         break;
     }
-    if (!moments) {
-        side_fork(t, s, kEvTopology);
-        tp::build_moments(D, t->side);
-    }
+    if (!moments) fork_moments(t, s);
     TP_LAUNCH(k_clamp_groups, 1, 1, 0, s, D);
     tp::build_groups(D, t->flag, t->gofs, s);
-    side_join(t, s, kEvMoments);
+    cudaStreamWaitEvent(s, t->sev[kEvBoxes], 0);
     construction.end();
     NvtxRange traversal("tree traversal");
     // walk: top items per group, then subtree tasks, then the entries
     tp::walk_top_count(D, t->split, t->scan_tmp, s);
     if (!sync && t->chunked) {             // the next force/vjp call plans the windows
+        cudaStreamWaitEvent(s, t->sev[kEvMasses], 0);
         t->windows_stale = true;
         return TP_OK;
     }

@@ -13,7 +13,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kLevelGrid = 152 * 4;   // fixed grid: node counts live on the device
 static_assert(kLevelGrid <= 1024, "the block-sum scratch of the topology passes holds 1024 sums");
-constexpr int kMomBatch = 2;          // particles or children loaded together by k_moments
+constexpr int kMomBatch = 2;          // particles or children loaded together by k_boxes / k_masses
 
 // x in [+0, 1): read as unsigned integers, the bits of such doubles (and of
 // no others) lie below those of 1.0.
@@ -356,25 +356,94 @@ __device__ __forceinline__ double ord_value(uint64_t k)
     return __longlong_as_double((long long)b);
 }
 
-// a5: monopoles bottom-up in canonical order (leaf: particles in key order;
-// internal: children in octant order), tight boxes, fixed-point images and
-// the walk record.
-__global__ void __launch_bounds__(kBlock, 4) k_moments(TreeDev T, int L)
+// a5, in two passes per level, bottom up.  k_boxes: tight boxes (leaf: the
+// particles; internal: the children), their centres and half-widths and the
+// walk record, which is all the walk reads.  k_masses: monopoles in canonical
+// order (leaf: particles in key order; internal: children in octant order),
+// centres of mass and their fixed-point images (the source records of
+// monopole entries), needed from the compaction on; the build runs them
+// beside the walk.  Loads take two particles (children) at a time, so that
+// their latencies overlap; an index past the end repeats the last one, which
+// leaves a min/max unchanged, and the sums take only the real ones, in order.
+// The box of node i from the min/max keys of its particles or children: its
+// bounds, centre, half-widths and walk record.
+__device__ __forceinline__ void write_box(TreeDev &T, int32_t i, uint64_t klx, uint64_t kly, uint64_t klz,
+                                          uint64_t khx, uint64_t khy, uint64_t khz)
+{
+    double lx = ord_value(klx), ly = ord_value(kly), lz = ord_value(klz);
+    double hx = ord_value(khx), hy = ord_value(khy), hz = ord_value(khz);
+    const int32_t cnt = T.count[i];
+    if (cnt == 0) { lx = ly = lz = hx = hy = hz = 0.0; }
+    T.lox[i] = lx; T.loy[i] = ly; T.loz[i] = lz;
+    T.hix[i] = hx; T.hiy[i] = hy; T.hiz[i] = hz;
+    const double cx = __dmul_rn(__dadd_rn(lx, hx), 0.5), cy = __dmul_rn(__dadd_rn(ly, hy), 0.5),
+                 cz = __dmul_rn(__dadd_rn(lz, hz), 0.5);
+    const double fx = __dmul_rn(__dsub_rn(hx, lx), 0.5), fy = __dmul_rn(__dsub_rn(hy, ly), 0.5),
+                 fz = __dmul_rn(__dsub_rn(hz, lz), 0.5);
+    T.cenx[i] = cx; T.ceny[i] = cy; T.cenz[i] = cz;
+    T.hfx[i] = fx; T.hfy[i] = fy; T.hfz[i] = fz;
+    WNode w;
+    w.cx = (uint32_t)(fixed64(wrap01(cx)) >> 32);
+    w.cy = (uint32_t)(fixed64(wrap01(cy)) >> 32);
+    w.cz = (uint32_t)(fixed64(wrap01(cz)) >> 32);
+    w.hx = (uint32_t)(fixed64(fx) >> 32);
+    w.hy = (uint32_t)(fixed64(fy) >> 32);
+    w.hz = (uint32_t)(fixed64(fz) >> 32);
+    const int32_t nc = T.nchild[i];
+    w.child = nc ? T.child[i] : -1;
+    w.skip = T.skip[i];
+    w.first = T.first[i];
+    w.count = cnt;
+    w.level = T.level[i];
+    w.pad = 0;
+    T.wn[i] = w;
+}
+
+__global__ void __launch_bounds__(kBlock) k_boxes(TreeDev T, int L)
+{
+    const int64_t nl = T.lcount[L], s0 = T.lstart[L];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = (int32_t)(s0 + t);
+        uint64_t klx = ~0ull, kly = ~0ull, klz = ~0ull, khx = 0ull, khy = 0ull, khz = 0ull;
+        auto minmax = [&](uint64_t ax, uint64_t ay, uint64_t az, uint64_t bx, uint64_t by, uint64_t bz) {
+            klx = ax < klx ? ax : klx; kly = ay < kly ? ay : kly; klz = az < klz ? az : klz;
+            khx = bx > khx ? bx : khx; khy = by > khy ? by : khy; khz = bz > khz ? bz : khz;
+        };
+        const int32_t nc = T.nchild[i];
+        if (nc == 0) {
+            const int32_t f = T.first[i], e = f + T.count[i];
+            for (int32_t p0 = f; p0 < e; p0 += kMomBatch) {
+                double xp[kMomBatch], yp[kMomBatch], zp[kMomBatch];
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    const int32_t p = p0 + k < e ? p0 + k : e - 1;
+                    xp[k] = T.x[p]; yp[k] = T.y[p]; zp[k] = T.z[p];
+                }
+#pragma unroll
+                for (int k = 0; k < kMomBatch; k++) {
+                    const uint64_t kx = ord_key(xp[k]), ky = ord_key(yp[k]), kz = ord_key(zp[k]);
+                    minmax(kx, ky, kz, kx, ky, kz);
+                }
+            }
+        } else {
+            const int32_t c0 = T.child[i];
+            for (int32_t c = c0; c < c0 + nc; c++)
+                minmax(ord_key(T.lox[c]), ord_key(T.loy[c]), ord_key(T.loz[c]), ord_key(T.hix[c]),
+                       ord_key(T.hiy[c]), ord_key(T.hiz[c]));
+        }
+        write_box(T, i, klx, kly, klz, khx, khy, khz);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_masses(TreeDev T, int L)
 {
     const int64_t nl = T.lcount[L], s0 = T.lstart[L];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nl;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = (int32_t)(s0 + t);
         double M = 0.0, Sx = 0.0, Sy = 0.0, Sz = 0.0;
-        uint64_t klx = ~0ull, kly = ~0ull, klz = ~0ull, khx = 0ull, khy = 0ull, khz = 0ull;
         const int32_t nc = T.nchild[i];
-        // Loads four particles (children) at a time, so that their latencies
-        // overlap; an index past the end repeats the last one, which leaves the
-        // min/max unchanged, and the sums take only the real ones, in order.
-        auto minmax = [&](uint64_t ax, uint64_t ay, uint64_t az, uint64_t bx, uint64_t by, uint64_t bz) {
-            klx = ax < klx ? ax : klx; kly = ay < kly ? ay : kly; klz = az < klz ? az : klz;
-            khx = bx > khx ? bx : khx; khy = by > khy ? by : khy; khz = bz > khz ? bz : khz;
-        };
         if (nc == 0) {
             const int32_t f = T.first[i], e = f + T.count[i];
             for (int32_t p0 = f; p0 < e; p0 += kMomBatch) {
@@ -386,8 +455,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_moments(TreeDev T, int L)
                 }
 #pragma unroll
                 for (int k = 0; k < kMomBatch; k++) {
-                    const uint64_t kx = ord_key(xp[k]), ky = ord_key(yp[k]), kz = ord_key(zp[k]);
-                    minmax(kx, ky, kz, kx, ky, kz);
                     if (p0 + k < e) {
                         M = __dadd_rn(M, mp[k]);
                         Sx = __dadd_rn(Sx, __dmul_rn(mp[k], xp[k]));
@@ -404,8 +471,6 @@ __global__ void __launch_bounds__(kBlock, 4) k_moments(TreeDev T, int L)
                 for (int k = 0; k < kMomBatch; k++) {
                     const int32_t c = b0 + k < c1 ? b0 + k : c1 - 1;
                     cm[k] = T.M[c]; cx[k] = T.Sx[c]; cy[k] = T.Sy[c]; cz[k] = T.Sz[c];
-                    minmax(ord_key(T.lox[c]), ord_key(T.loy[c]), ord_key(T.loz[c]), ord_key(T.hix[c]),
-                           ord_key(T.hiy[c]), ord_key(T.hiz[c]));
                 }
 #pragma unroll
                 for (int k = 0; k < kMomBatch; k++) {
@@ -418,41 +483,17 @@ __global__ void __launch_bounds__(kBlock, 4) k_moments(TreeDev T, int L)
                 }
             }
         }
-        double lx = ord_value(klx), ly = ord_value(kly), lz = ord_value(klz);
-        double hx = ord_value(khx), hy = ord_value(khy), hz = ord_value(khz);
-        if (T.count[i] == 0) { lx = ly = lz = hx = hy = hz = 0.0; }
         T.M[i] = M; T.Sx[i] = Sx; T.Sy[i] = Sy; T.Sz[i] = Sz;
-        T.lox[i] = lx; T.loy[i] = ly; T.loz[i] = lz;
-        T.hix[i] = hx; T.hiy[i] = hy; T.hiz[i] = hz;
-        const double cx = __dmul_rn(__dadd_rn(lx, hx), 0.5), cy = __dmul_rn(__dadd_rn(ly, hy), 0.5),
-                     cz = __dmul_rn(__dadd_rn(lz, hz), 0.5);
-        const double fx = __dmul_rn(__dsub_rn(hx, lx), 0.5), fy = __dmul_rn(__dsub_rn(hy, ly), 0.5),
-                     fz = __dmul_rn(__dsub_rn(hz, lz), 0.5);
-        T.cenx[i] = cx; T.ceny[i] = cy; T.cenz[i] = cz;
-        T.hfx[i] = fx; T.hfy[i] = fy; T.hfz[i] = fz;
-        const double mx = M > 0.0 ? __ddiv_rn(Sx, M) : cx;
-        const double my = M > 0.0 ? __ddiv_rn(Sy, M) : cy;
-        const double mz = M > 0.0 ? __ddiv_rn(Sz, M) : cz;
+        // an empty node's centre of mass is its box centre (k_boxes ran first)
+        const double mx = M > 0.0 ? __ddiv_rn(Sx, M) : T.cenx[i];
+        const double my = M > 0.0 ? __ddiv_rn(Sy, M) : T.ceny[i];
+        const double mz = M > 0.0 ? __ddiv_rn(Sz, M) : T.cenz[i];
         T.comx[i] = mx; T.comy[i] = my; T.comz[i] = mz;
         // images of the centres (in [0,1) after a build; after a refit they
         // may lie just outside, hence the wrap)
         const uint64_t CX = fixed64(wrap01(mx)), CY = fixed64(wrap01(my)), CZ = fixed64(wrap01(mz));
         T.cX[i] = CX; T.cY[i] = CY; T.cZ[i] = CZ;
         T.nsrc[i] = SrcRec{CX, CY, CZ, (float)M, 0.f};
-        WNode w;
-        w.cx = (uint32_t)(fixed64(wrap01(cx)) >> 32);
-        w.cy = (uint32_t)(fixed64(wrap01(cy)) >> 32);
-        w.cz = (uint32_t)(fixed64(wrap01(cz)) >> 32);
-        w.hx = (uint32_t)(fixed64(fx) >> 32);
-        w.hy = (uint32_t)(fixed64(fy) >> 32);
-        w.hz = (uint32_t)(fixed64(fz) >> 32);
-        w.child = nc ? T.child[i] : -1;
-        w.skip = T.skip[i];
-        w.first = T.first[i];
-        w.count = T.count[i];
-        w.level = L;
-        w.pad = 0;
-        T.wn[i] = w;
     }
 }
 
@@ -562,8 +603,9 @@ void build_keys_sort_gather(TreeDev &T, const double *pos, const double *mass, u
     TP_LAUNCH(k_gather, grid_for(T.n, kBlock), kBlock, 0, s, pos, mass, T);
 }
 
-// Topology (the monopoles follow in build_moments).  nch: scratch of cap_nodes u32; ofs: at least
-// kLevelGrid u32 (the count pass's block sums).
+// Topology (boxes and monopoles follow in build_boxes, build_masses).  nch:
+// scratch of cap_nodes u32; ofs: at least kLevelGrid u32 (the count pass's
+// block sums).
 void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void *scan_tmp, cudaStream_t s)
 {
     TP_LAUNCH(k_init_roots, (T.nbox + 127) / 128, 128, 0, s, T);
@@ -573,10 +615,22 @@ void build_topology(TreeDev &T, uint32_t *nch, uint32_t *ofs, int32_t *cb, void 
     }
 }
 
-// Monopoles of every node, bottom-up by level.
+// Boxes and walk records of every node, bottom-up by level.
+void build_boxes(TreeDev &T, cudaStream_t s)
+{
+    for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_boxes, kLevelGrid, kBlock, 0, s, T, L);
+}
+
+// Monopoles of every node, bottom-up by level (after build_boxes).
+void build_masses(TreeDev &T, cudaStream_t s)
+{
+    for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_masses, kLevelGrid, kBlock, 0, s, T, L);
+}
+
 void build_moments(TreeDev &T, cudaStream_t s)
 {
-    for (int L = TP_MAX_LEVEL; L >= 0; L--) TP_LAUNCH(k_moments, kLevelGrid, kBlock, 0, s, T, L);
+    build_boxes(T, s);
+    build_masses(T, s);
 }
 
 // New positions for a refit (same particles, same sorted order).
