@@ -260,7 +260,7 @@ __global__ void k_item_bounds(TreeDev T)
 // lane's group record sits in shared memory, where the testing lanes read
 // their owner's, the ambiguous-decision count is a block counter and the
 // item and budget are 32-bit: the kernel fits 56 registers, nine blocks per
-// SM (measured 5 % faster than 72 registers and seven blocks; 8 bytes spill).
+// SM (measured 5 % faster than 72 registers and seven blocks; 12 bytes spill).
 __global__ void __launch_bounds__(kBlock, 9) k_walk_task(TreeDev T, unsigned long long *counter)
 {
     const int64_t NI = *T.n_items < T.cap_items ? *T.n_items : T.cap_items;
@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kBlock, 9) k_walk_task(TreeDev T, unsigned lon
     __shared__ WalkGroup sW[kBlock];       // each lane's group, read by the lanes testing its particles
     int32_t *out = nullptr;
     int32_t nd = -1, end = -1, pcur = 0, pend = 0, cnt = 0, bound = 0;
+    bool pall = false;                     // the pending particles need no test
     int32_t budget = 0;                    // node visits left (the bound below 2^31)
     for (;;) {
         __syncwarp();                      // the last round's reads of sW before new items overwrite it
@@ -335,14 +336,10 @@ __global__ void __launch_bounds__(kBlock, 9) k_walk_task(TreeDev T, unsigned lon
                     if (cnt < bound) out[cnt] = -(nd + 1);
                     cnt++;
                     nd = w.skip;
-                } else if (w.child < 0 && allin) {     // an opened leaf wholly within r_cut: every particle
-                    for (int32_t k = 0; k < w.count; k++)
-                        if (cnt + k < bound) out[cnt + k] = w.first + k;
-                    cnt += w.count;
-                    nd = w.skip;
-                } else if (w.child < 0) {              // an opened leaf: its particles tested below
-                    pcur = w.first;
+                } else if (w.child < 0) {              // an opened leaf: its particles enter below,
+                    pcur = w.first;                    // untested when it lies wholly within r_cut
                     pend = w.first + w.count;
+                    pall = allin;
                     nd = w.skip;
                 } else {
                     nd = w.child;
@@ -353,7 +350,9 @@ __global__ void __launch_bounds__(kBlock, 9) k_walk_task(TreeDev T, unsigned lon
         // 32 at a time: lane k takes the k-th pending particle in lane order
         // and its owner's group from shared memory; a ballot ranks the kept ones
         // within each owner, which writes them in particle order after its
-        // entries so far (the list order of a lane-by-lane walk).
+        // entries so far (the list order of a lane-by-lane walk).  The
+        // particles of a leaf wholly within r_cut are kept without a test, in
+        // the same rounds, so that no lane writes a leaf alone.
         for (;;) {
             const bool has = it >= 0 && pcur < pend;
             if (!__ballot_sync(full, has)) break;
@@ -375,10 +374,10 @@ __global__ void __launch_bounds__(kBlock, 9) k_walk_task(TreeDev T, unsigned lon
             const int32_t cj = __shfl_sync(full, cnt, j), bj = __shfl_sync(full, bound, j);
             int32_t *oj = reinterpret_cast<int32_t *>(
                 __shfl_sync(full, reinterpret_cast<unsigned long long>(out), j));
-            const bool tester = lane < total;
+            const bool tester = lane < total, aj = __shfl_sync(full, pall, j);
             const int32_t p = pj + (lane - sj);
             int namb = 0;
-            const bool keep = tester && keep_particle(T, Wj, p, namb);
+            const bool keep = tester && (aj || keep_particle(T, Wj, p, namb));
             if (namb) atomicAdd(&s_ambig, (unsigned long long)namb);
             const unsigned kept = __ballot_sync(full, keep);
             if (keep) {
