@@ -639,11 +639,11 @@ __global__ void __launch_bounds__(kThreads) k_pair_packed(TreeDev T, float *acc,
 //   v  = m_j J' w_i = alpha w_i + beta d',  alpha = m_j phi, beta = m_j psi (d'.w_i)
 // and dL/dx_i -= G k^3 v, dL/dx_j += G k^3 v (a node passes its share to its
 // centre-of-mass cotangent); the kernels add -v and +v, and the common factor
-// G k^3 of a box is applied per particle at the end (k_unsort3).  Threads hold
-// list entries (j) and loop over the
-// group's particles (i) held in shared memory, so the j side sums in
-// registers; the i side (A_i = sum alpha, B_i = sum beta d') is a full-warp
-// butterfly per i, added into FP64 shared accumulators.
+// G k^3 of a box is applied per particle at the end (k_unsort_grad).
+// Threads hold list entries (j) and loop over the group's particles (i) held
+// in shared memory, so the j side sums in registers; the i side (A_i = sum
+// alpha, B_i = sum beta d') is reduce-scattered across each warp and summed
+// over the tiles in compensated FP32 (the kernels below).
 // ---------------------------------------------------------------------------
 
 // g and g'/xi in the cancellation-free form (u = max(0, 2 - xi),
