@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from paper_1211_4406_gb300 import inputs
-from paper_1211_4406_gb300.api import Params, ShortRangeTree
+from paper_1211_4406_gb300.api import CapturedStep, Params, ShortRangeTree
 
 pytestmark = pytest.mark.gpu
 
@@ -255,6 +255,49 @@ def test_lognormal_masses_far_images_and_default_mass():
     t_none = ShortRangeTree(p, None, prm)
     t_expl = ShortRangeTree(p, torch.full((base.n,), 1.0 / base.n, dtype=torch.float64, device="cuda"), prm)
     assert torch.equal(t_none.force(), t_expl.force())
+
+
+def test_rebuild_on_a_side_stream_and_from_a_graph_equals_a_fresh_build():
+    """A build forks work onto the tree's own second stream and joins it back
+    into the caller's stream: after a rebuild from new positions on another
+    stream, and after a graph replay of the rebuild, the keys, nodes
+    (monopoles included), groups, lists and one-pass forces equal those of a
+    fresh build on the same positions."""
+    pos0, mass = inputs.clustered_box(6000, 30, 77)
+    pos1 = pos0 + 0.002 * np.sin(np.arange(pos0.size, dtype=np.float64).reshape(pos0.shape))
+    prm = Params(1.3, 5e-4, 0.08, 0.5, 32, 4, "fp32")
+    dev = torch.device("cuda")
+    m = torch.tensor(mass, device=dev)
+    cot = torch.tensor(inputs.cotangent(pos0.shape[0], 31), device=dev)
+    fresh = ShortRangeTree(torch.tensor(pos1, device=dev), m, prm)
+    ref = [fresh.export_keys(), fresh.export_nodes(), fresh.export_groups(), fresh.export_lists()]
+    a_ref, _ = fresh.force_vjp(cot)
+    a_ref = a_ref.clone()
+
+    def same(t):
+        got = [t.export_keys(), t.export_nodes(), t.export_groups(), t.export_lists()]
+        for x, y in zip(got, ref):
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v)
+
+    t = ShortRangeTree(torch.tensor(pos0, device=dev), m, prm)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    t.rebuild(torch.tensor(pos1, device=dev), m, stream=side)
+    assert t.status() == 0
+    same(t)
+    p = torch.tensor(pos0, device=dev)
+    acc = torch.empty((t.n, 3), dtype=torch.float32, device=dev)
+    grad = torch.empty((t.n, 3), dtype=torch.float64, device=dev)
+    step = CapturedStep(t, p, m, cot, acc, grad)
+    p.copy_(torch.tensor(pos1, device=dev))
+    step.replay()
+    torch.cuda.synchronize()
+    assert t.status() == 0
+    same(t)
+    assert torch.equal(acc, a_ref)
+    t.close()
+    fresh.close()
 
 
 @pytest.mark.parametrize("box", small_boxes() + [inputs.config_box(1), inputs.config_box(4)],
