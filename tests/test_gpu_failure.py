@@ -7,6 +7,10 @@
   no spin-waits on flags.)
 - Rebuilding the same inputs reproduces keys, lists and FP32 forces bit for
   bit; the adjoint, summed with FP64 atomics, agrees to 1e-12 of its scale.
+- A rebuild whose lists outgrow the capacities of the allocating build
+  latches TP_ERR_LIST_OVERFLOW, and the forces and the adjoint of the
+  following one-pass call are zeros (every kernel bounds its writes by the
+  capacities and skips the lists once the status is latched).
 """
 import numpy as np
 import pytest
@@ -19,6 +23,7 @@ from paper_1211_4406_gb300.api import Params, ShortRangeTree
 pytestmark = pytest.mark.gpu
 
 TP_ERR_TIMEOUT = -5
+TP_ERR_LIST_OVERFLOW = -4
 
 
 def make_tree():
@@ -64,3 +69,23 @@ def test_rebuilds_are_deterministic():
     assert torch.equal(a1, a2)
     t1.close()
     t2.close()
+
+
+def test_rebuild_past_the_capacities_writes_zeros():
+    n = 8192
+    rng = np.random.default_rng(12)
+    prm = Params(G=1.0, eps=1e-3, r_cut=0.05, theta=0.5, n_crit=64)
+    t = ShortRangeTree(torch.tensor(rng.random((n, 3)), device="cuda"), None, prm)
+    assert t.status() == 0
+    # every particle within a 0.02 cube: each group's list holds all n
+    # particles, far beyond the capacities taken from the uniform box
+    t.rebuild(torch.tensor(0.5 + 0.02 * rng.random((n, 3)), device="cuda"), None)
+    assert t.status() == TP_ERR_LIST_OVERFLOW
+    cot = torch.tensor(inputs.cotangent(n, 13), device="cuda")
+    acc = torch.full((n, 3), 7.0, dtype=torch.float32, device="cuda")
+    grad = torch.full((n, 3), 7.0, dtype=torch.float64, device="cuda")
+    t.force_vjp(cot, acc, grad)
+    torch.cuda.synchronize()
+    assert t.status() == TP_ERR_LIST_OVERFLOW
+    assert not bool(acc.any()) and not bool(grad.any())
+    t.close()
